@@ -1,0 +1,198 @@
+/*
+ * mpsm.h -- C ABI of libmpsm, a GB300 (sm_103a) implementation of the MPSM
+ * massively parallel sort-merge equi-join (Albutiu, Kemper, Neumann, "Massively
+ * Parallel Sort-Merge Joins in Main Memory Multi-Core Database Systems").
+ *
+ * The join R |><| S on 64-bit keys runs as the paper's range-partitioned P-MPSM
+ * (Sec. 3.2, Fig. 5), with the two inputs in these roles:
+ *   - R is cut into T_R chunks, each sorted independently into a run
+ *     (phase 1, Sec. 2.1/3.2); runs are never merged (Sec. 2);
+ *   - S is range-partitioned by splitters computed from histograms and prefix
+ *     sums (phase 2, Sec. 3.2.1, 4.2, 4.3), then each partition is sorted
+ *     (phase 3);
+ *   - every sorted S partition is merge-joined against all R runs, a search
+ *     locating where each run's relevant part starts (phase 4, Sec. 3.2.2).
+ * This is the paper's role-reversal orientation (Sec. 3.2 last paragraph,
+ * Sec. 5.4): the partitioned input is S, the run input is R.  The result does
+ * not depend on the roles.
+ *
+ * Result (Sec. 5.1's query, with the aggregate every payload flows into):
+ *   count    = |{(r, s) in R x S : r.key == s.key}|
+ *   checksum = sum over those pairs of (r.payload + s.payload), modulo 2^64
+ *   pairs    = optionally the pairs (r.payload, s.payload), in no particular order.
+ *
+ * Conventions for every entry point:
+ *  - Tuples are 16-byte {key, payload} records, 16-byte aligned, in DEVICE
+ *    memory unless the function says HOST.  R and S are read only.
+ *  - All work is enqueued on the plan's CUDA stream.  Functions that return
+ *    host values (counts, checksums, stats, views) synchronise that stream.
+ *  - Return value: MPSM_OK (0) or an MPSM_ERR_* code; nothing aborts or prints.
+ *    mpsm_strerror() names a code.  After MPSM_ERR_CUDA the plan must be
+ *    destroyed.
+ *  - A plan is not thread-safe; use one plan per host thread / stream.
+ */
+#ifndef MPSM_H
+#define MPSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { uint64_t key, payload; } mpsm_tuple_t;          /* 16 B */
+typedef struct { uint64_t r_payload, s_payload; } mpsm_pair_t;    /* 16 B */
+typedef struct { mpsm_pair_t* data; uint64_t capacity; } mpsm_pairs_t;
+typedef struct mpsm_plan mpsm_plan_t;
+
+enum {
+  MPSM_OK = 0,
+  MPSM_ERR_INVALID_ARG = 1,   /* null/misaligned pointer, size above the plan's maximum   */
+  MPSM_ERR_OOM = 2,           /* device allocation failed                                  */
+  MPSM_ERR_CUDA = 3,          /* a CUDA call failed                                        */
+  MPSM_ERR_CAPACITY = 4,      /* pair buffer too small; *out_count holds the needed size   */
+  MPSM_ERR_DEVICE = 5,        /* a kernel detected a violated invariant or gave up a wait  */
+  MPSM_ERR_STATE = 6          /* a phase entry point called before the phase it needs      */
+};
+
+enum { MPSM_SPLIT_HIST = 0, MPSM_SPLIT_LEARNED = 1 };
+enum { MPSM_SEARCH_BINARY = 0, MPSM_SEARCH_LEARNED = 1 };
+enum { MPSM_FLAG_TIMING = 1u };   /* record per-phase CUDA events (read by mpsm_plan_stats) */
+
+typedef struct {
+  uint32_t runs_r;         /* T_R, runs cut from R (Sec. 2.1 "T chunks"); 0 = automatic       */
+  uint32_t partitions_s;   /* P, partitions of S (at most 2^fine_bits); 0 = automatic        */
+  uint32_t fine_bits;      /* B, bits of the fine S histogram (Sec. 4.2), 1..12; 0 = 12      */
+  uint32_t radix_bits;     /* log2 of the largest sort fan-out per pass, 4..11; 0 = 11       */
+  uint32_t join_tile;      /* S tuples per join tile, 256..4096, multiple of 256; 0 = 4096   */
+  int32_t splitter_mode;   /* MPSM_SPLIT_*                                                   */
+  int32_t search_mode;     /* MPSM_SEARCH_*                                                  */
+  uint32_t flags;          /* MPSM_FLAG_*                                                    */
+  uint64_t seed;           /* initialisation seed of the learned model                      */
+  uint32_t reserved[6];    /* must be zero                                                   */
+} mpsm_options_t;
+
+/* Fills *opt with the defaults (all automatic, histogram splitters, binary search). */
+int mpsm_options_default(mpsm_options_t* opt);
+
+/* Creates a plan able to join up to max_nR R tuples with up to max_nS S tuples
+ * (for mpsm_join_batch: the totals over all jobs, and at most max_jobs jobs).
+ * The plan owns all scratch: about (max_nR + 2 max_nS) x 16 bytes plus small
+ * tables.  `stream` is a cudaStream_t (NULL = the legacy default stream) on the
+ * current device.  opt == NULL takes the defaults.  max_nR, max_nS < 2^32. */
+int mpsm_plan_create(mpsm_plan_t** plan, uint64_t max_nR, uint64_t max_nS, uint32_t max_jobs,
+                     const mpsm_options_t* opt, void* stream);
+
+/* Frees the plan and its scratch (synchronises its stream first). */
+void mpsm_plan_destroy(mpsm_plan_t* plan);
+
+/* The whole join (phases 1-4).  R: nR tuples, S: nS tuples, device memory.
+ * out_count / out_checksum: HOST pointers, written when the call returns.
+ * opt_pairs: NULL, or a DEVICE buffer of capacity pairs; when the result has
+ * more pairs than that, nothing is written to it, *out_count holds the required
+ * capacity and the call returns MPSM_ERR_CAPACITY.  nR == 0 or nS == 0 give 0, 0. */
+int mpsm_join(mpsm_plan_t* plan, const mpsm_tuple_t* R, uint64_t nR, const mpsm_tuple_t* S,
+              uint64_t nS, uint64_t* out_count, uint64_t* out_checksum, mpsm_pairs_t* opt_pairs);
+
+/* Same as mpsm_join with R and S in HOST memory (pinned memory copies fastest):
+ * the plan copies them to device staging buffers on its stream first. */
+int mpsm_join_host(mpsm_plan_t* plan, const mpsm_tuple_t* R_host, uint64_t nR,
+                   const mpsm_tuple_t* S_host, uint64_t nS, uint64_t* out_count,
+                   uint64_t* out_checksum);
+
+/* ---- phase entry points: mpsm_join == these five in order ---------------- */
+
+/* Phase 1 (Sec. 2.1, 3.2): R cut into T_R chunks [floor(j nR/T_R), floor((j+1) nR/T_R)),
+ * each sorted by key into a run, kept in plan scratch (see mpsm_plan_view). */
+int mpsm_sort_runs(mpsm_plan_t* plan, const mpsm_tuple_t* R, uint64_t nR);
+
+/* Phase 2 (Sec. 3.2.1, 4.1-4.3): fine radix histograms of S over R's key range
+ * (per S chunk = per worker), the run side's counts per fine bucket, the
+ * cost-balanced splitters (fine bucket -> partition), and the prefix sums that
+ * give every chunk its write position in every partition.  Needs phase 1. */
+int mpsm_splitters(mpsm_plan_t* plan, const mpsm_tuple_t* S, uint64_t nS);
+
+/* Phase 2, scatter (Sec. 4.3): every S tuple inside R's key range written to its
+ * partition at its chunk's precomputed position; S tuples outside R's key range
+ * cannot match and are dropped.  Needs mpsm_splitters. */
+int mpsm_scatter(mpsm_plan_t* plan);
+
+/* Phase 3: each S partition sorted by key.  Needs mpsm_scatter. */
+int mpsm_sort_partitions(mpsm_plan_t* plan);
+
+/* Phase 4, search (Sec. 3.2.2): for every S tile and R run, the run's window
+ * [first key >= tile's first key, first key > tile's last key). Needs phase 3. */
+int mpsm_search(mpsm_plan_t* plan);
+
+/* Phase 4, merge join of every S tile against every run window; writes the
+ * result like mpsm_join.  Needs mpsm_search. */
+int mpsm_merge_join(mpsm_plan_t* plan, uint64_t* out_count, uint64_t* out_checksum,
+                    mpsm_pairs_t* opt_pairs);
+
+/* ---- batched joins -------------------------------------------------------- */
+
+typedef struct {
+  const mpsm_tuple_t* R; uint64_t nR;   /* device */
+  const mpsm_tuple_t* S; uint64_t nS;   /* device */
+} mpsm_job_t;
+
+/* njobs independent joins in one launch sequence: all jobs' runs, partitions
+ * and tiles are processed together by the same kernels, and the sequence is
+ * captured once into a CUDA graph that later calls with the same job sizes
+ * replay.  jobs: HOST array.  out_counts / out_checksums: HOST arrays of njobs. */
+int mpsm_join_batch(mpsm_plan_t* plan, const mpsm_job_t* jobs, uint32_t njobs,
+                    uint64_t* out_counts, uint64_t* out_checksums);
+
+/* ---- introspection --------------------------------------------------------- */
+
+typedef struct {
+  float ms_sort_runs, ms_splitters, ms_scatter, ms_sort_partitions, ms_search, ms_join, ms_learn;
+  float ms_total;               /* per-phase device time of the last call (MPSM_FLAG_TIMING) */
+  uint32_t runs_r;              /* T_R used                                                  */
+  uint32_t partitions_s;        /* P used                                                    */
+  uint32_t nfine, fine_shift;   /* fine histogram geometry                                   */
+  uint64_t s_kept;              /* S tuples inside R's key range                             */
+  uint64_t part_max;            /* largest partition                                         */
+  double imbalance;             /* largest / mean partition size                             */
+  double mean_window;           /* mean R tuples per (tile, run) window                      */
+  uint64_t tiles;               /* S join tiles                                              */
+  uint32_t levels_r, levels_s;  /* radix levels of phase 1 / phase 3 before the final sort   */
+  uint64_t segments_r, segments_s; /* final in-shared-memory sort segments                   */
+} mpsm_stats_t;
+
+/* Statistics of the last join (job 0 of a batch).  Synchronises. */
+int mpsm_plan_stats(mpsm_plan_t* plan, mpsm_stats_t* stats);
+
+typedef struct {
+  const mpsm_tuple_t* r_runs;      /* device: nR tuples, the T_R sorted runs back to back      */
+  const uint64_t* run_offsets;     /* device: T_R + 1 run boundaries                            */
+  uint32_t runs_r;
+  uint64_t key_min, key_max;       /* R's key range (valid when nR > 0)                         */
+  uint32_t nfine, fine_shift;      /* fine bucket b = (key - key_min) >> fine_shift, b < nfine  */
+  const uint64_t* fine_s;          /* device: nfine S counts                                    */
+  const uint64_t* fine_r;          /* device: nfine R counts                                    */
+  const uint32_t* splitters;       /* device: nfine entries, fine bucket -> partition            */
+  uint32_t partitions_s;           /* P used                                                    */
+  uint32_t s_chunks;               /* S chunks (workers) of phase 2                              */
+  const uint64_t* s_chunk_offsets; /* device: s_chunks + 1 chunk boundaries in S                */
+  const uint32_t* chunk_offsets;   /* device: s_chunks x P; ps_i[p], the s_buffer position where  */
+                                   /* chunk i writes its first tuple of partition p (Sec. 3.2.1)  */
+  const uint64_t* part_offsets;    /* device: P + 1 partition starts in s_buffer                 */
+  const mpsm_tuple_t* s_buffer;    /* device: S after the last phase run (partitioned / sorted)  */
+  uint64_t s_kept;
+  uint64_t tiles;                  /* S tiles of phase 4                                         */
+  uint32_t join_tile;              /* S tuples per tile (tile t = [t*join_tile, ...) of s_buffer) */
+  const uint32_t* windows;         /* device: tiles x T_R x 2 (start, end) relative to the run    */
+} mpsm_view_t;
+
+/* Device pointers into the plan's scratch after the last phase entry point
+ * (valid until the next call on the plan).  Synchronises. */
+int mpsm_plan_view(mpsm_plan_t* plan, mpsm_view_t* view);
+
+const char* mpsm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPSM_H */

@@ -7,9 +7,9 @@
  * only module both sides use is the input generator (gen/), which holds no join
  * arithmetic.
  *
- * What the method computes (Sec. 5.1, the benchmark query; Sec. 2, "MPSM is a
- * join, exact, with no final merge"): the equi-join of R and S on the 64-bit
- * key.  From the multiset of matching pairs {(r, s) : r.key == s.key} we report
+ * What the method computes (Sec. 5.1, the benchmark query; Sec. 2: an exact
+ * join of independently sorted runs, without a final merge): the equi-join of R
+ * and S on the 64-bit key.  From the multiset of matching pairs {(r, s) : r.key == s.key} we report
  *   count    = number of pairs,
  *   checksum = sum over pairs of (r.payload + s.payload), modulo 2^64,
  *   pairs    = optionally the pairs themselves as (r.payload, s.payload).
@@ -48,7 +48,7 @@ static bool by_key(const otuple& a, const otuple& b) { return a.key < b.key; }
 /* ------------------------------------------------------------ the join */
 
 /* Equi-join R and S (Sec. 5.1).  If pairs != NULL, writes up to cap pairs in
- * lexicographic (r_payload, s_payload) order; *npairs always receives count. */
+ * lexicographic (r_payload, s_payload) order; *count is always the full count. */
 OEXPORT int oracle_join(const otuple* R, uint64_t nR, const otuple* S, uint64_t nS,
                         uint64_t* count, uint64_t* checksum, opair* pairs, uint64_t cap) {
   std::vector<otuple> r(R, R + nR), s(S, S + nS);
@@ -208,19 +208,28 @@ OEXPORT int oracle_run_counts(const otuple* Rs, const uint64_t* run_off, uint32_
   return 0;
 }
 
-/* floor(log2(n) * 2^16) for n >= 1 (0 for n <= 1), by the classic bit-by-bit
- * method: normalise n to x in [1, 2), then square 16 times, each time taking
- * one fractional bit (x >= 2 -> bit 1, halve). */
-OEXPORT uint64_t oracle_log2_q16(uint64_t n) {
-  if (n <= 1) return 0;
-  const uint32_t k = bitlen64(n) - 1;
-  uint64_t x = (k <= 31) ? (n << (31 - k)) : (n >> (k - 31)); /* Q31 in [2^31, 2^32) */
+/* The bit-by-bit binary logarithm: for 1 <= m < 2^17, floor(log2(m) * 2^16),
+ * by normalising m to x in [1, 2) and squaring 16 times, each time taking one
+ * fractional bit (x >= 2 -> bit 1, halve). */
+static uint64_t log2_q16_small(uint64_t m) {
+  const uint32_t k = bitlen64(m) - 1;
+  uint64_t x = m << (31 - k); /* Q31 in [2^31, 2^32) */
   uint64_t r = (uint64_t)k << 16;
   for (int i = 15; i >= 0; --i) {
     x = (x * x) >> 31;
     if (x >= (1ull << 32)) { x >>= 1; r |= 1ull << i; }
   }
   return r;
+}
+
+/* log2(n) in Q16 for the cost model: the logarithm of n's leading 17 significant
+ * bits (exact below 2^17, at most 1.5 units low above), 0 for n <= 1. */
+OEXPORT uint64_t oracle_log2_q16(uint64_t n) {
+  if (n <= 1) return 0;
+  const uint32_t k = bitlen64(n) - 1;
+  if (k <= 16) return log2_q16_small(n);
+  const uint32_t s = k - 16;
+  return log2_q16_small(n >> s) + ((uint64_t)s << 16);
 }
 
 /* split-relevant cost of a partition (Sec. 4.3), in units of 2^-16 tuples:

@@ -1,0 +1,890 @@
+// api.cu -- libmpsm: plan management, phase orchestration and the C ABI (include/mpsm.h).
+//
+// Every phase is a fixed sequence of kernel launches on the plan's stream; work
+// lists (segments, chunks, tiles) live on the device, so the host never needs
+// the data-dependent sizes.  The host only reads back the number of segments
+// still too big after a radix pass (one 4-byte copy per pass) to stop early;
+// the batched path replaces that check by a fixed number of passes so that the
+// whole sequence can be captured into a CUDA graph.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "mpsm.h"
+#include "mpsm_internal.cuh"
+#include "mpsm_launch.h"
+
+using namespace mpsm;
+
+#define MPSM_API extern "C" __attribute__((visibility("default")))
+
+namespace {
+
+constexpr u64 CH_RADIX = 131072;  // tuples per chunk in the sort passes
+// counters in d_cnt
+enum { C_BIG0 = 0, C_BIG1 = 1, C_FIN = 2, C_WORK = 3, C_ERR = 4, C_SPLIT = 5, C_NUM = 8 };
+// totals in d_tot
+enum { T_LEVEL = 0, T_FINE = 3, T_SPLIT = 6, T_TILES = 9, T_PAIRS = 12, T_NUM = 16 };
+enum Stage { ST_NONE = 0, ST_RUNS, ST_SPLIT, ST_SCATTER, ST_SORTED, ST_SEARCH, ST_DONE };
+enum { EV_START = 0, EV_RUNS, EV_SPLIT, EV_SCATTER, EV_SORTS, EV_SEARCH, EV_JOIN, EV_NUM };
+
+struct Jobh {
+  const Tuple* R;
+  const Tuple* S;
+  u64 nR, nS;
+};
+
+}  // namespace
+
+struct mpsm_plan {
+  int device = 0, nsm = 0;
+  cudaStream_t st = nullptr;
+  mpsm_options_t opt{};
+  u64 max_nR = 0, max_nS = 0;
+  u32 max_jobs = 1;
+  // data buffers
+  Tuple *xr = nullptr, *xs = nullptr, *y = nullptr;
+  Tuple *stage_r = nullptr, *stage_s = nullptr;
+  // job / run tables
+  Job *d_jobs = nullptr, *h_jobs = nullptr;
+  Run *d_runs = nullptr, *h_runs = nullptr;
+  u32 runs_cap = 0;
+  // work lists
+  Seg *d_split = nullptr, *h_segs = nullptr;
+  Seg *d_big[2] = {nullptr, nullptr}, *d_fin = nullptr;
+  u32 big_cap = 0, fin_cap = 0, hseg_cap = 0;
+  u32 *d_cnt = nullptr, *h_cnt = nullptr;
+  // per-pass arrays
+  LSeg *d_ls = nullptr, *d_ls2 = nullptr;
+  u64* d_tot = nullptr;
+  u32 *d_hist_a = nullptr, *d_hist_b = nullptr;
+  u64 hist_a_cap = 0, hist_b_cap = 0;
+  u64 *d_bmin = nullptr, *d_bmax = nullptr;
+  u64 bucket_cap = 0;
+  // splitters
+  u64 *d_fine_s = nullptr, *d_fine_min = nullptr, *d_fine_max = nullptr, *d_fine_r = nullptr, *d_rc = nullptr;
+  u32 *d_sp = nullptr, *d_fstart = nullptr;
+  u64* d_part_off = nullptr;
+  u16* d_log2 = nullptr;  // Q16 fractional log2 table of the splitter cost
+  // join
+  u32* d_win = nullptr;
+  u64 win_cap = 0;
+  u64 *d_tile_cnt = nullptr, *d_tile_out = nullptr;
+  u64 tile_cap = 0;
+  u64* d_chunk_off = nullptr;
+  u64 chunk_off_cap = 0;
+  u64* h_scalar = nullptr;  // pinned scratch for small reads
+  // state of the current call
+  int stage = ST_NONE;
+  u32 njobs = 0;
+  u64 ch_s = 0;
+  u32 tile = 4096;
+  u32 levels_r = 0, levels_s = 0;
+  u64 segs_r = 0, segs_s = 0;
+  bool graph_mode = false;
+  bool own_stream = false;
+  cudaEvent_t ev[EV_NUM] = {};
+  bool timing = false;
+  // batched graph
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<u64> gsig;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? MPSM_OK : MPSM_ERR_CUDA; }
+
+#define CK(x)                                          \
+  do {                                                 \
+    cudaError_t e_ = (x);                              \
+    if (e_ != cudaSuccess) {                           \
+      return e_ == cudaErrorMemoryAllocation ? MPSM_ERR_OOM : MPSM_ERR_CUDA; \
+    }                                                  \
+  } while (0)
+
+template <typename T>
+int dalloc(T** p, u64 n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return MPSM_ERR_OOM;
+  }
+  return MPSM_OK;
+}
+
+template <typename T>
+int halloc(T** p, u64 n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMallocHost((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return MPSM_ERR_OOM;
+  }
+  return MPSM_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <typename T>
+void hfree(T*& p) {
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+}
+
+u64 chunk_start(u64 n, u64 T, u64 j) { return (u64)(((unsigned __int128)n * j) / T); }
+
+u32 auto_runs(u64 nR) {
+  // runs of at most ~2048 sort buckets x 6K tuples finish in one radix pass + the SMEM sort;
+  // small inputs keep the paper's T = 32 while each run still spans a few SMEM tiles
+  const u64 per = 2048ull * 6144ull;
+  u64 t = (nR + per - 1) / per;
+  const u64 small = std::min<u64>(32, (nR + NMAX - 1) / NMAX);
+  t = std::max<u64>(t, small);
+  return (u32)std::min<u64>(std::max<u64>(t, 1), RUNS_MAX);
+}
+
+u32 auto_parts(u64 nS) {
+  u64 p = 32;
+  while (p < P_MAX && p * 1536ull * 1024ull < nS) p <<= 1;
+  return (u32)p;
+}
+
+u32 runs_for(const mpsm_plan* p, u64 nR) {
+  u32 t = p->opt.runs_r ? p->opt.runs_r : auto_runs(nR);
+  if (nR && t > nR) t = (u32)nR;
+  return std::max<u32>(1, std::min<u32>(t, RUNS_MAX));
+}
+
+Bufs bufs(const mpsm_plan* p) { return Bufs{p->xr, p->xs, p->y}; }
+
+void record(mpsm_plan* p, int i) {
+  if (p->timing) cudaEventRecord(p->ev[i], p->st);
+}
+
+// ---------------------------------------------------------------- per-call setup
+int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
+  if (njobs == 0 || njobs > p->max_jobs) return MPSM_ERR_INVALID_ARG;
+  u64 totR = 0, totS = 0, totRuns = 0, win_need = 0, tiles_need = 0;
+  std::vector<u32> T(njobs);
+  for (u32 i = 0; i < njobs; ++i) {
+    totR += jobs[i].nR;
+    totS += jobs[i].nS;
+    T[i] = runs_for(p, jobs[i].nR);
+    totRuns += T[i];
+    const u64 nt = (jobs[i].nS + p->tile - 1) / p->tile;
+    tiles_need += nt;
+    win_need += nt * T[i];
+  }
+  if (totR > p->max_nR || totS > p->max_nS) return MPSM_ERR_INVALID_ARG;
+  if (totRuns > p->runs_cap) return MPSM_ERR_INVALID_ARG;
+  // grow the window / tile arrays if this call needs more
+  if (win_need * 2 > p->win_cap) {
+    dfree(p->d_win);
+    p->win_cap = std::max<u64>(win_need * 2, 1024);
+    if (dalloc(&p->d_win, p->win_cap)) return MPSM_ERR_OOM;
+  }
+  if (tiles_need + njobs > p->tile_cap) {
+    dfree(p->d_tile_cnt);
+    dfree(p->d_tile_out);
+    p->tile_cap = tiles_need + njobs + 1024;
+    if (dalloc(&p->d_tile_cnt, p->tile_cap) || dalloc(&p->d_tile_out, p->tile_cap)) return MPSM_ERR_OOM;
+  }
+  // S chunk (worker) size: about 4 chunks per SM in total
+  u64 ch = (totS + 4ull * p->nsm - 1) / (4ull * p->nsm);
+  ch = std::max<u64>(ch, 65536);
+  ch = (ch + 4095) / 4096 * 4096;
+  p->ch_s = ch;
+  // host tables
+  u64 rb = 0, sb = 0;
+  u32 rbase = 0;
+  u32 nbig = 0, nfin = 0;
+  std::vector<Seg> big, fin, split;
+  for (u32 i = 0; i < njobs; ++i) {
+    Job J{};
+    J.R = jobs[i].R;
+    J.S = jobs[i].S;
+    J.nR = jobs[i].nR;
+    J.nS = jobs[i].nS;
+    J.r_base = rb;
+    J.s_base = sb;
+    J.runs = T[i];
+    J.run_base = rbase;
+    J.parts_req = p->opt.partitions_s ? std::min<u32>(p->opt.partitions_s, P_MAX) : auto_parts(jobs[i].nS);
+    J.part_base = i * (P_MAX + 1);
+    J.fine_bits = p->opt.fine_bits ? p->opt.fine_bits : 12u;
+    J.fine_base = i * FINE_MAX;
+    p->h_jobs[i] = J;
+    for (u32 j = 0; j < T[i]; ++j) {
+      const u64 a = chunk_start(J.nR, T[i], j), b = chunk_start(J.nR, T[i], j + 1);
+      p->h_runs[rbase + j] = Run{rb + a, b - a};
+      if (b - a > NMAX) big.push_back(Seg{rb + a, b - a, 0, ~0ull, i, W_RIN});
+      else if (b > a) fin.push_back(Seg{rb + a, b - a, 0, ~0ull, i, W_RIN});
+    }
+    split.push_back(Seg{sb, J.nS, 0, 0, i, W_SIN});
+    rb += J.nR;
+    sb += J.nS;
+    rbase += T[i];
+  }
+  nbig = (u32)big.size();
+  nfin = (u32)fin.size();
+  if (nbig > p->big_cap || nfin > p->fin_cap) return MPSM_ERR_INVALID_ARG;
+  const u64 need = (u64)nbig + nfin + njobs;
+  if (need > p->hseg_cap) {
+    hfree(p->h_segs);
+    p->hseg_cap = (u32)(need + 1024);
+    if (halloc(&p->h_segs, p->hseg_cap)) return MPSM_ERR_OOM;
+  }
+  std::copy(big.begin(), big.end(), p->h_segs);
+  std::copy(fin.begin(), fin.end(), p->h_segs + nbig);
+  std::copy(split.begin(), split.end(), p->h_segs + nbig + nfin);
+  p->njobs = njobs;
+  for (int i = 0; i < C_NUM; ++i) p->h_cnt[i] = 0;
+  p->h_cnt[C_BIG0] = nbig;
+  p->h_cnt[C_FIN] = nfin;
+  p->h_cnt[C_SPLIT] = njobs;
+  CK(cudaMemcpyAsync(p->d_jobs, p->h_jobs, njobs * sizeof(Job), cudaMemcpyHostToDevice, p->st));
+  CK(cudaMemcpyAsync(p->d_runs, p->h_runs, rbase * sizeof(Run), cudaMemcpyHostToDevice, p->st));
+  if (nbig) CK(cudaMemcpyAsync(p->d_big[0], p->h_segs, nbig * sizeof(Seg), cudaMemcpyHostToDevice, p->st));
+  if (nfin) CK(cudaMemcpyAsync(p->d_fin, p->h_segs + nbig, nfin * sizeof(Seg), cudaMemcpyHostToDevice, p->st));
+  CK(cudaMemcpyAsync(p->d_split, p->h_segs + nbig + nfin, njobs * sizeof(Seg), cudaMemcpyHostToDevice, p->st));
+  CK(cudaMemcpyAsync(p->d_cnt, p->h_cnt, C_NUM * sizeof(u32), cudaMemcpyHostToDevice, p->st));
+  // the host copies above read pinned memory asynchronously; keep it stable until they ran
+  CK(cudaStreamSynchronize(p->st));
+  p->levels_r = p->levels_s = 0;
+  return MPSM_OK;
+}
+
+// radix passes over the big-segment list until every segment is final
+int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels) {
+  u32 cur = 0, src = first_src;
+  u32 done = 0;
+  for (u32 lvl = 0; lvl < MAX_LEVELS; ++lvl) {
+    if (!p->graph_mode) {
+      CK(cudaMemcpyAsync(&p->h_cnt[C_BIG0 + cur], &p->d_cnt[C_BIG0 + cur], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
+      CK(cudaStreamSynchronize(p->st));
+      if (p->h_cnt[C_BIG0 + cur] == 0) break;
+    }
+    const u32 dst = (src == W_Y) ? final_where : (u32)W_Y;
+    CK(cudaMemsetAsync(&p->d_cnt[C_BIG0 + (cur ^ 1)], 0, sizeof(u32), p->st));
+    u64* tot = p->d_tot + T_LEVEL;
+    const u32 rb = p->opt.radix_bits ? p->opt.radix_bits : 11u;
+    launch_level_plan(p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->big_cap, p->d_ls, tot, MODE_RADIX, CH_RADIX, rb,
+                      p->d_jobs, p->hist_a_cap, p->bucket_cap, &p->d_cnt[C_ERR], p->st);
+    launch_init_buckets(p->d_bmin, p->d_bmax, nullptr, tot, p->st, p->nsm);
+    launch_hist(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs, src,
+                p->d_hist_a, p->d_bmin, p->d_bmax, nullptr, p->st, p->nsm);
+    launch_scan(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, p->d_hist_a, p->d_bmin, p->d_bmax,
+                nullptr, p->d_big[cur ^ 1], &p->d_cnt[C_BIG0 + (cur ^ 1)], p->big_cap, p->d_fin, &p->d_cnt[C_FIN],
+                p->fin_cap, dst, p->d_jobs, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm);
+    launch_scatter(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs,
+                   src, dst, p->d_hist_a, nullptr, p->st, p->nsm);
+    CK(cudaGetLastError());
+    src = dst;
+    cur ^= 1;
+    ++done;
+  }
+  if (p->graph_mode) {
+    launch_check_empty(&p->d_cnt[C_BIG0 + cur], &p->d_cnt[C_ERR], DERR_LEVELS, p->st);
+  } else if (done == MAX_LEVELS) {
+    CK(cudaMemcpyAsync(&p->h_cnt[C_BIG0 + cur], &p->d_cnt[C_BIG0 + cur], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    if (p->h_cnt[C_BIG0 + cur]) return MPSM_ERR_DEVICE;
+  }
+  // the finished list must be list 0 for the next user
+  if (cur != 0) {
+    CK(cudaMemcpyAsync(&p->d_cnt[C_BIG0], &p->d_cnt[C_BIG0 + cur], sizeof(u32), cudaMemcpyDeviceToDevice, p->st));
+  }
+  *levels = done;
+  return MPSM_OK;
+}
+
+int final_sort(mpsm_plan* p, u32 dst_where) {
+  CK(cudaMemsetAsync(&p->d_cnt[C_WORK], 0, sizeof(u32), p->st));
+  launch_seg_sort(p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, &p->d_cnt[C_WORK], bufs(p), p->d_jobs, dst_where,
+                  &p->d_cnt[C_ERR], p->st, p->nsm);
+  CK(cudaGetLastError());
+  return MPSM_OK;
+}
+
+// ---------------------------------------------------------------- phases
+int phase_runs(mpsm_plan* p) {
+  record(p, EV_START);
+  CK(cudaMemsetAsync(&p->d_cnt[C_ERR], 0, sizeof(u32), p->st));
+  launch_sample_bounds(p->d_big[0], &p->d_cnt[C_BIG0], p->h_cnt[C_BIG0] ? p->big_cap : 0, bufs(p), p->d_jobs, p->st);
+  int rc = run_levels(p, W_RIN, W_XR, &p->levels_r);
+  if (rc) return rc;
+  rc = final_sort(p, W_XR);
+  if (rc) return rc;
+  launch_run_bounds(p->d_jobs, p->njobs, p->d_runs, p->xr, p->st);
+  CK(cudaGetLastError());
+  record(p, EV_RUNS);
+  p->stage = ST_RUNS;
+  return MPSM_OK;
+}
+
+int phase_splitters(mpsm_plan* p) {
+  const u32 nj = p->njobs;
+  CK(cudaMemsetAsync(p->d_rc, 0, (u64)nj * (FINE_MAX + 1) * sizeof(u64), p->st));
+  CK(cudaMemsetAsync(p->d_fine_s, 0, (u64)nj * FINE_MAX * sizeof(u64), p->st));
+  CK(cudaMemsetAsync(p->d_fine_min, 0xFF, (u64)nj * FINE_MAX * sizeof(u64), p->st));
+  CK(cudaMemsetAsync(p->d_fine_max, 0, (u64)nj * FINE_MAX * sizeof(u64), p->st));
+  u64* tf = p->d_tot + T_FINE;
+  u64* ts = p->d_tot + T_SPLIT;
+  launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls, tf, MODE_FINE, p->ch_s, 11, p->d_jobs,
+                    p->hist_b_cap, ~0ull, &p->d_cnt[C_ERR], p->st);
+  launch_hist(MODE_FINE, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls, tf, p->ch_s, bufs(p), p->d_jobs, W_SIN,
+              p->d_hist_b, p->d_fine_min, p->d_fine_max, p->d_fine_s, p->st, p->nsm);
+  launch_run_cdf(p->d_jobs, nj, p->d_runs, p->xr, p->d_rc, p->st);
+  launch_splitters(p->d_jobs, nj, p->d_fine_s, p->d_rc, p->d_fine_r, p->d_sp, p->d_fstart, p->d_log2, p->st);
+  launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls2, ts, MODE_SPLIT, p->ch_s, 11, p->d_jobs,
+                    p->hist_a_cap, ~0ull, &p->d_cnt[C_ERR], p->st);
+  launch_fold(p->d_split, &p->d_cnt[C_SPLIT], p->d_ls, p->d_ls2, tf, p->d_jobs, p->d_hist_b, p->d_fstart,
+              p->d_hist_a, p->st, p->nsm);
+  CK(cudaMemsetAsync(&p->d_cnt[C_BIG0], 0, sizeof(u32), p->st));
+  CK(cudaMemsetAsync(&p->d_cnt[C_FIN], 0, sizeof(u32), p->st));
+  launch_scan(MODE_SPLIT, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_hist_a, p->d_fine_min, p->d_fine_max,
+              p->d_fstart, p->d_big[0], &p->d_cnt[C_BIG0], p->big_cap, p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, W_XS,
+              p->d_jobs, p->d_part_off, &p->d_cnt[C_ERR], p->st, p->nsm);
+  CK(cudaGetLastError());
+  record(p, EV_SPLIT);
+  p->stage = ST_SPLIT;
+  return MPSM_OK;
+}
+
+int phase_scatter(mpsm_plan* p) {
+  launch_scatter(MODE_SPLIT, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_tot + T_SPLIT, p->ch_s, bufs(p),
+                 p->d_jobs, W_SIN, W_XS, p->d_hist_a, p->d_sp, p->st, p->nsm);
+  CK(cudaGetLastError());
+  record(p, EV_SCATTER);
+  p->stage = ST_SCATTER;
+  return MPSM_OK;
+}
+
+int phase_sort_parts(mpsm_plan* p) {
+  int rc = run_levels(p, W_XS, W_XS, &p->levels_s);
+  if (rc) return rc;
+  rc = final_sort(p, W_XS);
+  if (rc) return rc;
+  record(p, EV_SORTS);
+  p->stage = ST_SORTED;
+  return MPSM_OK;
+}
+
+int phase_search(mpsm_plan* p) {
+  launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, p->st);
+  launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win, p->st, p->nsm);
+  CK(cudaGetLastError());
+  record(p, EV_SEARCH);
+  p->stage = ST_SEARCH;
+  return MPSM_OK;
+}
+
+int read_err(mpsm_plan* p) {
+  CK(cudaMemcpyAsync(&p->h_cnt[C_ERR], &p->d_cnt[C_ERR], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  return p->h_cnt[C_ERR] ? MPSM_ERR_DEVICE : MPSM_OK;
+}
+
+int phase_join(mpsm_plan* p, uint64_t* out_count, uint64_t* out_checksum, mpsm_pairs_t* pairs) {
+  const u64* tot = p->d_tot + T_TILES;
+  if (pairs) {
+    launch_join(JOIN_COUNT, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, tot, p->d_win, p->d_tile_cnt,
+                nullptr, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm);
+    launch_pair_offsets(p->d_jobs, p->njobs, tot, p->d_tile_cnt, p->d_tile_out, p->d_tot + T_PAIRS, p->st);
+    CK(cudaMemcpyAsync(p->h_scalar, p->d_tot + T_PAIRS, sizeof(u64), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    const u64 need = p->h_scalar[0];
+    if (need <= pairs->capacity && need > 0) {
+      if (!pairs->data) return MPSM_ERR_INVALID_ARG;
+      launch_join(JOIN_WRITE, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, tot, p->d_win, p->d_tile_cnt,
+                  p->d_tile_out, reinterpret_cast<Tuple*>(pairs->data), &p->d_cnt[C_ERR], p->st, p->nsm);
+    }
+  } else {
+    launch_join(JOIN_AGG, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, tot, p->d_win, nullptr, nullptr,
+                nullptr, &p->d_cnt[C_ERR], p->st, p->nsm);
+  }
+  CK(cudaGetLastError());
+  record(p, EV_JOIN);
+  CK(cudaMemcpyAsync(p->h_jobs, p->d_jobs, p->njobs * sizeof(Job), cudaMemcpyDeviceToHost, p->st));
+  int rc = read_err(p);
+  p->stage = ST_DONE;
+  if (rc) return rc;
+  if (out_count) *out_count = p->h_jobs[0].count;
+  if (out_checksum) *out_checksum = p->h_jobs[0].checksum;
+  if (pairs && p->h_jobs[0].count > pairs->capacity) return MPSM_ERR_CAPACITY;
+  return MPSM_OK;
+}
+
+bool aligned16(const void* q) { return ((uintptr_t)q & 15u) == 0; }
+
+int check_inputs(const mpsm_plan* p, const mpsm_tuple_t* R, u64 nR, const mpsm_tuple_t* S, u64 nS) {
+  if (!p) return MPSM_ERR_INVALID_ARG;
+  if ((nR && !R) || (nS && !S)) return MPSM_ERR_INVALID_ARG;
+  if (!aligned16(R) || !aligned16(S)) return MPSM_ERR_INVALID_ARG;
+  if (nR > p->max_nR || nS > p->max_nS) return MPSM_ERR_INVALID_ARG;
+  return MPSM_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+MPSM_API int mpsm_options_default(mpsm_options_t* opt) {
+  if (!opt) return MPSM_ERR_INVALID_ARG;
+  memset(opt, 0, sizeof(*opt));
+  opt->splitter_mode = MPSM_SPLIT_HIST;
+  opt->search_mode = MPSM_SEARCH_BINARY;
+  opt->seed = 20120145ull;
+  return MPSM_OK;
+}
+
+MPSM_API void mpsm_plan_destroy(mpsm_plan_t* p) {
+  if (!p) return;
+  if (p->st) cudaStreamSynchronize(p->st);
+  dfree(p->xr);
+  dfree(p->xs);
+  dfree(p->y);
+  dfree(p->stage_r);
+  dfree(p->stage_s);
+  dfree(p->d_jobs);
+  hfree(p->h_jobs);
+  dfree(p->d_runs);
+  hfree(p->h_runs);
+  dfree(p->d_split);
+  hfree(p->h_segs);
+  dfree(p->d_big[0]);
+  dfree(p->d_big[1]);
+  dfree(p->d_fin);
+  dfree(p->d_cnt);
+  hfree(p->h_cnt);
+  dfree(p->d_ls);
+  dfree(p->d_ls2);
+  dfree(p->d_tot);
+  dfree(p->d_hist_a);
+  dfree(p->d_hist_b);
+  dfree(p->d_bmin);
+  dfree(p->d_bmax);
+  dfree(p->d_fine_s);
+  dfree(p->d_fine_min);
+  dfree(p->d_fine_max);
+  dfree(p->d_fine_r);
+  dfree(p->d_rc);
+  dfree(p->d_sp);
+  dfree(p->d_fstart);
+  dfree(p->d_part_off);
+  dfree(p->d_log2);
+  dfree(p->d_win);
+  dfree(p->d_tile_cnt);
+  dfree(p->d_tile_out);
+  dfree(p->d_chunk_off);
+  hfree(p->h_scalar);
+  for (auto& e : p->ev)
+    if (e) cudaEventDestroy(e);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->own_stream && p->st) cudaStreamDestroy(p->st);
+  delete p;
+}
+
+MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_nS, uint32_t max_jobs,
+                              const mpsm_options_t* opt, void* stream) {
+  if (!out) return MPSM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (max_nR >= (1ull << 32) || max_nS >= (1ull << 32)) return MPSM_ERR_INVALID_ARG;
+  if (max_jobs == 0) max_jobs = 1;
+  mpsm_options_t o;
+  if (opt) {
+    o = *opt;
+    for (int i = 0; i < 6; ++i)
+      if (o.reserved[i]) return MPSM_ERR_INVALID_ARG;
+  } else {
+    mpsm_options_default(&o);
+  }
+  if (o.fine_bits > 12 || (o.radix_bits && (o.radix_bits < 4 || o.radix_bits > 11))) return MPSM_ERR_INVALID_ARG;
+  if (o.partitions_s > P_MAX || o.runs_r > RUNS_MAX) return MPSM_ERR_INVALID_ARG;
+  if (o.join_tile && (o.join_tile < 256 || o.join_tile > TILE_MAX || o.join_tile % 256)) return MPSM_ERR_INVALID_ARG;
+  if (o.splitter_mode != MPSM_SPLIT_HIST && o.splitter_mode != MPSM_SPLIT_LEARNED) return MPSM_ERR_INVALID_ARG;
+  if (o.search_mode != MPSM_SEARCH_BINARY && o.search_mode != MPSM_SEARCH_LEARNED) return MPSM_ERR_INVALID_ARG;
+  mpsm_plan* p = new (std::nothrow) mpsm_plan();
+  if (!p) return MPSM_ERR_OOM;
+  p->opt = o;
+  p->st = (cudaStream_t)stream;
+  p->max_nR = max_nR;
+  p->max_nS = max_nS;
+  p->max_jobs = max_jobs;
+  p->tile = o.join_tile ? o.join_tile : TILE_MAX;
+  p->timing = (o.flags & MPSM_FLAG_TIMING) != 0;
+  int rc = MPSM_OK;
+#define TRY(x)                 \
+  do {                         \
+    rc = (x);                  \
+    if (rc) {                  \
+      mpsm_plan_destroy(p);    \
+      return rc;               \
+    }                          \
+  } while (0)
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return MPSM_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
+  if (p->nsm <= 0) p->nsm = 1;
+  if (!p->st) {  // a stream of our own, synchronising with the legacy default stream like the caller's work
+    if (cudaStreamCreate(&p->st) != cudaSuccess) {
+      cudaGetLastError();
+      delete p;
+      return MPSM_ERR_CUDA;
+    }
+    p->own_stream = true;
+  }
+  init_attrs_pass();
+  init_attrs_split();
+  init_attrs_join();
+  const u64 nside = std::max(max_nR, max_nS);
+  TRY(dalloc(&p->xr, max_nR));
+  TRY(dalloc(&p->xs, max_nS));
+  TRY(dalloc(&p->y, nside));
+  p->runs_cap = max_jobs * RUNS_MAX;
+  TRY(dalloc(&p->d_jobs, max_jobs));
+  TRY(halloc(&p->h_jobs, max_jobs));
+  TRY(dalloc(&p->d_runs, p->runs_cap));
+  TRY(halloc(&p->h_runs, p->runs_cap));
+  TRY(dalloc(&p->d_split, max_jobs));
+  p->big_cap = (u32)(nside / NMAX + p->runs_cap + 1024);
+  p->fin_cap = (u32)(nside / 256 + 65536 + p->runs_cap);
+  TRY(dalloc(&p->d_big[0], p->big_cap));
+  TRY(dalloc(&p->d_big[1], p->big_cap));
+  TRY(dalloc(&p->d_fin, p->fin_cap));
+  TRY(dalloc(&p->d_cnt, C_NUM));
+  TRY(halloc(&p->h_cnt, C_NUM));
+  TRY(dalloc(&p->d_ls, std::max<u64>(p->big_cap, max_jobs)));
+  TRY(dalloc(&p->d_ls2, max_jobs));
+  TRY(dalloc(&p->d_tot, T_NUM));
+  const u64 s_chunks = 4ull * p->nsm + 2ull * max_jobs + 16;
+  p->hist_a_cap = std::max<u64>(nside / 32 + nside / 400 + (1u << 20), s_chunks * P_MAX);
+  p->hist_b_cap = s_chunks * FINE_MAX;
+  TRY(dalloc(&p->d_hist_a, p->hist_a_cap));
+  TRY(dalloc(&p->d_hist_b, p->hist_b_cap));
+  p->bucket_cap = nside / 400 + 65536 + (u64)max_jobs * 64;
+  TRY(dalloc(&p->d_bmin, p->bucket_cap));
+  TRY(dalloc(&p->d_bmax, p->bucket_cap));
+  const u64 nf = (u64)max_jobs * FINE_MAX;
+  TRY(dalloc(&p->d_fine_s, nf));
+  TRY(dalloc(&p->d_fine_min, nf));
+  TRY(dalloc(&p->d_fine_max, nf));
+  TRY(dalloc(&p->d_fine_r, nf));
+  TRY(dalloc(&p->d_rc, (u64)max_jobs * (FINE_MAX + 1)));
+  TRY(dalloc(&p->d_sp, nf));
+  TRY(dalloc(&p->d_fstart, (u64)max_jobs * (P_MAX + 1)));
+  TRY(dalloc(&p->d_part_off, (u64)max_jobs * (P_MAX + 1)));
+  TRY(halloc(&p->h_scalar, 16));
+  TRY(dalloc(&p->d_log2, 65536));
+  launch_log2_table(p->d_log2, p->st);
+  if (cudaGetLastError() != cudaSuccess) TRY(MPSM_ERR_CUDA);
+  if (p->timing)
+    for (auto& e : p->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) TRY(MPSM_ERR_CUDA);
+#undef TRY
+  *out = p;
+  return MPSM_OK;
+}
+
+MPSM_API int mpsm_sort_runs(mpsm_plan_t* p, const mpsm_tuple_t* R, uint64_t nR) {
+  int rc = check_inputs(p, R, nR, nullptr, 0);
+  if (rc) return rc;
+  Jobh j{reinterpret_cast<const Tuple*>(R), nullptr, nR, 0};
+  rc = setup_jobs(p, &j, 1);
+  if (rc) return rc;
+  return phase_runs(p);
+}
+
+MPSM_API int mpsm_splitters(mpsm_plan_t* p, const mpsm_tuple_t* S, uint64_t nS) {
+  if (!p) return MPSM_ERR_INVALID_ARG;
+  if (p->stage < ST_RUNS || p->njobs != 1) return MPSM_ERR_STATE;
+  int rc = check_inputs(p, nullptr, 0, S, nS);
+  if (rc) return rc;
+  // attach S to the single job and re-upload the S tables (R's state on the device is kept)
+  const u64 tiles_need = (nS + p->tile - 1) / p->tile;
+  const u64 win_need = tiles_need * p->h_jobs[0].runs;
+  if (win_need * 2 > p->win_cap) {
+    dfree(p->d_win);
+    p->win_cap = std::max<u64>(win_need * 2, 1024);
+    if (dalloc(&p->d_win, p->win_cap)) return MPSM_ERR_OOM;
+  }
+  if (tiles_need + 1 > p->tile_cap) {
+    dfree(p->d_tile_cnt);
+    dfree(p->d_tile_out);
+    p->tile_cap = tiles_need + 1024;
+    if (dalloc(&p->d_tile_cnt, p->tile_cap) || dalloc(&p->d_tile_out, p->tile_cap)) return MPSM_ERR_OOM;
+  }
+  u64 ch = (nS + 4ull * p->nsm - 1) / (4ull * p->nsm);
+  ch = std::max<u64>(ch, 65536);
+  p->ch_s = (ch + 4095) / 4096 * 4096;
+  // device job: set S fields only (R fields were updated on the device by phase 1)
+  CK(cudaMemcpyAsync(p->h_jobs, p->d_jobs, sizeof(Job), cudaMemcpyDeviceToHost, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  p->h_jobs[0].S = reinterpret_cast<const Tuple*>(S);
+  p->h_jobs[0].nS = nS;
+  p->h_jobs[0].s_base = 0;
+  p->h_jobs[0].parts_req = p->opt.partitions_s ? p->opt.partitions_s : auto_parts(nS);
+  Seg sg{0, nS, 0, 0, 0, W_SIN};
+  p->h_segs[0] = sg;
+  p->h_cnt[C_SPLIT] = 1;
+  CK(cudaMemcpyAsync(p->d_jobs, p->h_jobs, sizeof(Job), cudaMemcpyHostToDevice, p->st));
+  CK(cudaMemcpyAsync(p->d_split, p->h_segs, sizeof(Seg), cudaMemcpyHostToDevice, p->st));
+  CK(cudaMemcpyAsync(&p->d_cnt[C_SPLIT], &p->h_cnt[C_SPLIT], sizeof(u32), cudaMemcpyHostToDevice, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  return phase_splitters(p);
+}
+
+MPSM_API int mpsm_scatter(mpsm_plan_t* p) {
+  if (!p) return MPSM_ERR_INVALID_ARG;
+  if (p->stage < ST_SPLIT) return MPSM_ERR_STATE;
+  return phase_scatter(p);
+}
+
+MPSM_API int mpsm_sort_partitions(mpsm_plan_t* p) {
+  if (!p) return MPSM_ERR_INVALID_ARG;
+  if (p->stage < ST_SCATTER) return MPSM_ERR_STATE;
+  return phase_sort_parts(p);
+}
+
+MPSM_API int mpsm_search(mpsm_plan_t* p) {
+  if (!p) return MPSM_ERR_INVALID_ARG;
+  if (p->stage < ST_SORTED) return MPSM_ERR_STATE;
+  return phase_search(p);
+}
+
+MPSM_API int mpsm_merge_join(mpsm_plan_t* p, uint64_t* out_count, uint64_t* out_checksum, mpsm_pairs_t* pairs) {
+  if (!p) return MPSM_ERR_INVALID_ARG;
+  if (p->stage < ST_SEARCH) return MPSM_ERR_STATE;
+  if (pairs && pairs->capacity && (!pairs->data || !aligned16(pairs->data))) return MPSM_ERR_INVALID_ARG;
+  return phase_join(p, out_count, out_checksum, pairs);
+}
+
+static int join_device(mpsm_plan_t* p, const mpsm_tuple_t* R, uint64_t nR, const mpsm_tuple_t* S, uint64_t nS,
+                       uint64_t* out_count, uint64_t* out_checksum, mpsm_pairs_t* pairs) {
+  Jobh j{reinterpret_cast<const Tuple*>(R), reinterpret_cast<const Tuple*>(S), nR, nS};
+  int rc = setup_jobs(p, &j, 1);
+  if (rc) return rc;
+  if ((rc = phase_runs(p))) return rc;
+  if ((rc = phase_splitters(p))) return rc;
+  if ((rc = phase_scatter(p))) return rc;
+  if ((rc = phase_sort_parts(p))) return rc;
+  if ((rc = phase_search(p))) return rc;
+  return phase_join(p, out_count, out_checksum, pairs);
+}
+
+MPSM_API int mpsm_join(mpsm_plan_t* p, const mpsm_tuple_t* R, uint64_t nR, const mpsm_tuple_t* S, uint64_t nS,
+                       uint64_t* out_count, uint64_t* out_checksum, mpsm_pairs_t* pairs) {
+  int rc = check_inputs(p, R, nR, S, nS);
+  if (rc) return rc;
+  if (pairs && pairs->capacity && (!pairs->data || !aligned16(pairs->data))) return MPSM_ERR_INVALID_ARG;
+  return join_device(p, R, nR, S, nS, out_count, out_checksum, pairs);
+}
+
+MPSM_API int mpsm_join_host(mpsm_plan_t* p, const mpsm_tuple_t* R_host, uint64_t nR, const mpsm_tuple_t* S_host,
+                            uint64_t nS, uint64_t* out_count, uint64_t* out_checksum) {
+  if (!p) return MPSM_ERR_INVALID_ARG;
+  if ((nR && !R_host) || (nS && !S_host) || nR > p->max_nR || nS > p->max_nS) return MPSM_ERR_INVALID_ARG;
+  if (!p->stage_r && dalloc(&p->stage_r, p->max_nR)) return MPSM_ERR_OOM;
+  if (!p->stage_s && dalloc(&p->stage_s, p->max_nS)) return MPSM_ERR_OOM;
+  if (nR) CK(cudaMemcpyAsync(p->stage_r, R_host, nR * sizeof(Tuple), cudaMemcpyHostToDevice, p->st));
+  if (nS) CK(cudaMemcpyAsync(p->stage_s, S_host, nS * sizeof(Tuple), cudaMemcpyHostToDevice, p->st));
+  return join_device(p, reinterpret_cast<const mpsm_tuple_t*>(p->stage_r), nR,
+                     reinterpret_cast<const mpsm_tuple_t*>(p->stage_s), nS, out_count, out_checksum, nullptr);
+}
+
+MPSM_API int mpsm_join_batch(mpsm_plan_t* p, const mpsm_job_t* jobs, uint32_t njobs, uint64_t* out_counts,
+                             uint64_t* out_checksums) {
+  if (!p || !jobs || !njobs || njobs > p->max_jobs) return MPSM_ERR_INVALID_ARG;
+  std::vector<Jobh> jh(njobs);
+  u64 tR = 0, tS = 0;
+  for (u32 i = 0; i < njobs; ++i) {
+    if ((jobs[i].nR && !jobs[i].R) || (jobs[i].nS && !jobs[i].S)) return MPSM_ERR_INVALID_ARG;
+    if (!aligned16(jobs[i].R) || !aligned16(jobs[i].S)) return MPSM_ERR_INVALID_ARG;
+    jh[i] = Jobh{reinterpret_cast<const Tuple*>(jobs[i].R), reinterpret_cast<const Tuple*>(jobs[i].S), jobs[i].nR,
+                 jobs[i].nS};
+    tR += jobs[i].nR;
+    tS += jobs[i].nS;
+  }
+  if (tR > p->max_nR || tS > p->max_nS) return MPSM_ERR_INVALID_ARG;
+  int rc = setup_jobs(p, jh.data(), njobs);
+  if (rc) return rc;
+  // same job sizes and pointers as the captured graph -> replay it
+  std::vector<u64> sig;
+  sig.reserve(4 * njobs);
+  for (u32 i = 0; i < njobs; ++i) {
+    sig.push_back((u64)(uintptr_t)jh[i].R);
+    sig.push_back(jh[i].nR);
+    sig.push_back((u64)(uintptr_t)jh[i].S);
+    sig.push_back(jh[i].nS);
+  }
+  if (!p->gexec || sig != p->gsig) {
+    if (p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    p->graph_mode = true;
+    const bool saved_timing = p->timing;
+    p->timing = false;
+    CK(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+    int prc = MPSM_OK;
+    if (!prc) prc = phase_runs(p);
+    if (!prc) prc = phase_splitters(p);
+    if (!prc) prc = phase_scatter(p);
+    if (!prc) prc = phase_sort_parts(p);
+    if (!prc) {
+      launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, p->st);
+      launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win, p->st,
+                    p->nsm);
+      launch_join(JOIN_AGG, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win,
+                  nullptr, nullptr, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm);
+    }
+    cudaError_t ce = cudaStreamEndCapture(p->st, &g);
+    p->graph_mode = false;
+    p->timing = saved_timing;
+    if (prc) {
+      if (g) cudaGraphDestroy(g);
+      return prc;
+    }
+    if (ce != cudaSuccess) return MPSM_ERR_CUDA;
+    ce = cudaGraphInstantiate(&p->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return MPSM_ERR_CUDA;
+    p->gsig = sig;
+  }
+  record(p, EV_START);
+  CK(cudaGraphLaunch(p->gexec, p->st));
+  record(p, EV_JOIN);
+  CK(cudaMemcpyAsync(p->h_jobs, p->d_jobs, njobs * sizeof(Job), cudaMemcpyDeviceToHost, p->st));
+  rc = read_err(p);
+  p->stage = ST_DONE;
+  if (rc) return rc;
+  for (u32 i = 0; i < njobs; ++i) {
+    if (out_counts) out_counts[i] = p->h_jobs[i].count;
+    if (out_checksums) out_checksums[i] = p->h_jobs[i].checksum;
+  }
+  return MPSM_OK;
+}
+
+MPSM_API int mpsm_plan_stats(mpsm_plan_t* p, mpsm_stats_t* s) {
+  if (!p || !s) return MPSM_ERR_INVALID_ARG;
+  memset(s, 0, sizeof(*s));
+  CK(cudaStreamSynchronize(p->st));
+  if (p->njobs == 0) return MPSM_OK;
+  CK(cudaMemcpy(p->h_jobs, p->d_jobs, sizeof(Job), cudaMemcpyDeviceToHost));
+  const Job& J = p->h_jobs[0];
+  s->runs_r = J.runs;
+  s->partitions_s = J.parts;
+  s->nfine = J.nfine;
+  s->fine_shift = J.fine_shift;
+  s->s_kept = J.s_kept;
+  s->tiles = J.ntiles;
+  s->levels_r = p->levels_r;
+  s->levels_s = p->levels_s;
+  if (J.parts) {
+    std::vector<u64> po(J.parts + 1);
+    CK(cudaMemcpy(po.data(), p->d_part_off + J.part_base, (J.parts + 1) * sizeof(u64), cudaMemcpyDeviceToHost));
+    u64 mx = 0;
+    for (u32 i = 0; i < J.parts; ++i) mx = std::max<u64>(mx, po[i + 1] - po[i]);
+    s->part_max = mx;
+    s->imbalance = po[J.parts] ? (double)mx * J.parts / (double)po[J.parts] : 0.0;
+  }
+  if (J.ntiles && J.runs && p->stage >= ST_SEARCH) {
+    const u64 nw = J.ntiles * J.runs;
+    std::vector<u32> w(2 * nw);
+    CK(cudaMemcpy(w.data(), p->d_win + 2 * J.win_base, 2 * nw * sizeof(u32), cudaMemcpyDeviceToHost));
+    double sum = 0;
+    for (u64 i = 0; i < nw; ++i) sum += (double)(w[2 * i + 1] - w[2 * i]);
+    s->mean_window = sum / (double)nw;
+  }
+  if (p->timing) {
+    auto el = [&](int a, int b) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, p->ev[a], p->ev[b]) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 0;
+      }
+      return ms;
+    };
+    s->ms_sort_runs = el(EV_START, EV_RUNS);
+    s->ms_splitters = el(EV_RUNS, EV_SPLIT);
+    s->ms_scatter = el(EV_SPLIT, EV_SCATTER);
+    s->ms_sort_partitions = el(EV_SCATTER, EV_SORTS);
+    s->ms_search = el(EV_SORTS, EV_SEARCH);
+    s->ms_join = el(EV_SEARCH, EV_JOIN);
+    s->ms_total = el(EV_START, EV_JOIN);
+  }
+  return MPSM_OK;
+}
+
+MPSM_API int mpsm_plan_view(mpsm_plan_t* p, mpsm_view_t* v) {
+  if (!p || !v) return MPSM_ERR_INVALID_ARG;
+  memset(v, 0, sizeof(*v));
+  CK(cudaStreamSynchronize(p->st));
+  if (p->njobs == 0) return MPSM_ERR_STATE;
+  CK(cudaMemcpy(p->h_jobs, p->d_jobs, sizeof(Job), cudaMemcpyDeviceToHost));
+  const Job& J = p->h_jobs[0];
+  // run boundaries of job 0 as one array (xr offsets)
+  const u64 nchunks = J.nS ? (J.nS + p->ch_s - 1) / p->ch_s : 0;
+  const u64 need = (u64)J.runs + 1 + nchunks + 1;
+  if (need > p->chunk_off_cap) {
+    dfree(p->d_chunk_off);
+    p->chunk_off_cap = need + 64;
+    if (dalloc(&p->d_chunk_off, p->chunk_off_cap)) return MPSM_ERR_OOM;
+  }
+  std::vector<u64> h(need);
+  for (u32 j = 0; j < J.runs; ++j) h[j] = p->h_runs[J.run_base + j].off - J.r_base;
+  h[J.runs] = J.nR;
+  for (u64 c = 0; c <= nchunks; ++c) h[J.runs + 1 + c] = std::min<u64>(c * p->ch_s, J.nS);
+  CK(cudaMemcpy(p->d_chunk_off, h.data(), need * sizeof(u64), cudaMemcpyHostToDevice));
+  v->r_runs = reinterpret_cast<const mpsm_tuple_t*>(p->xr + J.r_base);
+  v->run_offsets = reinterpret_cast<const uint64_t*>(p->d_chunk_off);
+  v->runs_r = J.runs;
+  v->key_min = J.kmin;
+  v->key_max = J.kmax;
+  v->nfine = J.nfine;
+  v->fine_shift = J.fine_shift;
+  v->fine_s = reinterpret_cast<const uint64_t*>(p->d_fine_s + J.fine_base);
+  v->fine_r = reinterpret_cast<const uint64_t*>(p->d_fine_r + J.fine_base);
+  v->splitters = p->d_sp + J.fine_base;
+  v->partitions_s = J.parts;
+  v->s_chunks = (u32)nchunks;
+  v->s_chunk_offsets = reinterpret_cast<const uint64_t*>(p->d_chunk_off + J.runs + 1);
+  v->chunk_offsets = p->d_hist_a;  // valid after mpsm_splitters / mpsm_scatter (job 0's chunks first)
+  v->part_offsets = reinterpret_cast<const uint64_t*>(p->d_part_off + J.part_base);
+  v->s_buffer = reinterpret_cast<const mpsm_tuple_t*>(p->xs + J.s_base);
+  v->s_kept = J.s_kept;
+  v->tiles = J.ntiles;
+  v->join_tile = p->tile;
+  v->windows = p->d_win + 2 * J.win_base;
+  return MPSM_OK;
+}
+
+MPSM_API const char* mpsm_strerror(int status) {
+  switch (status) {
+    case MPSM_OK: return "ok";
+    case MPSM_ERR_INVALID_ARG: return "invalid argument";
+    case MPSM_ERR_OOM: return "out of device memory";
+    case MPSM_ERR_CUDA: return "CUDA error";
+    case MPSM_ERR_CAPACITY: return "pair buffer too small";
+    case MPSM_ERR_DEVICE: return "device-side check failed";
+    case MPSM_ERR_STATE: return "phase called out of order";
+    default: return "unknown status";
+  }
+}

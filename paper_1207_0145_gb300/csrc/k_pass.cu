@@ -1,0 +1,733 @@
+// k_pass.cu -- the partitioning machinery shared by phases 1-3 of MPSM.
+//
+// A pass takes a list of "big" segments (contiguous, key-ordered slices too large
+// to sort in one block's shared memory) and splits each into F key-ordered
+// buckets, the paper's radix clustering (Sec. 3.2.1):
+//   k_level_plan : per segment, the bucket function and the chunking (one chunk
+//                  = one "worker" W_i of the paper, a contiguous piece of input)
+//   k_hist       : per chunk, the histogram h_i over the F buckets (+ exact
+//                  per-bucket key min/max)
+//   k_scan       : per segment, the prefix sums ps_i[b] = start of bucket b +
+//                  sum over chunks k < i of h_k[b] (the ps equation under Fig. 6),
+//                  and the children segments for the next pass
+//   k_scatter    : per chunk, every tuple copied to ps_i[bucket]++ (Sec. 4.3) --
+//                  synchronisation-free, since each chunk owns its ranges
+// The same kernels run three bucket functions: MODE_RADIX (top bits of
+// key - segment min, the sort passes of phases 1 and 3), MODE_FINE (the fine
+// B-bit histogram of S over R's key range, Sec. 4.2) and MODE_SPLIT (fine bucket
+// -> partition through the splitter vector sp, Sec. 4.3).
+// Segments that fit NMAX tuples are finished by k_seg_sort: one block loads the
+// segment with a bulk async copy (TMA) into shared memory and radix-sorts it
+// there (first digit by an unstable counting pass, further digits by stable
+// warp-ballot ranking), then writes it out in order.
+#include "mpsm_internal.cuh"
+#include "mpsm_launch.h"
+
+namespace mpsm {
+
+namespace {
+
+constexpr u32 NT_PASS = 512;
+constexpr u32 SC_TILE = 4096;  // tuples per scatter tile
+constexpr u32 NT_SORT = 512;
+constexpr u32 NW_SORT = NT_SORT / 32;
+
+__device__ __forceinline__ u64 ld_key_stream(const Tuple* p) {
+  return (u64)__ldcs(reinterpret_cast<const long long*>(&p->key));
+}
+
+__device__ __forceinline__ void emit(Seg* out, u32* cnt, u32 cap, const Seg& s, u32* err) {
+  const u32 i = atomicAdd(cnt, 1u);
+  if (i < cap) out[i] = s; else atomicOr(err, (u32)DERR_SEG_OVERFLOW);
+}
+
+__device__ __forceinline__ u32 find_seg(const LSeg* ls, u32 n, u64 c) {
+  u32 lo = 0, hi = n;  // last s with chunk_base <= c
+  while (hi - lo > 1) {
+    const u32 mid = (lo + hi) >> 1;
+    if (ls[mid].chunk_base <= c) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------- bounds by sampling
+__global__ void k_sample_bounds(Seg* segs, const u32* nseg_ptr, Bufs bufs, const Job* jobs) {
+  const u32 n = *nseg_ptr;
+  const u32 lane = lane_id();
+  const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const u32 nw = (gridDim.x * blockDim.x) >> 5;
+  for (u32 s = gw; s < n; s += nw) {
+    const Seg sg = segs[s];
+    const Tuple* src = seg_src(bufs, jobs, sg.flags & 7u, sg.job, sg.off);
+    u64 mn = ~0ull, mx = 0;
+    for (u32 i = lane; i < 1024; i += 32) {
+      const u64 p = (sg.len - 1) * (u64)i / 1023ull;
+      const u64 k = src[p].key;
+      mn = k < mn ? k : mn;
+      mx = k > mx ? k : mx;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const u64 a = __shfl_xor_sync(0xffffffffu, mn, d), b = __shfl_xor_sync(0xffffffffu, mx, d);
+      mn = a < mn ? a : mn;
+      mx = b > mx ? b : mx;
+    }
+    // a sample misses the extremes by about range/1024: widen so the edge buckets stay small
+    const u64 pad = (mx - mn) >> 8;
+    mn = mn > pad ? mn - pad : 0ull;
+    mx = (~0ull - mx) > pad ? mx + pad : ~0ull;
+    if (lane == 0) {
+      segs[s].kmin = mn;
+      segs[s].kmax = mx;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- level plan
+__global__ void __launch_bounds__(1024) k_level_plan(const Seg* segs, u32* nseg_ptr, u32 seg_cap, LSeg* ls,
+                                                     u64* totals, u32 mode, u64 chunk, u32 radix_bits,
+                                                     const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err) {
+  __shared__ u64 s_warp[33];
+  __shared__ u64 carry[3];
+  u32 n = *nseg_ptr;
+  if (n > seg_cap) n = seg_cap;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *nseg_ptr = n;
+    carry[0] = carry[1] = carry[2] = 0;
+  }
+  __syncthreads();
+  const u32 fmax = 1u << radix_bits;
+  for (u32 base = 0; base < n; base += 1024) {
+    const u32 i = base + threadIdx.x;
+    u64 nch = 0, nh = 0, nb = 0;
+    LSeg L{};
+    if (i < n) {
+      const Seg s = segs[i];
+      u32 F, shift;
+      u64 lo;
+      if (mode == MODE_RADIX) {
+        const u64 want = (s.len + N_LEAF - 1) / N_LEAF;
+        u32 f = F_MIN;
+        while (f < want && f < fmax) f <<= 1;
+        const u32 d = 31u - (u32)__clz(f);
+        const u64 range = s.kmax - s.kmin;
+        const u32 bits = bitlen64(range);
+        shift = bits > d ? bits - d : 0u;
+        F = (u32)(range >> shift) + 1u;
+        lo = s.kmin;
+      } else {
+        const Job& J = jobs[s.job];
+        lo = J.kmin;
+        shift = J.fine_shift;
+        F = (mode == MODE_FINE) ? J.nfine : J.parts;
+      }
+      nch = F ? (s.len + chunk - 1) / chunk : 0;
+      nh = nch * F;
+      nb = F;
+      L.lo = lo;
+      L.shift = shift;
+      L.F = F;
+      L.nchunks = (u32)nch;
+      L.pad = (mode == MODE_FINE) ? 1u : 0u;
+      L.bucket_base = (mode == MODE_FINE) ? jobs[s.job].fine_base : 0ull;
+    }
+    u64 t0, t1, t2;
+    const u64 p0 = block_exclusive_scan<u64, 1024>(nch, &t0, s_warp);
+    const u64 p1 = block_exclusive_scan<u64, 1024>(nh, &t1, s_warp);
+    const u64 p2 = block_exclusive_scan<u64, 1024>(nb, &t2, s_warp);
+    if (i < n) {
+      L.chunk_base = carry[0] + p0;
+      L.hist_base = carry[1] + p1;
+      if (mode != MODE_FINE) L.bucket_base = carry[2] + p2;  // fine buckets sit at the job's fixed slot
+      ls[i] = L;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      carry[0] += t0;
+      carry[1] += t1;
+      carry[2] += t2;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (carry[1] > hist_cap || carry[2] > bucket_cap) {
+      atomicOr(err, (u32)DERR_HIST_OVERFLOW);
+      carry[0] = carry[1] = carry[2] = 0;
+      *nseg_ptr = 0;
+    }
+    totals[0] = carry[0];
+    totals[1] = carry[1];
+    totals[2] = carry[2];
+  }
+}
+
+__global__ void k_init_buckets(u64* bmin, u64* bmax, u64* btot, const u64* totals) {
+  const u64 n = totals[2];
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+    bmin[i] = ~0ull;
+    bmax[i] = 0;
+    if (btot) btot[i] = 0;
+  }
+}
+
+// ---------------------------------------------------------------- histograms
+template <u32 MODE, u32 FCAP>
+__global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* nseg_ptr, const LSeg* ls,
+                                                  const u64* totals, u64 chunk, Bufs bufs, const Job* jobs,
+                                                  u32 src_where, u32* hist, u64* bmin, u64* bmax, u64* btot) {
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  u64* smin = reinterpret_cast<u64*>(sm_raw);
+  u64* smax = smin + FCAP;
+  u32* scnt = reinterpret_cast<u32*>(smax + FCAP);
+  __shared__ u32 s_seg;
+  const u64 nch = totals[0];
+  const u32 nseg = *nseg_ptr;
+  for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+    if (threadIdx.x == 0) s_seg = find_seg(ls, nseg, c);
+    __syncthreads();
+    const LSeg L = ls[s_seg];
+    const Seg S = segs[s_seg];
+    const u32 F = L.F;
+    for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
+      scnt[b] = 0;
+      smin[b] = ~0ull;
+      smax[b] = 0;
+    }
+    __syncthreads();
+    const u64 ci = c - L.chunk_base;
+    const u64 a = ci * chunk;
+    const u64 e = (a + chunk < S.len) ? a + chunk : S.len;
+    const Tuple* src = seg_src(bufs, jobs, src_where, S.job, S.off);
+    u64 kmin = 0, kmax = ~0ull;
+    if (MODE == MODE_FINE) {
+      kmin = jobs[S.job].kmin;
+      kmax = jobs[S.job].kmax;
+    }
+    for (u64 t0 = a + threadIdx.x; t0 < e; t0 += NT_PASS * 4) {
+      u64 k[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const u64 t = t0 + (u64)i * NT_PASS;
+        k[i] = t < e ? ld_key_stream(src + t) : 0;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const u64 t = t0 + (u64)i * NT_PASS;
+        if (t >= e) continue;
+        u32 b;
+        if (MODE == MODE_RADIX) {
+          const u64 d = k[i] < L.lo ? 0ull : (k[i] - L.lo) >> L.shift;
+          b = d >= F ? F - 1u : (u32)d;
+        } else {
+          if (k[i] < kmin || k[i] > kmax) continue;
+          b = (u32)((k[i] - kmin) >> L.shift);
+        }
+        atomicAdd(&scnt[b], 1u);
+        atomicMin(&smin[b], k[i]);
+        atomicMax(&smax[b], k[i]);
+      }
+    }
+    __syncthreads();
+    u32* hrow = hist + L.hist_base + ci * F;
+    for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
+      const u32 cnt = scnt[b];
+      hrow[b] = cnt;
+      if (cnt) {
+        atomicMin(&bmin[L.bucket_base + b], smin[b]);
+        atomicMax(&bmax[L.bucket_base + b], smax[b]);
+        if (btot) atomicAdd(&btot[L.bucket_base + b], (u64)cnt);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- prefix sums + children
+template <u32 MODE>
+__global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* nseg_ptr, const LSeg* ls, u32* hist,
+                                                  const u64* bmin, const u64* bmax, const u32* part_fstart,
+                                                  Seg* big_out, u32* big_cnt, u32 big_cap, Seg* fin_out,
+                                                  u32* fin_cnt, u32 fin_cap, u32 dst_where, u32 final_where,
+                                                  Job* jobs, u64* part_off, u32* err) {
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  u64* start = reinterpret_cast<u64*>(sm_raw);  // F_MAX + 1
+  u64* bkmin = start + (F_MAX + 1);             // F_MAX
+  u64* bkmax = bkmin + F_MAX;                   // F_MAX
+  __shared__ u64 s_warp[NT_PASS / 32 + 1];
+  const u32 nseg = *nseg_ptr;
+  constexpr u64 HALF = NMAX / 2;
+  for (u32 s = blockIdx.x; s < nseg; s += gridDim.x) {
+    const LSeg L = ls[s];
+    const Seg S = segs[s];
+    const u32 F = L.F;
+    const u64 C = L.nchunks;
+    u32* h = hist + L.hist_base;
+    const Job J = jobs[S.job];
+    for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
+      u64 run = 0;
+      for (u64 c = 0; c < C; ++c) {
+        const u32 v = h[c * F + b];
+        h[c * F + b] = (u32)run;
+        run += v;
+      }
+      start[b] = run;
+      if (MODE == MODE_SPLIT) {
+        const u32 fa = part_fstart[J.part_base + b], fb = part_fstart[J.part_base + b + 1];
+        u64 mn = ~0ull, mx = 0;
+        for (u32 f = fa; f < fb; ++f) {
+          const u64 a = bmin[J.fine_base + f], z = bmax[J.fine_base + f];
+          mn = a < mn ? a : mn;
+          mx = z > mx ? z : mx;
+        }
+        bkmin[b] = mn;
+        bkmax[b] = mx;
+      } else {
+        bkmin[b] = bmin[L.bucket_base + b];
+        bkmax[b] = bmax[L.bucket_base + b];
+      }
+    }
+    __syncthreads();
+    const u64 total = smem_exclusive_scan<u64, NT_PASS, F_MAX / NT_PASS>(start, F, s_warp);
+    if (threadIdx.x == 0) start[F] = total;
+    __syncthreads();
+    for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
+      const u32 base = (u32)start[b];
+      for (u64 c = 0; c < C; ++c) h[c * F + b] += base;
+    }
+    if (MODE == MODE_SPLIT) {
+      for (u32 b = threadIdx.x; b <= F; b += NT_PASS) part_off[J.part_base + b] = start[b];
+      if (threadIdx.x == 0) jobs[S.job].s_kept = total;
+    }
+    // children: buckets of at most NMAX/2 tuples whose starts share a NMAX/2 window
+    // are packed into one final segment (<= NMAX); larger ones stand alone.
+    for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
+      const u64 st = start[b], len = start[b + 1] - st;
+      const bool pk = len <= HALF;
+      const u64 grp = st / HALF;
+      if (pk) {
+        if (b > 0 && (start[b] - start[b - 1]) <= HALF && start[b - 1] / HALF == grp) continue;  // not a leader
+        u64 end = start[b + 1], mn = bkmin[b], mx = bkmax[b];
+        for (u32 e = b + 1; e < F; ++e) {
+          const u64 le = start[e + 1] - start[e];
+          if (le > HALF || start[e] / HALF != grp) break;
+          end = start[e + 1];
+          if (le) {
+            mn = bkmin[e] < mn ? bkmin[e] : mn;
+            mx = bkmax[e] > mx ? bkmax[e] : mx;
+          }
+        }
+        const u64 glen = end - st;
+        if (glen == 0) continue;
+        if (mn == mx && dst_where == final_where) continue;  // constant keys already in place
+        Seg c{S.off + st, glen, mn, mx, S.job, dst_where | SEG_EXACT};
+        emit(fin_out, fin_cnt, fin_cap, c, err);
+      } else {
+        const u64 mn = bkmin[b], mx = bkmax[b];
+        if (len > NMAX && mn < mx) {
+          Seg c{S.off + st, len, mn, mx, S.job, dst_where | SEG_EXACT};
+          emit(big_out, big_cnt, big_cap, c, err);
+        } else if (mn == mx) {
+          if (dst_where == final_where) continue;
+          for (u64 p = 0; p < len; p += NMAX) {
+            const u64 l = (len - p < NMAX) ? len - p : NMAX;
+            Seg c{S.off + st + p, l, mn, mx, S.job, dst_where | SEG_EXACT};
+            emit(fin_out, fin_cnt, fin_cap, c, err);
+          }
+        } else {
+          Seg c{S.off + st, len, mn, mx, S.job, dst_where | SEG_EXACT};
+          emit(fin_out, fin_cnt, fin_cap, c, err);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- scatter
+template <u32 MODE>
+__global__ void __launch_bounds__(NT_PASS) k_scatter(const Seg* segs, const u32* nseg_ptr, const LSeg* ls,
+                                                     const u64* totals, u64 chunk, Bufs bufs, const Job* jobs,
+                                                     u32 src_where, u32 dst_where, const u32* hist, const u32* sp) {
+  constexpr u32 IT = SC_TILE / NT_PASS;
+  constexpr u32 DROP = 0xFFFFFFFFu;
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  Tuple* stage = reinterpret_cast<Tuple*>(sm_raw);                 // SC_TILE
+  u32* hcnt = reinterpret_cast<u32*>(stage + SC_TILE);             // F_MAX
+  u32* hb = hcnt + F_MAX;                                          // F_MAX
+  u32* cur = hb + F_MAX;                                           // F_MAX
+  u16* sb = reinterpret_cast<u16*>(cur + F_MAX);                   // SC_TILE
+  u16* spl = sb + SC_TILE;                                         // FINE_MAX (MODE_SPLIT)
+  __shared__ u32 s_seg;
+  __shared__ u32 s_warp[NT_PASS / 32 + 1];
+  const u64 nch = totals[0];
+  const u32 nseg = *nseg_ptr;
+  Tuple* dbase = dst_where == W_XR ? bufs.xr : (dst_where == W_XS ? bufs.xs : bufs.y);
+  for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
+    if (threadIdx.x == 0) s_seg = find_seg(ls, nseg, c);
+    __syncthreads();
+    const LSeg L = ls[s_seg];
+    const Seg S = segs[s_seg];
+    const u32 F = L.F;
+    const u64 ci = c - L.chunk_base;
+    const u32* orow = hist + L.hist_base + ci * F;
+    for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
+      cur[b] = orow[b];
+      hcnt[b] = 0;
+    }
+    u64 kmin = 0, kmax = ~0ull;
+    if (MODE == MODE_SPLIT) {
+      const Job& J = jobs[S.job];
+      kmin = J.kmin;
+      kmax = J.kmax;
+      for (u32 f = threadIdx.x; f < J.nfine; f += NT_PASS) spl[f] = (u16)sp[J.fine_base + f];
+    }
+    __syncthreads();
+    const u64 a = ci * chunk;
+    const u64 e = (a + chunk < S.len) ? a + chunk : S.len;
+    const Tuple* src = seg_src(bufs, jobs, src_where, S.job, S.off);
+    Tuple* dst = dbase + S.off;
+    for (u64 t0 = a; t0 < e; t0 += SC_TILE) {
+      Tuple v[IT];
+      u32 bk[IT], rk[IT];
+#pragma unroll
+      for (u32 i = 0; i < IT; ++i) {
+        const u64 t = t0 + i * NT_PASS + threadIdx.x;
+        bk[i] = DROP;
+        rk[i] = 0;
+        if (t < e) v[i] = ld_stream(src + t);
+      }
+#pragma unroll
+      for (u32 i = 0; i < IT; ++i) {
+        const u64 t = t0 + i * NT_PASS + threadIdx.x;
+        if (t >= e) continue;
+        const u64 k = v[i].key;
+        u32 b;
+        if (MODE == MODE_RADIX) {
+          const u64 d = k < L.lo ? 0ull : (k - L.lo) >> L.shift;
+          b = d >= F ? F - 1u : (u32)d;
+        } else {
+          if (k < kmin || k > kmax) continue;
+          b = spl[(k - kmin) >> L.shift];
+        }
+        bk[i] = b;
+        rk[i] = atomicAdd(&hcnt[b], 1u);
+      }
+      __syncthreads();
+      // hb = exclusive scan of hcnt
+      {
+        constexpr u32 PER = F_MAX / NT_PASS;
+        u32 loc[PER], sum = 0;
+#pragma unroll
+        for (u32 i = 0; i < PER; ++i) {
+          const u32 b = threadIdx.x * PER + i;
+          loc[i] = b < F ? hcnt[b] : 0u;
+          sum += loc[i];
+        }
+        u32 tot;
+        u32 pre = block_exclusive_scan<u32, NT_PASS>(sum, &tot, s_warp);
+#pragma unroll
+        for (u32 i = 0; i < PER; ++i) {
+          const u32 b = threadIdx.x * PER + i;
+          if (b < F) hb[b] = pre;
+          pre += loc[i];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (u32 i = 0; i < IT; ++i) {
+        if (bk[i] == DROP) continue;
+        const u32 p = hb[bk[i]] + rk[i];
+        stage[p] = v[i];
+        sb[p] = (u16)bk[i];
+      }
+      __syncthreads();
+      const u32 kept = hb[F - 1] + hcnt[F - 1];
+      for (u32 p = threadIdx.x; p < kept; p += NT_PASS) {
+        const u32 b = sb[p];
+        st_tuple(dst + cur[b] + (p - hb[b]), stage[p]);
+      }
+      __syncthreads();
+      for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
+        cur[b] += hcnt[b];
+        hcnt[b] = 0;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------- final in-SMEM sort
+__global__ void __launch_bounds__(NT_SORT, 1) k_seg_sort(const Seg* segs, const u32* nseg_ptr, u32 cap, u32* work,
+                                                         Bufs bufs, const Job* jobs, u32 dst_where, u32* err) {
+  constexpr u32 IT = NMAX / NT_SORT;  // 16
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  Tuple* tup = reinterpret_cast<Tuple*>(sm_raw);        // NMAX
+  u16* ia = reinterpret_cast<u16*>(tup + NMAX);         // NMAX
+  u16* ib = ia + NMAX;                                  // NMAX
+  u32* cnt = reinterpret_cast<u32*>(ib + NMAX);         // NW_SORT * 256 (>= 2048)
+  __shared__ __align__(8) u64 mbar;
+  __shared__ u32 s_item;
+  __shared__ u32 s_warp[NT_SORT / 32 + 1];
+  __shared__ u64 s_mn[NW_SORT], s_mx[NW_SORT];
+  const u32 tid = threadIdx.x, lane = lane_id(), wid = warp_id();
+  if (tid == 0) mbar_init(&mbar, 1);
+  __syncthreads();
+  u32 phase = 0;
+  u32 n_items = *nseg_ptr;
+  if (n_items > cap) n_items = cap;
+  Tuple* dstb = dst_where == W_XR ? bufs.xr : bufs.xs;
+  for (;;) {
+    // order this block's earlier generic-proxy use of the buffers before the next bulk copy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) s_item = atomicAdd(work, 1u);
+    __syncthreads();
+    const u32 item = s_item;
+    __syncthreads();
+    if (item >= n_items) break;
+    const Seg sg = segs[item];
+    const Tuple* src = seg_src(bufs, jobs, sg.flags & 7u, sg.job, sg.off);
+    Tuple* dst = dstb + sg.off;
+    const u32 n = (u32)sg.len;
+    const bool inplace = (src == dst);
+    if ((sg.flags & SEG_EXACT) && sg.kmin == sg.kmax) {
+      if (!inplace)
+        for (u32 i = tid; i < n; i += NT_SORT) st_tuple(dst + i, src[i]);
+      continue;
+    }
+    if (sg.len > NMAX) {
+      if (tid == 0) atomicOr(err, (u32)DERR_SEG_TOO_BIG);
+      continue;
+    }
+    if (tid == 0) tma_load_1d(tup, src, n * (u32)sizeof(Tuple), &mbar);
+    const bool ok = mbar_wait(&mbar, phase, SPIN_LIMIT);
+    phase ^= 1u;
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicOr(err, (u32)DERR_TMA_TIMEOUT);
+      break;
+    }
+    // exact key range of the segment
+    u64 mn = ~0ull, mx = 0;
+    for (u32 i = tid; i < n; i += NT_SORT) {
+      const u64 k = tup[i].key;
+      mn = k < mn ? k : mn;
+      mx = k > mx ? k : mx;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const u64 a = __shfl_xor_sync(0xffffffffu, mn, d), b = __shfl_xor_sync(0xffffffffu, mx, d);
+      mn = a < mn ? a : mn;
+      mx = b > mx ? b : mx;
+    }
+    if (lane == 0) {
+      s_mn[wid] = mn;
+      s_mx[wid] = mx;
+    }
+    __syncthreads();
+    mn = s_mn[0];
+    mx = s_mx[0];
+#pragma unroll
+    for (u32 w = 1; w < NW_SORT; ++w) {
+      mn = s_mn[w] < mn ? s_mn[w] : mn;
+      mx = s_mx[w] > mx ? s_mx[w] : mx;
+    }
+    const u32 bits = bitlen64(mx - mn);
+    if (bits == 0) {
+      if (!inplace)
+        for (u32 i = tid; i < n; i += NT_SORT) st_tuple(dst + i, tup[i]);
+      __syncthreads();
+      continue;
+    }
+    // pass 1: counting sort on the low digit (order within a digit is free here)
+    const u32 w1 = bits < 11u ? bits : 11u;
+    const u32 F1 = 1u << w1;
+    for (u32 b = tid; b < F1; b += NT_SORT) cnt[b] = 0;
+    __syncthreads();
+    u32 dr[IT];
+#pragma unroll
+    for (u32 i = 0; i < IT; ++i) {
+      const u32 e = tid + i * NT_SORT;
+      if (e < n) {
+        const u32 d = (u32)((tup[e].key - mn) & (u64)(F1 - 1u));
+        const u32 r = atomicAdd(&cnt[d], 1u);
+        dr[i] = (d << 16) | r;
+      }
+    }
+    __syncthreads();
+    smem_exclusive_scan<u32, NT_SORT, 4>(cnt, F1, s_warp);
+#pragma unroll
+    for (u32 i = 0; i < IT; ++i) {
+      const u32 e = tid + i * NT_SORT;
+      if (e < n) ia[cnt[dr[i] >> 16] + (dr[i] & 0xFFFFu)] = (u16)e;
+    }
+    __syncthreads();
+    // further digits: stable ranking, 8 bits per pass
+    u32 sh = w1;
+    const u32 per = (((n + NW_SORT - 1) / NW_SORT) + 31u) & ~31u;
+    const u32 wb = wid * per;
+    const u32 we = (wb + per < n) ? wb + per : n;
+    const u32 nb = per / 32u;
+    const u32 lt = (1u << lane) - 1u;
+    while (sh < bits) {
+      const u32 w = (bits - sh) < 8u ? (bits - sh) : 8u;
+      const u32 FB = 1u << w;
+      for (u32 i = tid; i < NW_SORT * 256u; i += NT_SORT) cnt[i] = 0;
+      __syncthreads();
+      u32 rec[IT];
+      u16 ee[IT];
+#pragma unroll
+      for (u32 k = 0; k < IT; ++k) {
+        if (k < nb) {
+          const u32 pos = wb + k * 32u + lane;
+          const bool valid = pos < we;
+          const u32 e = valid ? ia[pos] : 0u;
+          const u32 d = valid ? (u32)(((tup[e].key - mn) >> sh) & (u64)(FB - 1u)) : 0u;
+          u32 peers = __ballot_sync(0xffffffffu, valid);
+          for (u32 bit = 0; bit < w; ++bit) {
+            const u32 bb = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? bb : ~bb;
+          }
+          const u32 rank_in = __popc(peers & lt);
+          const u32 leader = __ffs(peers) - 1u;
+          u32 base = 0;
+          if (valid) base = cnt[wid * 256u + d];
+          __syncwarp();
+          if (valid && lane == leader) cnt[wid * 256u + d] = base + __popc(peers);
+          __syncwarp();
+          rec[k] = (d << 16) | (base + rank_in);
+          ee[k] = (u16)e;
+        }
+      }
+      __syncthreads();
+      {
+        u32 tot_d = 0;
+        if (tid < FB)
+          for (u32 ww = 0; ww < NW_SORT; ++ww) tot_d += cnt[ww * 256u + tid];
+        u32 total;
+        const u32 dbase = block_exclusive_scan<u32, NT_SORT>(tid < FB ? tot_d : 0u, &total, s_warp);
+        if (tid < FB) {
+          u32 run = dbase;
+          for (u32 ww = 0; ww < NW_SORT; ++ww) {
+            const u32 c = cnt[ww * 256u + tid];
+            cnt[ww * 256u + tid] = run;
+            run += c;
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (u32 k = 0; k < IT; ++k) {
+        if (k < nb) {
+          const u32 pos = wb + k * 32u + lane;
+          if (pos < we) ib[cnt[wid * 256u + (rec[k] >> 16)] + (rec[k] & 0xFFFFu)] = ee[k];
+        }
+      }
+      __syncthreads();
+      u16* t = ia;
+      ia = ib;
+      ib = t;
+      sh += w;
+    }
+    for (u32 i = tid; i < n; i += NT_SORT) st_tuple(dst + i, tup[ia[i]]);
+    __syncthreads();
+  }
+}
+
+__global__ void k_check_empty(const u32* cnt, u32* err, u32 flag) {
+  if (threadIdx.x == 0 && *cnt != 0) atomicOr(err, flag);
+}
+
+constexpr size_t SMEM_SCATTER = SC_TILE * sizeof(Tuple) + 3 * F_MAX * sizeof(u32) + SC_TILE * sizeof(u16) +
+                                FINE_MAX * sizeof(u16);
+constexpr size_t SMEM_SORT = NMAX * sizeof(Tuple) + 2 * NMAX * sizeof(u16) + NW_SORT * 256 * sizeof(u32);
+constexpr size_t SMEM_SCAN = (3 * F_MAX + 1) * sizeof(u64);
+
+template <class K>
+void set_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+void init_attrs_pass() {
+  set_smem(k_hist<MODE_RADIX, F_MAX>, F_MAX * 20);
+  set_smem(k_hist<MODE_FINE, FINE_MAX>, FINE_MAX * 20);
+  set_smem(k_scan<MODE_RADIX>, SMEM_SCAN);
+  set_smem(k_scan<MODE_SPLIT>, SMEM_SCAN);
+  set_smem(k_scatter<MODE_RADIX>, SMEM_SCATTER);
+  set_smem(k_scatter<MODE_SPLIT>, SMEM_SCATTER);
+  set_smem(k_seg_sort, SMEM_SORT);
+}
+
+namespace {
+
+}  // namespace
+
+void launch_sample_bounds(Seg* segs, const u32* nseg, u32 max_segs, Bufs bufs, const Job* jobs, cudaStream_t st) {
+  if (!max_segs) return;
+  const u32 blocks = (max_segs + 7) / 8;
+  k_sample_bounds<<<blocks < 1024 ? blocks : 1024, 256, 0, st>>>(segs, nseg, bufs, jobs);
+}
+
+void launch_level_plan(const Seg* segs, u32* nseg, u32 seg_cap, LSeg* ls, u64* totals, u32 mode, u64 chunk,
+                       u32 radix_bits, const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err, cudaStream_t st) {
+  k_level_plan<<<1, 1024, 0, st>>>(segs, nseg, seg_cap, ls, totals, mode, chunk, radix_bits, jobs, hist_cap,
+                                   bucket_cap, err);
+}
+
+void launch_init_buckets(u64* bmin, u64* bmax, u64* btot, const u64* totals, cudaStream_t st, int nsm) {
+  k_init_buckets<<<nsm * 2, 512, 0, st>>>(bmin, bmax, btot, totals);
+}
+
+void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
+                 Bufs bufs, const Job* jobs, u32 src_where, u32* hist, u64* bmin, u64* bmax, u64* btot,
+                 cudaStream_t st, int nsm) {
+  if (mode == MODE_RADIX) {
+    const size_t sm = F_MAX * 20;
+    k_hist<MODE_RADIX, F_MAX><<<nsm * 4, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs, src_where,
+                                                             hist, bmin, bmax, btot);
+  } else {
+    const size_t sm = FINE_MAX * 20;
+    k_hist<MODE_FINE, FINE_MAX><<<nsm * 2, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
+                                                               src_where, hist, bmin, bmax, btot);
+  }
+}
+
+void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32* hist, const u64* bmin,
+                 const u64* bmax, const u32* part_fstart, Seg* big_out, u32* big_cnt, u32 big_cap, Seg* fin_out,
+                 u32* fin_cnt, u32 fin_cap, u32 dst_where, Job* jobs, u64* part_off, u32* err, cudaStream_t st,
+                 int nsm) {
+  const u32 final_where = (dst_where == W_XR || dst_where == W_XS) ? dst_where : 0xFFu;
+  if (mode == MODE_SPLIT) {
+    k_scan<MODE_SPLIT><<<nsm * 2, NT_PASS, SMEM_SCAN, st>>>(segs, nseg, ls, hist, bmin, bmax, part_fstart, big_out,
+                                                            big_cnt, big_cap, fin_out, fin_cnt, fin_cap, dst_where,
+                                                            final_where, jobs, part_off, err);
+  } else {
+    k_scan<MODE_RADIX><<<nsm * 2, NT_PASS, SMEM_SCAN, st>>>(segs, nseg, ls, hist, bmin, bmax, part_fstart, big_out,
+                                                            big_cnt, big_cap, fin_out, fin_cnt, fin_cap, dst_where,
+                                                            final_where, jobs, part_off, err);
+  }
+}
+
+void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
+                    Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
+                    cudaStream_t st, int nsm) {
+  if (mode == MODE_SPLIT) {
+    k_scatter<MODE_SPLIT><<<nsm * 2, NT_PASS, SMEM_SCATTER, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
+                                                                  src_where, dst_where, hist, sp);
+  } else {
+    k_scatter<MODE_RADIX><<<nsm * 2, NT_PASS, SMEM_SCATTER, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
+                                                                  src_where, dst_where, hist, sp);
+  }
+}
+
+void launch_seg_sort(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs,
+                     u32 dst_where, u32* err, cudaStream_t st, int nsm) {
+  k_seg_sort<<<nsm, NT_SORT, SMEM_SORT, st>>>(segs, nseg, cap, work, bufs, jobs, dst_where, err);
+}
+
+void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st) {
+  k_check_empty<<<1, 32, 0, st>>>(cnt, err, flag);
+}
+
+}  // namespace mpsm

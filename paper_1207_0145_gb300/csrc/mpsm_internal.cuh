@@ -1,0 +1,235 @@
+// mpsm_internal.cuh -- device data structures and helpers shared by the MPSM kernels.
+//
+// Data layout in HBM (all tuples 16-byte {key, payload} records):
+//   xr : the R runs after phase 1, back to back (run g of job i at runs[g].off)
+//   xs : S after phase 2 (partitions back to back, tuples outside R's key range
+//        dropped) and, after phase 3, the same ranges sorted
+//   y  : ping-pong buffer of the radix passes (shared by phases 1 and 3)
+// A "segment" is a contiguous key-ordered slice still to be sorted; radix
+// passes split segments into children until they fit a thread block's shared
+// memory, where a final in-SMEM sort finishes them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mpsm {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+typedef unsigned short u16;
+
+struct __align__(16) Tuple {
+  u64 key, pay;
+};
+
+// ---------------------------------------------------------------- constants
+constexpr u32 NMAX = 8192;        // tuples one block sorts in shared memory (128 KB)
+constexpr u32 N_LEAF = 4096;      // target segment size after a radix pass
+constexpr u32 F_MIN = 16;         // smallest radix fan-out (guarantees 4 bits/pass progress)
+constexpr u32 F_MAX = 2048;       // largest radix fan-out (radix_bits <= 11)
+constexpr u32 FINE_MAX = 4096;    // largest fine histogram (fine_bits <= 12)
+constexpr u32 P_MAX = 2048;       // largest number of S partitions
+constexpr u32 RUNS_MAX = 1024;    // largest T_R per job
+constexpr u32 TILE_MAX = 4096;    // largest join tile
+constexpr u32 MAX_LEVELS = 16;    // radix passes of 4..11 bits cover any 64-bit key range
+
+// where a segment's tuples live
+enum Where : u32 { W_RIN = 0, W_SIN = 1, W_XR = 2, W_XS = 3, W_Y = 4 };
+// segment flag bits above the 3-bit `where`
+constexpr u32 SEG_EXACT = 8u;     // kmin/kmax are the exact extremes of the segment
+
+// bucket functions of a partitioning pass
+enum PassMode : u32 { MODE_RADIX = 0, MODE_FINE = 1, MODE_SPLIT = 2 };
+
+// device-side error flags (bit set)
+enum DevErr : u32 {
+  DERR_SEG_OVERFLOW = 1u,   // a work list ran out of capacity
+  DERR_SEG_TOO_BIG = 2u,    // a final segment larger than NMAX reached the SMEM sort
+  DERR_TMA_TIMEOUT = 4u,    // a bulk copy did not complete within the spin limit
+  DERR_LEVELS = 8u,         // radix levels exhausted with big segments left
+  DERR_HIST_OVERFLOW = 16u, // a pass needed more histogram entries than allocated
+  DERR_LEARN = 32u          // learned model invariant (prediction window) violated
+};
+
+struct Job {
+  const Tuple* R;
+  const Tuple* S;
+  u64 nR, nS;
+  u64 r_base, s_base;       // offsets of this job's region in xr / xs / y
+  u32 runs, run_base;       // T_R and the job's first global run index
+  u32 parts_req, part_base; // requested P; first global partition index (job * P_MAX)
+  u32 fine_bits, fine_base; // B; first global fine-bucket index (job * FINE_MAX)
+  // written on the device
+  u64 kmin, kmax;           // R's key range
+  u32 has_range;            // R non-empty
+  u32 fine_shift, nfine;    // fine bucket = (key - kmin) >> fine_shift, < nfine
+  u32 parts;                // P used
+  u64 s_kept;               // S tuples inside [kmin, kmax]
+  u64 tile_base, ntiles;    // global index of the job's first join tile; its tile count
+  u64 win_base;             // first window entry of the job (tiles * runs pairs before it)
+  u64 count, checksum;      // result
+  u64 pair_base;            // first output pair of the job (pairs mode)
+};
+
+struct Run {
+  u64 off;                  // offset in xr (and in the job's R input: off - r_base)
+  u64 len;
+};
+
+struct Seg {
+  u64 off, len;             // global offset in the buffer family of its side
+  u64 kmin, kmax;           // bounds on the keys (exact when SEG_EXACT)
+  u32 job;
+  u32 flags;                // Where | SEG_EXACT
+};
+
+// per big segment of one partitioning pass
+struct LSeg {
+  u64 lo;                   // key origin of the bucket function
+  u64 chunk_base;           // first global chunk of the segment
+  u64 hist_base;            // first histogram entry (chunks x F, chunk-major)
+  u64 bucket_base;          // first bucket-bound entry (F)
+  u32 shift, F;             // bucket = min(F-1, (key - lo) >> shift)
+  u32 nchunks, pad;
+};
+
+// pointer table of the buffers a segment may live in
+struct Bufs {
+  Tuple* xr;
+  Tuple* xs;
+  Tuple* y;
+};
+
+__device__ __forceinline__ const Tuple* seg_src(const Bufs& b, const Job* jobs, u32 where, u32 job, u64 off) {
+  switch (where) {
+    case W_RIN: return jobs[job].R + (off - jobs[job].r_base);
+    case W_SIN: return jobs[job].S + (off - jobs[job].s_base);
+    case W_XR: return b.xr + off;
+    case W_XS: return b.xs + off;
+    default: return b.y + off;
+  }
+}
+
+__host__ __device__ __forceinline__ u32 bitlen64(u64 x) {
+#if defined(__CUDA_ARCH__)
+  return 64u - (u32)__clzll((long long)x);
+#else
+  return x ? 64u - (u32)__builtin_clzll(x) : 0u;
+#endif
+}
+
+__device__ __forceinline__ u32 lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ u32 warp_id() { return threadIdx.x >> 5; }
+
+// ---------------------------------------------------------------- block scans
+// Exclusive scan of one value per thread; returns the prefix and (via *total) the block sum.
+template <typename T, int NT>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* s_warp /* >= NT/32 + 1 */) {
+  const u32 lane = lane_id(), wid = warp_id();
+  T x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= (u32)d) x += y;
+  }
+  if (lane == 31) s_warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    T w = (lane < (u32)(NT / 32)) ? s_warp[lane] : T(0);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= (u32)d) w += y;
+    }
+    if (lane < (u32)(NT / 32)) s_warp[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  const T warp_prefix = wid ? s_warp[wid - 1] : T(0);
+  const T tot = s_warp[NT / 32 - 1];
+  __syncthreads();
+  *total = tot;
+  return warp_prefix + x - v;
+}
+
+// In-place exclusive scan of n <= NT*ITEMS u32/u64 values in shared memory.
+template <typename T, int NT, int ITEMS>
+__device__ __forceinline__ T smem_exclusive_scan(T* a, u32 n, T* s_warp) {
+  T loc[ITEMS];
+  T sum = 0;
+  const u32 base = threadIdx.x * ITEMS;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const u32 k = base + i;
+    loc[i] = k < n ? a[k] : T(0);
+    sum += loc[i];
+  }
+  T total;
+  T pre = block_exclusive_scan<T, NT>(sum, &total, s_warp);
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const u32 k = base + i;
+    if (k < n) a[k] = pre;
+    pre += loc[i];
+  }
+  __syncthreads();
+  return total;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+// ---------------------------------------------------------------- bulk async copy (TMA)
+__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(u64* bar, u32 count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One elected thread: expect `bytes` and start a bulk global->shared copy.
+// dst, src 16-byte aligned; bytes a multiple of 16 and < 2^20.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, u32 bytes, u64* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Wait for phase `parity` of the barrier; gives up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity, u32 limit) {
+  const u32 a = smem_u32(bar);
+  for (u32 it = 0; it < limit; ++it) {
+    u32 done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+constexpr u32 SPIN_LIMIT = 1u << 26;
+
+// streaming 16-byte load (read once; do not keep in L2)
+__device__ __forceinline__ Tuple ld_stream(const Tuple* p) {
+  longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(p));
+  Tuple t;
+  t.key = (u64)v.x;
+  t.pay = (u64)v.y;
+  return t;
+}
+
+__device__ __forceinline__ void st_tuple(Tuple* p, const Tuple& t) {
+  *reinterpret_cast<longlong2*>(p) = make_longlong2((long long)t.key, (long long)t.pay);
+}
+
+}  // namespace mpsm

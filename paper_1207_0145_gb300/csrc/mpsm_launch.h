@@ -1,0 +1,56 @@
+// mpsm_launch.h -- host-side launchers of the MPSM kernels (one per kernel family).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mpsm_internal.cuh"
+
+namespace mpsm {
+
+// one-time kernel attribute setup (dynamic shared memory limits); call before any capture
+void init_attrs_pass();
+void init_attrs_split();
+void init_attrs_join();
+
+// ---- partitioning passes (k_pass.cu)
+void launch_sample_bounds(Seg* segs, const u32* nseg, u32 max_segs, Bufs bufs, const Job* jobs, cudaStream_t st);
+void launch_level_plan(const Seg* segs, u32* nseg, u32 seg_cap, LSeg* ls, u64* totals, u32 mode, u64 chunk,
+                       u32 radix_bits, const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err, cudaStream_t st);
+void launch_init_buckets(u64* bmin, u64* bmax, u64* btot, const u64* totals, cudaStream_t st, int nsm);
+void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
+                 Bufs bufs, const Job* jobs, u32 src_where, u32* hist, u64* bmin, u64* bmax, u64* btot,
+                 cudaStream_t st, int nsm);
+void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32* hist, const u64* bmin,
+                 const u64* bmax, const u32* part_fstart, Seg* big_out, u32* big_cnt, u32 big_cap, Seg* fin_out,
+                 u32* fin_cnt, u32 fin_cap, u32 dst_where, Job* jobs, u64* part_off, u32* err, cudaStream_t st,
+                 int nsm);
+void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
+                    Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
+                    cudaStream_t st, int nsm);
+void launch_seg_sort(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs,
+                     u32 dst_where, u32* err, cudaStream_t st, int nsm);
+void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st);
+
+// ---- splitters (k_split.cu)
+void launch_run_bounds(Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, cudaStream_t st);
+void launch_run_cdf(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, u64* rc, cudaStream_t st);
+void launch_log2_table(u16* tab, cudaStream_t st);
+void launch_splitters(Job* jobs, u32 njobs, const u64* fine_s, const u64* rc, u64* fine_r, u32* sp,
+                      u32* part_fstart, const u16* log2tab, cudaStream_t st);
+void launch_fold(const Seg* segs, const u32* nseg, const LSeg* ls_fine, const LSeg* ls_split, const u64* totals,
+                 const Job* jobs, const u32* hist_fine, const u32* part_fstart, u32* hist_split, cudaStream_t st,
+                 int nsm);
+
+// ---- join (k_join.cu)
+void launch_tiles(Job* jobs, u32 njobs, u32 tile, u64* totals, cudaStream_t st);
+void launch_search(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,
+                   const u64* totals, u32* win, cudaStream_t st, int nsm);
+void launch_join(u32 mode, Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,
+                 const u64* totals, const u32* win, u64* tile_cnt, const u64* tile_out, Tuple* pairs,
+                 u32* err, cudaStream_t st, int nsm);
+void launch_pair_offsets(Job* jobs, u32 njobs, const u64* totals, const u64* tile_cnt, u64* tile_out,
+                         u64* pair_total, cudaStream_t st);
+
+enum JoinMode : u32 { JOIN_AGG = 0, JOIN_COUNT = 1, JOIN_WRITE = 2 };
+
+}  // namespace mpsm

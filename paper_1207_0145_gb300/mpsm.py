@@ -1,0 +1,241 @@
+"""ctypes binding of libmpsm (include/mpsm.h): argument marshalling only.
+
+Every step of the join runs in the library's CUDA kernels; this module only
+passes pointers and sizes.  Tuples are [n, 2] tensors of int64 or uint64
+(key, payload) in CUDA memory, 16-byte aligned (fresh torch allocations are).
+If the compiled library is missing the import fails: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpsm.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_DEVICE, ERR_STATE = range(7)
+SPLIT_HIST, SPLIT_LEARNED = 0, 1
+SEARCH_BINARY, SEARCH_LEARNED = 0, 1
+FLAG_TIMING = 1
+
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_i32 = ctypes.c_int32
+_p = ctypes.c_void_p
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("runs_r", _u32), ("partitions_s", _u32), ("fine_bits", _u32), ("radix_bits", _u32),
+                ("join_tile", _u32), ("splitter_mode", _i32), ("search_mode", _i32), ("flags", _u32),
+                ("seed", _u64), ("reserved", _u32 * 6)]
+
+
+class Pairs(ctypes.Structure):
+    _fields_ = [("data", _p), ("capacity", _u64)]
+
+
+class JobDesc(ctypes.Structure):
+    _fields_ = [("R", _p), ("nR", _u64), ("S", _p), ("nS", _u64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("ms_sort_runs", ctypes.c_float), ("ms_splitters", ctypes.c_float), ("ms_scatter", ctypes.c_float),
+                ("ms_sort_partitions", ctypes.c_float), ("ms_search", ctypes.c_float), ("ms_join", ctypes.c_float),
+                ("ms_learn", ctypes.c_float), ("ms_total", ctypes.c_float), ("runs_r", _u32),
+                ("partitions_s", _u32), ("nfine", _u32), ("fine_shift", _u32), ("s_kept", _u64),
+                ("part_max", _u64), ("imbalance", ctypes.c_double), ("mean_window", ctypes.c_double),
+                ("tiles", _u64), ("levels_r", _u32), ("levels_s", _u32), ("segments_r", _u64),
+                ("segments_s", _u64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class View(ctypes.Structure):
+    _fields_ = [("r_runs", _p), ("run_offsets", _p), ("runs_r", _u32), ("key_min", _u64), ("key_max", _u64),
+                ("nfine", _u32), ("fine_shift", _u32), ("fine_s", _p), ("fine_r", _p), ("splitters", _p),
+                ("partitions_s", _u32), ("s_chunks", _u32), ("s_chunk_offsets", _p), ("chunk_offsets", _p),
+                ("part_offsets", _p), ("s_buffer", _p), ("s_kept", _u64), ("tiles", _u64), ("join_tile", _u32),
+                ("windows", _p)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libmpsm.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        sig = {
+            "mpsm_options_default": ([P(Options)], ctypes.c_int),
+            "mpsm_plan_create": ([P(_p), _u64, _u64, _u32, P(Options), _p], ctypes.c_int),
+            "mpsm_plan_destroy": ([_p], None),
+            "mpsm_join": ([_p, _p, _u64, _p, _u64, P(_u64), P(_u64), P(Pairs)], ctypes.c_int),
+            "mpsm_join_host": ([_p, _p, _u64, _p, _u64, P(_u64), P(_u64)], ctypes.c_int),
+            "mpsm_sort_runs": ([_p, _p, _u64], ctypes.c_int),
+            "mpsm_splitters": ([_p, _p, _u64], ctypes.c_int),
+            "mpsm_scatter": ([_p], ctypes.c_int),
+            "mpsm_sort_partitions": ([_p], ctypes.c_int),
+            "mpsm_search": ([_p], ctypes.c_int),
+            "mpsm_merge_join": ([_p, P(_u64), P(_u64), P(Pairs)], ctypes.c_int),
+            "mpsm_join_batch": ([_p, P(JobDesc), _u32, P(_u64), P(_u64)], ctypes.c_int),
+            "mpsm_plan_stats": ([_p, P(Stats)], ctypes.c_int),
+            "mpsm_plan_view": ([_p, P(View)], ctypes.c_int),
+            "mpsm_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+class MPSMError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {lib().mpsm_strerror(status).decode()} (status {status})")
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise MPSMError(rc, what)
+
+
+def _tuples(t) -> Tuple[int, int]:
+    """(device pointer, n) of an [n, 2] 64-bit tensor."""
+    if t is None:
+        return 0, 0
+    assert t.dim() == 2 and t.shape[1] == 2 and t.element_size() == 8, "tuples are [n, 2] 64-bit"
+    assert t.is_contiguous(), "tuples must be contiguous"
+    return t.data_ptr(), t.shape[0]
+
+
+def make_options(runs_r=0, partitions_s=0, fine_bits=0, radix_bits=0, join_tile=0, splitter_mode=SPLIT_HIST,
+                 search_mode=SEARCH_BINARY, timing=False, seed=20120145) -> Options:
+    o = Options()
+    lib().mpsm_options_default(ctypes.byref(o))
+    o.runs_r, o.partitions_s, o.fine_bits, o.radix_bits, o.join_tile = runs_r, partitions_s, fine_bits, radix_bits, join_tile
+    o.splitter_mode, o.search_mode = splitter_mode, search_mode
+    o.flags = FLAG_TIMING if timing else 0
+    o.seed = seed
+    return o
+
+
+class Plan:
+    """A join plan: owns the device scratch for joins up to (max_nR, max_nS)."""
+
+    def __init__(self, max_nR: int, max_nS: int, max_jobs: int = 1, stream: Optional[int] = None, **options):
+        self.options = make_options(**options)
+        h = _p()
+        _check(lib().mpsm_plan_create(ctypes.byref(h), max_nR, max_nS, max_jobs, ctypes.byref(self.options),
+                                      stream or None), "mpsm_plan_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mpsm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- whole join
+    def join(self, R, S, pairs=None) -> Tuple[int, int]:
+        """(count, checksum); `pairs` an optional [cap, 2] CUDA tensor receiving (r_payload, s_payload)."""
+        rp, nr = _tuples(R)
+        sp, ns = _tuples(S)
+        c, k = _u64(), _u64()
+        pr = None
+        if pairs is not None:
+            pp, cap = _tuples(pairs)
+            pr = Pairs(pp, cap)
+        rc = lib().mpsm_join(self.handle, rp, nr, sp, ns, ctypes.byref(c), ctypes.byref(k),
+                             ctypes.byref(pr) if pr is not None else None)
+        if rc == ERR_CAPACITY:
+            raise MPSMError(rc, f"mpsm_join needs {c.value} pairs")
+        _check(rc, "mpsm_join")
+        return c.value, k.value
+
+    def join_host(self, R_host, S_host) -> Tuple[int, int]:
+        """R_host, S_host: host tensors (pinned for speed) or numpy arrays [n, 2] of 64-bit."""
+        def ptr(a):
+            if hasattr(a, "data_ptr"):
+                return a.data_ptr(), a.shape[0]
+            return a.ctypes.data, a.shape[0]
+        rp, nr = ptr(R_host)
+        sp, ns = ptr(S_host)
+        c, k = _u64(), _u64()
+        _check(lib().mpsm_join_host(self.handle, rp, nr, sp, ns, ctypes.byref(c), ctypes.byref(k)), "mpsm_join_host")
+        return c.value, k.value
+
+    # ---- phases
+    def sort_runs(self, R):
+        rp, nr = _tuples(R)
+        _check(lib().mpsm_sort_runs(self.handle, rp, nr), "mpsm_sort_runs")
+
+    def splitters(self, S):
+        sp, ns = _tuples(S)
+        _check(lib().mpsm_splitters(self.handle, sp, ns), "mpsm_splitters")
+
+    def scatter(self):
+        _check(lib().mpsm_scatter(self.handle), "mpsm_scatter")
+
+    def sort_partitions(self):
+        _check(lib().mpsm_sort_partitions(self.handle), "mpsm_sort_partitions")
+
+    def search(self):
+        _check(lib().mpsm_search(self.handle), "mpsm_search")
+
+    def merge_join(self, pairs=None) -> Tuple[int, int]:
+        c, k = _u64(), _u64()
+        pr = None
+        if pairs is not None:
+            pp, cap = _tuples(pairs)
+            pr = Pairs(pp, cap)
+        _check(lib().mpsm_merge_join(self.handle, ctypes.byref(c), ctypes.byref(k),
+                                     ctypes.byref(pr) if pr is not None else None), "mpsm_merge_join")
+        return c.value, k.value
+
+    # ---- batched
+    def join_batch(self, jobs: Sequence[Tuple[object, object]]):
+        """jobs: sequence of (R, S) CUDA tensors -> (counts, checksums) lists."""
+        n = len(jobs)
+        arr = (JobDesc * n)()
+        for i, (R, S) in enumerate(jobs):
+            rp, nr = _tuples(R)
+            sp, ns = _tuples(S)
+            arr[i] = JobDesc(rp, nr, sp, ns)
+        counts = (_u64 * n)()
+        sums = (_u64 * n)()
+        _check(lib().mpsm_join_batch(self.handle, arr, n, counts, sums), "mpsm_join_batch")
+        return list(counts), list(sums)
+
+    # ---- introspection
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().mpsm_plan_stats(self.handle, ctypes.byref(s)), "mpsm_plan_stats")
+        return s.as_dict()
+
+    def view(self) -> View:
+        v = View()
+        _check(lib().mpsm_plan_view(self.handle, ctypes.byref(v)), "mpsm_plan_view")
+        return v
+
+
+def strerror(status: int) -> str:
+    return lib().mpsm_strerror(status).decode()
