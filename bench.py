@@ -1,0 +1,411 @@
+#!/usr/bin/env python3
+"""Benchmark: MPSM join throughput on one GB300 (or N independent replicas).
+
+One step = one whole join (phases 1-4: sort R runs, splitters + scatter of S,
+sort S partitions, search + merge join) of the configured workload, inputs
+already resident in HBM.  Metric: (|R| + |S|) / t in M tuples/s (M = 10^6 for
+rates; the workload sizes use the paper's M = 2^20).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME] [--impl ours|reference]
+
+Default workload: plain-400M-1600M, |R| = 400*2^20 unique keys (a permutation
+of a dense domain), |S| = 1600*2^20 uniform foreign keys, 16-byte tuples.  The
+inputs (33.5 GB) are far larger than L2 (129 MB), so every step streams them
+from HBM; no flush is needed.
+
+Under torchrun (N > 1) every rank joins its own replica (seed + rank): the
+units (tuples) of all ranks over the slowest rank's time give `value`
+("scaling": "weak"); the join itself has no cross-GPU exchange.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPSM join M tuples/s ((|R|+|S|)/t), % HBM roofline; learned+batched vs plain"
+UNIT = "M tuples/s"
+MEGA = 1 << 20
+
+# Algorithmic bytes per unit (one read + one write per data-moving phase):
+# partitioned side 32 (partition) + 32 (sort) + 16 (join read) per tuple kept,
+# run side 32 (sort) + 16 (join read).  Per kernel family: the bytes one launch
+# must move at the least for the units it processes.
+ALG_BYTES = {
+    "scatter_split": ("S tuples", 32),      # read S, write partitioned S (kept tuples)
+    "seg_sort": ("tuples sorted", 32),      # read a segment, write it sorted
+    "join": ("S' + R tuples", 16),          # read each kept S tuple and each R tuple once
+    "scatter_radix": ("tuples", 32),        # one radix pass: read + write
+    "hist_fine": ("S tuples", 16),          # read S
+    "hist_radix": ("tuples", 16),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="plain-400M-1600M")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=20120145)
+    ap.add_argument("--runs", type=int, default=0, help="T_R (0 = automatic)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=32, help="CPU baseline runs 1/this of the workload")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(name: str, seed: int):
+    import gen
+
+    if name not in gen.CONFIGS:
+        raise SystemExit(f"unknown config {name}; choose from {sorted(gen.CONFIGS)}")
+    return gen.CONFIGS[name](seed)
+
+
+def sample_workload(w, div: int):
+    """The same shape at 1/div of the size (the bounded CPU sample)."""
+    import gen
+
+    return gen.Workload(w.kind, max(1, w.n_r // div), max(1, w.n_s // div), w.seed, theta=w.theta,
+                        fk_share=w.fk_share)
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(os.path.join(ROOT, "paper_1207_0145_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1207_0145_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, config: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{config}_traffic.txt")
+    try:
+        vals = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("source_hash") != kernel_source_hash():
+            return None
+        return int(float(vals["dram_bytes_per_launch"]))
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(w, div: int):
+    import oracle
+
+    sw = sample_workload(w, div)
+    R, S = sw.r_host(), sw.s_host()
+    t = time.perf_counter()
+    c, k = oracle.join(R, S)
+    dt = time.perf_counter() - t
+    units = sw.n_r + sw.n_s
+    return {"value": units / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"same workload shape at 1/{div}: |R|={sw.n_r}, |S|={sw.n_s} "
+                      f"(single-threaded std::sort + merge join, {dt:.1f} s)",
+            "seconds": round(dt, 2), "result": [c, k]}
+
+
+# ------------------------------------------------------------------ reference arm
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    w = workload(args.config, args.seed)
+    div = args.cpu_sample * 2
+    sw = sample_workload(w, div)
+    R, S = sw.r_host(), sw.s_host()
+    for _ in range(args.warmup):
+        oracle.join(R, S)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.join(R, S)
+        times.append(time.perf_counter() - t)
+    units = sw.n_r + sw.n_s
+    ms = 1e3 * sum(times) / len(times)
+    value = units / (ms / 1e3) / 1e6
+    sample = f"same workload shape at 1/{div}: |R|={sw.n_r}, |S|={sw.n_s} per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.config, "n_r": w.n_r, "n_s": w.n_s, "sample_div": div},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+
+def run_ours(args):
+    import numpy as np  # noqa: F401
+    import torch
+
+    import oracle
+    from paper_1207_0145_gb300 import Plan
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = workload(args.config, args.seed + rank)
+    units = w.n_r + w.n_s
+
+    # expected result from the generator's bookkeeping, on the host, while the GPU warms up
+    expect = {}
+    th = threading.Thread(target=lambda: expect.setdefault("v", oracle.closed_form(w)), daemon=True)
+    th.start()
+
+    stream = torch.cuda.Stream(device=dev)
+    R = torch.empty((w.n_r, 2), dtype=torch.int64, device=dev)
+    S = torch.empty((w.n_s, 2), dtype=torch.int64, device=dev)
+    with torch.cuda.stream(stream):
+        w.fill_r_device(R.data_ptr(), stream.cuda_stream)
+        w.fill_s_device(S.data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+    plan = Plan(w.n_r, w.n_s, stream=stream.cuda_stream, runs_r=args.runs)
+
+    for _ in range(args.warmup):
+        got = plan.join(R, S)
+    st = plan.stats()
+    launches_per_step = st["launches"]
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    # ---- device-timed steps
+    torch.cuda.synchronize()
+    barrier()
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        results = []
+        for _ in range(args.steps):
+            results.append(plan.join(R, S))
+        e1.record(stream)
+        e1.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_units = units * ws
+    value = total_units / (ms / 1e3) / 1e6
+
+    # ---- per-kernel device time (CUDA events around every launch, separate instrumented steps)
+    plan.set_flags(kernel_timing=True)
+    kt_steps = min(3, args.steps)
+    ktimes = {}
+    for _ in range(kt_steps):
+        plan.join(R, S)
+        for name, (n, t) in plan.kernel_times().items():
+            a = ktimes.setdefault(name, [0, 0.0])
+            a[0] += n
+            a[1] += t
+    plan.set_flags(timing=True)
+    plan.join(R, S)
+    st = plan.stats()
+    plan.set_flags()
+    th.join()
+    want = expect.get("v")
+    parity = all(r == want for r in results) if want is not None else None
+
+    dom = max(ktimes.items(), key=lambda kv: kv[1][1]) if ktimes else None
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if dom:
+        name, (n, t_ms) = dom
+        per_launch_ms = t_ms / n
+        unit_name, per_unit = ALG_BYTES.get(name, ("tuples", 16))
+        if name == "scatter_split":
+            units_launch = w.n_s
+        elif name == "join":
+            units_launch = st["s_kept"] + w.n_r
+        elif name == "seg_sort":
+            units_launch = (w.n_r + st["s_kept"]) * kt_steps / n  # the two final sorts share the family
+        else:
+            units_launch = (w.n_r + w.n_s) * kt_steps / n
+        alg_bytes = per_unit * units_launch
+        achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+        traffic = recorded_traffic(name, args.config)
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                "alg_bytes_per_launch": alg_bytes, "alg_unit": f"{per_unit} B per {unit_name}",
+                "ms_per_launch": per_launch_ms}
+    alg_step = 80 * st["s_kept"] + 48 * w.n_r
+    roof_step = {"alg_bytes_per_step": alg_step, "achieved": alg_step / (ms / 1e3) / 1e9,
+                 "frac": alg_step / (ms / 1e3) / 1e9 / peak}
+
+    # ---- end to end through the host-buffer entry point (pinned memory)
+    e2e = None
+    if not args.no_e2e:
+        Rh = torch.empty((w.n_r, 2), dtype=torch.int64, pin_memory=True)
+        Sh = torch.empty((w.n_s, 2), dtype=torch.int64, pin_memory=True)
+        Rh.copy_(R)
+        Sh.copy_(S)
+        del R, S
+        torch.cuda.empty_cache()
+        plan.join_host(Rh, Sh)
+        torch.cuda.synchronize()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            plan.join_host(Rh, Sh)
+        f1.record(stream)
+        f1.synchronize()
+        barrier()
+        ems = f0.elapsed_time(f1) / args.steps
+        if dist:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": total_units / (ems / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": units * 16,
+               "d2h_bytes_per_step": 16, "ms_per_step": ems}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, args.cpu_sample)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.config, "n_r": w.n_r, "n_s": w.n_s, "tuple_bytes": 16,
+                       "runs_r": st["runs_r"], "partitions_s": st["partitions_s"],
+                       "l2": "inputs (33.5 GB at the default size) far exceed L2; no flush",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "parity": parity, "result": list(results[-1]),
+            "roofline": roof, "roofline_step": roof_step,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": launches_per_step * args.steps,
+            "phases_ms": {k: round(st[k], 3) for k in ("ms_sort_runs", "ms_splitters", "ms_scatter",
+                                                       "ms_sort_partitions", "ms_search", "ms_join", "ms_total")},
+            "kernels_ms": {k: [v[0], round(v[1] / kt_steps, 3)] for k, v in sorted(ktimes.items(),
+                                                                                  key=lambda kv: -kv[1][1])},
+            "levels": [st["levels_r"], st["levels_s"]], "imbalance": st["imbalance"],
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

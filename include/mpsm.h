@@ -57,7 +57,11 @@ enum {
 
 enum { MPSM_SPLIT_HIST = 0, MPSM_SPLIT_LEARNED = 1 };
 enum { MPSM_SEARCH_BINARY = 0, MPSM_SEARCH_LEARNED = 1 };
-enum { MPSM_FLAG_TIMING = 1u };   /* record per-phase CUDA events (read by mpsm_plan_stats) */
+enum {
+  MPSM_FLAG_TIMING = 1u,          /* record per-phase CUDA events (read by mpsm_plan_stats)        */
+  MPSM_FLAG_KERNEL_TIMING = 2u    /* record CUDA events around every kernel launch (read by
+                                     mpsm_plan_kernel_times); adds a few microseconds per launch  */
+};
 
 typedef struct {
   uint32_t runs_r;         /* T_R, runs cut from R (Sec. 2.1 "T chunks"); 0 = automatic       */
@@ -158,6 +162,8 @@ typedef struct {
   uint64_t tiles;               /* S join tiles                                              */
   uint32_t levels_r, levels_s;  /* radix levels of phase 1 / phase 3 before the final sort   */
   uint64_t segments_r, segments_s; /* final in-shared-memory sort segments                   */
+  uint32_t launches;            /* kernels launched by the last call                         */
+  uint32_t pad;
 } mpsm_stats_t;
 
 /* Statistics of the last join (job 0 of a batch).  Synchronises. */
@@ -184,6 +190,20 @@ typedef struct {
   uint32_t join_tile;              /* S tuples per tile (tile t = [t*join_tile, ...) of s_buffer) */
   const uint32_t* windows;         /* device: tiles x T_R x 2 (start, end) relative to the run    */
 } mpsm_view_t;
+
+/* Replaces the plan's MPSM_FLAG_* flags (timing on/off) for later calls. */
+int mpsm_plan_set_flags(mpsm_plan_t* plan, uint32_t flags);
+
+typedef struct {
+  char name[24];                /* kernel family, e.g. "scatter_split"                       */
+  uint32_t launches;            /* launches in the last call                                 */
+  float ms;                     /* summed device time of those launches (CUDA events)        */
+} mpsm_kernel_time_t;
+
+/* Per kernel family device time of the last call made with MPSM_FLAG_KERNEL_TIMING:
+ * writes up to cap entries (families that launched) and their number to *n.
+ * Synchronises. */
+int mpsm_plan_kernel_times(mpsm_plan_t* plan, mpsm_kernel_time_t* out, uint32_t cap, uint32_t* n);
 
 /* Device pointers into the plan's scratch after the last phase entry point
  * (valid until the next call on the plan).  Synchronises. */

@@ -208,7 +208,7 @@ OEXPORT int oracle_run_counts(const otuple* Rs, const uint64_t* run_off, uint32_
   return 0;
 }
 
-/* The bit-by-bit binary logarithm: for 1 <= m < 2^17, floor(log2(m) * 2^16),
+/* The bit-by-bit binary logarithm: for 1 <= m < 2^11, floor(log2(m) * 2^16),
  * by normalising m to x in [1, 2) and squaring 16 times, each time taking one
  * fractional bit (x >= 2 -> bit 1, halve). */
 static uint64_t log2_q16_small(uint64_t m) {
@@ -222,13 +222,13 @@ static uint64_t log2_q16_small(uint64_t m) {
   return r;
 }
 
-/* log2(n) in Q16 for the cost model: the logarithm of n's leading 17 significant
- * bits (exact below 2^17, at most 1.5 units low above), 0 for n <= 1. */
+/* log2(n) in Q16 for the cost model: the logarithm of n's leading 11 significant
+ * bits (exact below 2^11, at most log2(1 + 2^-10) ~ 0.0014 low above), 0 for n <= 1. */
 OEXPORT uint64_t oracle_log2_q16(uint64_t n) {
   if (n <= 1) return 0;
   const uint32_t k = bitlen64(n) - 1;
-  if (k <= 16) return log2_q16_small(n);
-  const uint32_t s = k - 16;
+  if (k <= 10) return log2_q16_small(n);
+  const uint32_t s = k - 10;
   return log2_q16_small(n >> s) + ((uint64_t)s << 16);
 }
 

@@ -8,6 +8,8 @@
 // whole sequence can be captured into a CUDA graph.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -37,6 +39,18 @@ struct Jobh {
   const Tuple* S;
   u64 nR, nS;
 };
+
+// kernel families for launch counting and per-kernel timing
+enum Kid {
+  K_SAMPLE, K_PLAN, K_INIT, K_HIST_RADIX, K_SCAN_RADIX, K_SCATTER_RADIX, K_SEG_SORT, K_RUN_BOUNDS, K_HIST_FINE,
+  K_RUN_CDF, K_SPLITTERS, K_FOLD, K_SCAN_SPLIT, K_SCATTER_SPLIT, K_TILES, K_SEARCH, K_JOIN, K_PAIR_OFFSETS, K_CHECK,
+  K_NUM
+};
+const char* const KNAME[K_NUM] = {"sample_bounds", "level_plan", "init_buckets", "hist_radix", "scan_radix",
+                                  "scatter_radix", "seg_sort", "run_bounds", "hist_fine", "run_cdf", "splitters",
+                                  "fold", "scan_split", "scatter_split", "tiles", "search", "join", "pair_offsets",
+                                  "check_empty"};
+constexpr u32 KT_POOL = 512;
 
 }  // namespace
 
@@ -69,7 +83,6 @@ struct mpsm_plan {
   u64 *d_fine_s = nullptr, *d_fine_min = nullptr, *d_fine_max = nullptr, *d_fine_r = nullptr, *d_rc = nullptr;
   u32 *d_sp = nullptr, *d_fstart = nullptr;
   u64* d_part_off = nullptr;
-  u16* d_log2 = nullptr;  // Q16 fractional log2 table of the splitter cost
   // join
   u32* d_win = nullptr;
   u64 win_cap = 0;
@@ -89,6 +102,11 @@ struct mpsm_plan {
   bool own_stream = false;
   cudaEvent_t ev[EV_NUM] = {};
   bool timing = false;
+  // launch counting / per-kernel timing
+  u32 launches = 0;
+  cudaEvent_t* kt_ev = nullptr;
+  u32 kt_id[KT_POOL];
+  u32 kt_n = 0;
   // batched graph
   cudaGraphExec_t gexec = nullptr;
   std::vector<u64> gsig;
@@ -173,6 +191,55 @@ Bufs bufs(const mpsm_plan* p) { return Bufs{p->xr, p->xs, p->y}; }
 void record(mpsm_plan* p, int i) {
   if (p->timing) cudaEventRecord(p->ev[i], p->st);
 }
+
+bool kernel_timing(const mpsm_plan* p) { return (p->opt.flags & MPSM_FLAG_KERNEL_TIMING) && p->kt_ev && !p->graph_mode; }
+
+void kt_begin(mpsm_plan* p, u32 id) {
+  ++p->launches;
+  if (kernel_timing(p) && p->kt_n < KT_POOL) {
+    p->kt_id[p->kt_n] = id;
+    cudaEventRecord(p->kt_ev[2 * p->kt_n], p->st);
+  }
+}
+
+void kt_end(mpsm_plan* p) {
+  if (kernel_timing(p) && p->kt_n < KT_POOL) {
+    cudaEventRecord(p->kt_ev[2 * p->kt_n + 1], p->st);
+    ++p->kt_n;
+  }
+}
+
+// MPSM_DEBUG=1 in the environment: synchronise after every launch and name the
+// kernel family that failed on stderr (diagnostics only; off by default)
+bool debug_sync() {
+  static const int on = [] {
+    const char* e = getenv("MPSM_DEBUG");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
+int debug_check(mpsm_plan* p, u32 id) {
+  if (!debug_sync() || p->graph_mode) return MPSM_OK;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "mpsm debug: kernel family %s failed: %s\n", KNAME[id], cudaGetErrorString(e));
+    return MPSM_ERR_CUDA;
+  }
+  u32 err = 0;
+  cudaMemcpy(&err, &p->d_cnt[C_ERR], sizeof(u32), cudaMemcpyDeviceToHost);
+  if (err) fprintf(stderr, "mpsm debug: device error flags 0x%x after %s\n", err, KNAME[id]);
+  return MPSM_OK;
+}
+
+#define LAUNCH(id, call)                  \
+  do {                                    \
+    kt_begin(p, id);                      \
+    call;                                 \
+    kt_end(p);                            \
+    if (debug_check(p, id)) return MPSM_ERR_CUDA; \
+  } while (0)
 
 // ---------------------------------------------------------------- per-call setup
 int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
@@ -264,6 +331,8 @@ int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
   // the host copies above read pinned memory asynchronously; keep it stable until they ran
   CK(cudaStreamSynchronize(p->st));
   p->levels_r = p->levels_s = 0;
+  p->launches = 0;
+  p->kt_n = 0;
   return MPSM_OK;
 }
 
@@ -281,23 +350,23 @@ int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels) {
     CK(cudaMemsetAsync(&p->d_cnt[C_BIG0 + (cur ^ 1)], 0, sizeof(u32), p->st));
     u64* tot = p->d_tot + T_LEVEL;
     const u32 rb = p->opt.radix_bits ? p->opt.radix_bits : 11u;
-    launch_level_plan(p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->big_cap, p->d_ls, tot, MODE_RADIX, CH_RADIX, rb,
-                      p->d_jobs, p->hist_a_cap, p->bucket_cap, &p->d_cnt[C_ERR], p->st);
-    launch_init_buckets(p->d_bmin, p->d_bmax, nullptr, tot, p->st, p->nsm);
-    launch_hist(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs, src,
-                p->d_hist_a, p->d_bmin, p->d_bmax, nullptr, p->st, p->nsm);
-    launch_scan(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, p->d_hist_a, p->d_bmin, p->d_bmax,
+    LAUNCH(K_PLAN, launch_level_plan(p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->big_cap, p->d_ls, tot, MODE_RADIX, CH_RADIX, rb,
+                      p->d_jobs, p->hist_a_cap, p->bucket_cap, &p->d_cnt[C_ERR], p->st));
+    LAUNCH(K_INIT, launch_init_buckets(p->d_bmin, p->d_bmax, nullptr, tot, p->st, p->nsm));
+    LAUNCH(K_HIST_RADIX, launch_hist(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs, src,
+                p->d_hist_a, p->d_bmin, p->d_bmax, nullptr, p->st, p->nsm));
+    LAUNCH(K_SCAN_RADIX, launch_scan(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, p->d_hist_a, p->d_bmin, p->d_bmax,
                 nullptr, p->d_big[cur ^ 1], &p->d_cnt[C_BIG0 + (cur ^ 1)], p->big_cap, p->d_fin, &p->d_cnt[C_FIN],
-                p->fin_cap, dst, p->d_jobs, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm);
-    launch_scatter(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs,
-                   src, dst, p->d_hist_a, nullptr, p->st, p->nsm);
+                p->fin_cap, dst, p->d_jobs, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm));
+    LAUNCH(K_SCATTER_RADIX, launch_scatter(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs,
+                   src, dst, p->d_hist_a, nullptr, p->st, p->nsm));
     CK(cudaGetLastError());
     src = dst;
     cur ^= 1;
     ++done;
   }
   if (p->graph_mode) {
-    launch_check_empty(&p->d_cnt[C_BIG0 + cur], &p->d_cnt[C_ERR], DERR_LEVELS, p->st);
+    LAUNCH(K_CHECK, launch_check_empty(&p->d_cnt[C_BIG0 + cur], &p->d_cnt[C_ERR], DERR_LEVELS, p->st));
   } else if (done == MAX_LEVELS) {
     CK(cudaMemcpyAsync(&p->h_cnt[C_BIG0 + cur], &p->d_cnt[C_BIG0 + cur], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
     CK(cudaStreamSynchronize(p->st));
@@ -313,8 +382,8 @@ int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels) {
 
 int final_sort(mpsm_plan* p, u32 dst_where) {
   CK(cudaMemsetAsync(&p->d_cnt[C_WORK], 0, sizeof(u32), p->st));
-  launch_seg_sort(p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, &p->d_cnt[C_WORK], bufs(p), p->d_jobs, dst_where,
-                  &p->d_cnt[C_ERR], p->st, p->nsm);
+  LAUNCH(K_SEG_SORT, launch_seg_sort(p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, &p->d_cnt[C_WORK], bufs(p), p->d_jobs, dst_where,
+                  &p->d_cnt[C_ERR], p->st, p->nsm));
   CK(cudaGetLastError());
   return MPSM_OK;
 }
@@ -323,12 +392,12 @@ int final_sort(mpsm_plan* p, u32 dst_where) {
 int phase_runs(mpsm_plan* p) {
   record(p, EV_START);
   CK(cudaMemsetAsync(&p->d_cnt[C_ERR], 0, sizeof(u32), p->st));
-  launch_sample_bounds(p->d_big[0], &p->d_cnt[C_BIG0], p->h_cnt[C_BIG0] ? p->big_cap : 0, bufs(p), p->d_jobs, p->st);
+  LAUNCH(K_SAMPLE, launch_sample_bounds(p->d_big[0], &p->d_cnt[C_BIG0], p->h_cnt[C_BIG0] ? p->big_cap : 0, bufs(p), p->d_jobs, p->st));
   int rc = run_levels(p, W_RIN, W_XR, &p->levels_r);
   if (rc) return rc;
   rc = final_sort(p, W_XR);
   if (rc) return rc;
-  launch_run_bounds(p->d_jobs, p->njobs, p->d_runs, p->xr, p->st);
+  LAUNCH(K_RUN_BOUNDS, launch_run_bounds(p->d_jobs, p->njobs, p->d_runs, p->xr, p->st));
   CK(cudaGetLastError());
   record(p, EV_RUNS);
   p->stage = ST_RUNS;
@@ -343,21 +412,21 @@ int phase_splitters(mpsm_plan* p) {
   CK(cudaMemsetAsync(p->d_fine_max, 0, (u64)nj * FINE_MAX * sizeof(u64), p->st));
   u64* tf = p->d_tot + T_FINE;
   u64* ts = p->d_tot + T_SPLIT;
-  launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls, tf, MODE_FINE, p->ch_s, 11, p->d_jobs,
-                    p->hist_b_cap, ~0ull, &p->d_cnt[C_ERR], p->st);
-  launch_hist(MODE_FINE, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls, tf, p->ch_s, bufs(p), p->d_jobs, W_SIN,
-              p->d_hist_b, p->d_fine_min, p->d_fine_max, p->d_fine_s, p->st, p->nsm);
-  launch_run_cdf(p->d_jobs, nj, p->d_runs, p->xr, p->d_rc, p->st);
-  launch_splitters(p->d_jobs, nj, p->d_fine_s, p->d_rc, p->d_fine_r, p->d_sp, p->d_fstart, p->d_log2, p->st);
-  launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls2, ts, MODE_SPLIT, p->ch_s, 11, p->d_jobs,
-                    p->hist_a_cap, ~0ull, &p->d_cnt[C_ERR], p->st);
-  launch_fold(p->d_split, &p->d_cnt[C_SPLIT], p->d_ls, p->d_ls2, tf, p->d_jobs, p->d_hist_b, p->d_fstart,
-              p->d_hist_a, p->st, p->nsm);
+  LAUNCH(K_PLAN, launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls, tf, MODE_FINE, p->ch_s, 11, p->d_jobs,
+                    p->hist_b_cap, ~0ull, &p->d_cnt[C_ERR], p->st));
+  LAUNCH(K_HIST_FINE, launch_hist(MODE_FINE, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls, tf, p->ch_s, bufs(p), p->d_jobs, W_SIN,
+              p->d_hist_b, p->d_fine_min, p->d_fine_max, p->d_fine_s, p->st, p->nsm));
+  LAUNCH(K_RUN_CDF, launch_run_cdf(p->d_jobs, nj, p->d_runs, p->xr, p->d_rc, p->st));
+  LAUNCH(K_SPLITTERS, launch_splitters(p->d_jobs, nj, p->d_fine_s, p->d_rc, p->d_fine_r, p->d_sp, p->d_fstart, &p->d_cnt[C_ERR], p->st));
+  LAUNCH(K_PLAN, launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls2, ts, MODE_SPLIT, p->ch_s, 11, p->d_jobs,
+                    p->hist_a_cap, ~0ull, &p->d_cnt[C_ERR], p->st));
+  LAUNCH(K_FOLD, launch_fold(p->d_split, &p->d_cnt[C_SPLIT], p->d_ls, p->d_ls2, tf, p->d_jobs, p->d_hist_b, p->d_fstart,
+              p->d_hist_a, p->st, p->nsm));
   CK(cudaMemsetAsync(&p->d_cnt[C_BIG0], 0, sizeof(u32), p->st));
   CK(cudaMemsetAsync(&p->d_cnt[C_FIN], 0, sizeof(u32), p->st));
-  launch_scan(MODE_SPLIT, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_hist_a, p->d_fine_min, p->d_fine_max,
+  LAUNCH(K_SCAN_SPLIT, launch_scan(MODE_SPLIT, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_hist_a, p->d_fine_min, p->d_fine_max,
               p->d_fstart, p->d_big[0], &p->d_cnt[C_BIG0], p->big_cap, p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, W_XS,
-              p->d_jobs, p->d_part_off, &p->d_cnt[C_ERR], p->st, p->nsm);
+              p->d_jobs, p->d_part_off, &p->d_cnt[C_ERR], p->st, p->nsm));
   CK(cudaGetLastError());
   record(p, EV_SPLIT);
   p->stage = ST_SPLIT;
@@ -365,8 +434,8 @@ int phase_splitters(mpsm_plan* p) {
 }
 
 int phase_scatter(mpsm_plan* p) {
-  launch_scatter(MODE_SPLIT, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_tot + T_SPLIT, p->ch_s, bufs(p),
-                 p->d_jobs, W_SIN, W_XS, p->d_hist_a, p->d_sp, p->st, p->nsm);
+  LAUNCH(K_SCATTER_SPLIT, launch_scatter(MODE_SPLIT, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_tot + T_SPLIT, p->ch_s, bufs(p),
+                 p->d_jobs, W_SIN, W_XS, p->d_hist_a, p->d_sp, p->st, p->nsm));
   CK(cudaGetLastError());
   record(p, EV_SCATTER);
   p->stage = ST_SCATTER;
@@ -384,8 +453,8 @@ int phase_sort_parts(mpsm_plan* p) {
 }
 
 int phase_search(mpsm_plan* p) {
-  launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, p->st);
-  launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win, p->st, p->nsm);
+  LAUNCH(K_TILES, launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, p->st));
+  LAUNCH(K_SEARCH, launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win, p->st, p->nsm));
   CK(cudaGetLastError());
   record(p, EV_SEARCH);
   p->stage = ST_SEARCH;
@@ -401,20 +470,20 @@ int read_err(mpsm_plan* p) {
 int phase_join(mpsm_plan* p, uint64_t* out_count, uint64_t* out_checksum, mpsm_pairs_t* pairs) {
   const u64* tot = p->d_tot + T_TILES;
   if (pairs) {
-    launch_join(JOIN_COUNT, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, tot, p->d_win, p->d_tile_cnt,
-                nullptr, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm);
-    launch_pair_offsets(p->d_jobs, p->njobs, tot, p->d_tile_cnt, p->d_tile_out, p->d_tot + T_PAIRS, p->st);
+    LAUNCH(K_JOIN, launch_join(JOIN_COUNT, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, tot, p->d_win, p->d_tile_cnt,
+                nullptr, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm));
+    LAUNCH(K_PAIR_OFFSETS, launch_pair_offsets(p->d_jobs, p->njobs, tot, p->d_tile_cnt, p->d_tile_out, p->d_tot + T_PAIRS, p->st));
     CK(cudaMemcpyAsync(p->h_scalar, p->d_tot + T_PAIRS, sizeof(u64), cudaMemcpyDeviceToHost, p->st));
     CK(cudaStreamSynchronize(p->st));
     const u64 need = p->h_scalar[0];
     if (need <= pairs->capacity && need > 0) {
       if (!pairs->data) return MPSM_ERR_INVALID_ARG;
-      launch_join(JOIN_WRITE, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, tot, p->d_win, p->d_tile_cnt,
-                  p->d_tile_out, reinterpret_cast<Tuple*>(pairs->data), &p->d_cnt[C_ERR], p->st, p->nsm);
+      LAUNCH(K_JOIN, launch_join(JOIN_WRITE, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, tot, p->d_win, p->d_tile_cnt,
+                  p->d_tile_out, reinterpret_cast<Tuple*>(pairs->data), &p->d_cnt[C_ERR], p->st, p->nsm));
     }
   } else {
-    launch_join(JOIN_AGG, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, tot, p->d_win, nullptr, nullptr,
-                nullptr, &p->d_cnt[C_ERR], p->st, p->nsm);
+    LAUNCH(K_JOIN, launch_join(JOIN_AGG, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, tot, p->d_win, nullptr, nullptr,
+                nullptr, &p->d_cnt[C_ERR], p->st, p->nsm));
   }
   CK(cudaGetLastError());
   record(p, EV_JOIN);
@@ -485,7 +554,6 @@ MPSM_API void mpsm_plan_destroy(mpsm_plan_t* p) {
   dfree(p->d_sp);
   dfree(p->d_fstart);
   dfree(p->d_part_off);
-  dfree(p->d_log2);
   dfree(p->d_win);
   dfree(p->d_tile_cnt);
   dfree(p->d_tile_out);
@@ -494,6 +562,10 @@ MPSM_API void mpsm_plan_destroy(mpsm_plan_t* p) {
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->kt_ev) {
+    for (u32 i = 0; i < 2 * KT_POOL; ++i) cudaEventDestroy(p->kt_ev[i]);
+    delete[] p->kt_ev;
+  }
   if (p->own_stream && p->st) cudaStreamDestroy(p->st);
   delete p;
 }
@@ -591,12 +663,11 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   TRY(dalloc(&p->d_fstart, (u64)max_jobs * (P_MAX + 1)));
   TRY(dalloc(&p->d_part_off, (u64)max_jobs * (P_MAX + 1)));
   TRY(halloc(&p->h_scalar, 16));
-  TRY(dalloc(&p->d_log2, 65536));
-  launch_log2_table(p->d_log2, p->st);
-  if (cudaGetLastError() != cudaSuccess) TRY(MPSM_ERR_CUDA);
-  if (p->timing)
-    for (auto& e : p->ev)
-      if (cudaEventCreate(&e) != cudaSuccess) TRY(MPSM_ERR_CUDA);
+  {
+    const u32 fl = o.flags;
+    p->opt.flags = 0;
+    TRY(mpsm_plan_set_flags(p, fl));
+  }
 #undef TRY
   *out = p;
   return MPSM_OK;
@@ -749,11 +820,11 @@ MPSM_API int mpsm_join_batch(mpsm_plan_t* p, const mpsm_job_t* jobs, uint32_t nj
     if (!prc) prc = phase_scatter(p);
     if (!prc) prc = phase_sort_parts(p);
     if (!prc) {
-      launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, p->st);
-      launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win, p->st,
-                    p->nsm);
-      launch_join(JOIN_AGG, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win,
-                  nullptr, nullptr, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm);
+      LAUNCH(K_TILES, launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, p->st));
+      LAUNCH(K_SEARCH, launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win, p->st,
+                    p->nsm));
+      LAUNCH(K_JOIN, launch_join(JOIN_AGG, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win,
+                  nullptr, nullptr, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm));
     }
     cudaError_t ce = cudaStreamEndCapture(p->st, &g);
     p->graph_mode = false;
@@ -797,6 +868,7 @@ MPSM_API int mpsm_plan_stats(mpsm_plan_t* p, mpsm_stats_t* s) {
   s->tiles = J.ntiles;
   s->levels_r = p->levels_r;
   s->levels_s = p->levels_s;
+  s->launches = p->launches;
   if (J.parts) {
     std::vector<u64> po(J.parts + 1);
     CK(cudaMemcpy(po.data(), p->d_part_off + J.part_base, (J.parts + 1) * sizeof(u64), cudaMemcpyDeviceToHost));
@@ -830,6 +902,52 @@ MPSM_API int mpsm_plan_stats(mpsm_plan_t* p, mpsm_stats_t* s) {
     s->ms_join = el(EV_SEARCH, EV_JOIN);
     s->ms_total = el(EV_START, EV_JOIN);
   }
+  return MPSM_OK;
+}
+
+MPSM_API int mpsm_plan_set_flags(mpsm_plan_t* p, uint32_t flags) {
+  if (!p) return MPSM_ERR_INVALID_ARG;
+  if (flags & ~(u32)(MPSM_FLAG_TIMING | MPSM_FLAG_KERNEL_TIMING)) return MPSM_ERR_INVALID_ARG;
+  if ((flags & MPSM_FLAG_TIMING) && !p->ev[0])
+    for (auto& e : p->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return MPSM_ERR_CUDA;
+  if ((flags & MPSM_FLAG_KERNEL_TIMING) && !p->kt_ev) {
+    p->kt_ev = new (std::nothrow) cudaEvent_t[2 * KT_POOL];
+    if (!p->kt_ev) return MPSM_ERR_OOM;
+    for (u32 i = 0; i < 2 * KT_POOL; ++i)
+      if (cudaEventCreate(&p->kt_ev[i]) != cudaSuccess) return MPSM_ERR_CUDA;
+  }
+  p->opt.flags = flags;
+  p->timing = (flags & MPSM_FLAG_TIMING) != 0;
+  return MPSM_OK;
+}
+
+MPSM_API int mpsm_plan_kernel_times(mpsm_plan_t* p, mpsm_kernel_time_t* out, uint32_t cap, uint32_t* n) {
+  if (!p || !n || (cap && !out)) return MPSM_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(p->st));
+  float ms[K_NUM] = {};
+  u32 cnt[K_NUM] = {};
+  for (u32 i = 0; i < p->kt_n; ++i) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, p->kt_ev[2 * i], p->kt_ev[2 * i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      t = 0;
+    }
+    ms[p->kt_id[i]] += t;
+    cnt[p->kt_id[i]] += 1;
+  }
+  u32 k = 0;
+  for (u32 id = 0; id < K_NUM; ++id) {
+    if (!cnt[id]) continue;
+    if (k < cap) {
+      memset(&out[k], 0, sizeof(out[k]));
+      strncpy(out[k].name, KNAME[id], sizeof(out[k].name) - 1);
+      out[k].launches = cnt[id];
+      out[k].ms = ms[id];
+    }
+    ++k;
+  }
+  *n = k;
   return MPSM_OK;
 }
 

@@ -36,10 +36,10 @@ __device__ __forceinline__ u64 lower_bound_key(const Tuple* a, u64 n, u64 key) {
   return lo;
 }
 
-// The bit-by-bit binary logarithm of 2^16 + i in Q16, fractional part only:
+// Fractional part of log2(1 + i/1024) in Q16 by the bit-by-bit method:
 // normalise to [1, 2) in Q31, square 16 times, one fractional bit per squaring.
 __device__ __forceinline__ u32 log2_frac_entry(u32 i) {
-  u64 x = (u64)(65536u + i) << 15;
+  u64 x = (u64)(1024u + i) << 21;
   u32 r = 0;
 #pragma unroll
   for (int b = 15; b >= 0; --b) {
@@ -52,20 +52,15 @@ __device__ __forceinline__ u32 log2_frac_entry(u32 i) {
   return r;
 }
 
-__global__ void k_log2_table(u16* tab) {
-  const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < 65536u) tab[i] = (u16)log2_frac_entry(i);
-}
-
-// log2(n) in Q16 from n's leading 17 significant bits (0 for n <= 1)
-__device__ __forceinline__ u64 log2_q16(u64 n, const u16* frac) {
+// log2(n) in Q16 from n's leading 11 significant bits (0 for n <= 1)
+__device__ __forceinline__ u64 log2_q16(u64 n, const u32* frac) {
   if (n <= 1) return 0;
   const u32 k = 63u - (u32)__clzll((long long)n);
-  const u32 m = (k >= 16) ? (u32)(n >> (k - 16)) : (u32)(n << (16 - k));
-  return ((u64)k << 16) + frac[m - 65536u];
+  const u32 m = (k >= 10) ? (u32)(n >> (k - 10)) : (u32)(n << (10 - k));
+  return ((u64)k << 16) + frac[m - 1024u];
 }
 
-__device__ __forceinline__ u64 part_cost(const u64* PH, const u64* PG, u32 a, u32 b, u32 T, const u16* frac) {
+__device__ __forceinline__ u64 part_cost(const u64* PH, const u64* PG, u32 a, u32 b, u32 T, const u32* frac) {
   const u64 n = PH[b] - PH[a], r = PG[b] - PG[a];
   return n * log2_q16(n, frac) + (((u64)T * n + r) << 16);
 }
@@ -138,21 +133,28 @@ __global__ void k_run_cdf(const Job* jobs, u32 njobs, const Run* runs, const Tup
 }
 
 __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s, const u64* rc, u64* fine_r, u32* sp,
-                                                    u32* part_fstart, const u16* log2tab) {
+                                                    u32* part_fstart, u32* err) {
   constexpr u32 NT = 1024;
+  // dynamic shared memory: PH, PG (u64, FINE_MAX + 1 each), frac (u32, 1024), A, B (u16, FINE_MAX + 8 each)
   extern __shared__ __align__(128) unsigned char sm_raw[];
-  u64* PH = reinterpret_cast<u64*>(sm_raw);  // FINE_MAX + 1
-  u64* PG = PH + (FINE_MAX + 1);              // FINE_MAX + 1
-  u16* A = reinterpret_cast<u16*>(PG + (FINE_MAX + 1));
+  u64* PH = reinterpret_cast<u64*>(sm_raw);
+  u64* PG = PH + (FINE_MAX + 1);
+  u32* frac = reinterpret_cast<u32*>(PG + (FINE_MAX + 1));
+  u16* A = reinterpret_cast<u16*>(frac + 1024);
   u16* B = A + (FINE_MAX + 8);
-  u16* frac = B + (FINE_MAX + 8);             // 65536-entry log2 table
+  __shared__ u64 s_red[2 * (NT / 32)];
   __shared__ u64 s_warp[NT / 32 + 1];
-  __shared__ u64 s_lo, s_hi;
+  __shared__ u64 s_lo;
+  __shared__ u64 s_hi;
   __shared__ u32 s_parts;
   const u32 job = blockIdx.x;
   const Job J = jobs[job];
   const u32 nb = J.nfine;
   const u32 tid = threadIdx.x;
+  if (nb > FINE_MAX) {
+    if (tid == 0) atomicOr(err, (u32)DERR_BOUNDS);
+    return;
+  }
   if (nb == 0) {
     if (tid == 0) {
       jobs[job].parts = 0;
@@ -162,8 +164,7 @@ __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s
   }
   const u32 P = J.parts_req < nb ? J.parts_req : nb;
   const u32 T = J.runs;
-  for (u32 i = tid; i < 65536u / 8u; i += NT)
-    reinterpret_cast<uint4*>(frac)[i] = reinterpret_cast<const uint4*>(log2tab)[i];
+  frac[tid] = log2_frac_entry(tid);  // one entry per thread: NT == 1024 entries
   const u64* rcj = rc + (u64)job * (FINE_MAX + 1);
   // per-bucket counts, then prefix sums PH, PG over nb + 1 entries
   for (u32 f = tid; f < nb; f += NT) {
@@ -174,9 +175,8 @@ __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s
     fine_r[J.fine_base + f] = r1 - r0;
   }
   __syncthreads();
-  __syncthreads();
-  // lower bound of the optimum: the largest single bucket, and the mean of the
-  // per-bucket costs over P partitions (costs only grow when buckets merge)
+  // lower bound of the optimum: the largest single bucket, and the per-bucket
+  // costs spread over P partitions (merging buckets never lowers the cost)
   u64 mx = 0, sm = 0;
   for (u32 f = tid; f < nb; f += NT) {
     const u64 n = PH[f], r = PG[f];
@@ -184,43 +184,40 @@ __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s
     mx = c > mx ? c : mx;
     sm += c;
   }
-  {
-    u64 t = mx, u = sm;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      const u64 o = __shfl_xor_sync(0xffffffffu, t, d);
-      t = o > t ? o : t;
-      u += __shfl_xor_sync(0xffffffffu, u, d);
-    }
-    __shared__ u64 s_sum[NT / 32];
-    if (lane_id() == 0) {
-      s_warp[warp_id()] = t;
-      s_sum[warp_id()] = u;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      u64 m = 0, z = 0;
-      for (u32 w = 0; w < NT / 32; ++w) {
-        m = s_warp[w] > m ? s_warp[w] : m;
-        z += s_sum[w];
-      }
-      const u64 mean = (z + P - 1) / P;
-      s_lo = m > mean ? m : mean;
-    }
-    __syncthreads();
+  for (int d = 16; d > 0; d >>= 1) {
+    const u64 o = __shfl_xor_sync(0xffffffffu, mx, d);
+    mx = o > mx ? o : mx;
+    sm += __shfl_xor_sync(0xffffffffu, sm, d);
   }
+  if (lane_id() == 0) {
+    s_red[warp_id()] = mx;
+    s_red[NT / 32 + warp_id()] = sm;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    u64 m = 0, z = 0;
+    for (u32 w = 0; w < NT / 32; ++w) {
+      m = s_red[w] > m ? s_red[w] : m;
+      z += s_red[NT / 32 + w];
+    }
+    const u64 mean = (z + P - 1) / P;
+    s_lo = m > mean ? m : mean;
+  }
+  __syncthreads();
   const u64 totH = smem_exclusive_scan<u64, NT, FINE_MAX / NT>(PH, nb, s_warp);
   const u64 totG = smem_exclusive_scan<u64, NT, FINE_MAX / NT>(PG, nb, s_warp);
   if (tid == 0) {
     PH[nb] = totH;
     PG[nb] = totG;
-    s_hi = totH * log2_q16(totH, frac) + (((u64)T * totH + totG) << 16);
-    if (s_hi < s_lo) s_hi = s_lo;
+    const u64 h = totH * log2_q16(totH, frac) + (((u64)T * totH + totG) << 16);
+    s_hi = h > s_lo ? h : s_lo;
   }
   __syncthreads();
   // bisection on the largest admissible cost C
   for (;;) {
-    const u64 lo = s_lo, hi = s_hi;
+    const u64 lo = s_lo;
+    const u64 hi = s_hi;
     const bool last = !(lo < hi);
     const u64 C = last ? lo : lo + (hi - lo) / 2;
     // greedy jump: A[a] = furthest end b with cost(a, b) <= C (>= a+1 since C >= single costs)
@@ -260,6 +257,10 @@ __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s
   if (tid == 0) {
     u32 g = 0, a = 0;
     while (a < nb) {
+      if (g >= P_MAX || A[a] <= a) {  // more groups than allowed, or no progress
+        atomicOr(err, (u32)DERR_BOUNDS);
+        break;
+      }
       fst[g++] = a;
       a = A[a];
     }
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s
   __syncthreads();
   const u32 parts = s_parts;
   for (u32 g = tid; g < parts; g += NT)
-    for (u32 f = fst[g]; f < fst[g + 1]; ++f) sp[J.fine_base + f] = g;
+    for (u32 f = fst[g]; f < fst[g + 1] && f < nb; ++f) sp[J.fine_base + f] = g;
 }
 
 // per chunk: partition histogram = sum of the chunk's fine histogram over each partition's buckets
@@ -306,8 +307,7 @@ __global__ void k_fold(const Seg* segs, const u32* nseg_ptr, const LSeg* ls_fine
   }
 }
 
-constexpr size_t SMEM_SPLITTERS =
-    2 * (FINE_MAX + 1) * sizeof(u64) + 2 * (FINE_MAX + 8) * sizeof(u16) + 65536 * sizeof(u16);
+constexpr size_t SMEM_SPLITTERS = 2 * (FINE_MAX + 1) * sizeof(u64) + 1024 * sizeof(u32) + 2 * (FINE_MAX + 8) * sizeof(u16);
 
 }  // namespace
 
@@ -323,11 +323,9 @@ void launch_run_cdf(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr
   k_run_cdf<<<dim3(64, njobs), 256, 0, st>>>(jobs, njobs, runs, xr, rc);
 }
 
-void launch_log2_table(u16* tab, cudaStream_t st) { k_log2_table<<<64, 1024, 0, st>>>(tab); }
-
 void launch_splitters(Job* jobs, u32 njobs, const u64* fine_s, const u64* rc, u64* fine_r, u32* sp,
-                      u32* part_fstart, const u16* log2tab, cudaStream_t st) {
-  k_splitters<<<njobs, 1024, SMEM_SPLITTERS, st>>>(jobs, fine_s, rc, fine_r, sp, part_fstart, log2tab);
+                      u32* part_fstart, u32* err, cudaStream_t st) {
+  k_splitters<<<njobs, 1024, SMEM_SPLITTERS, st>>>(jobs, fine_s, rc, fine_r, sp, part_fstart, err);
 }
 
 void launch_fold(const Seg* segs, const u32* nseg, const LSeg* ls_fine, const LSeg* ls_split, const u64* totals,

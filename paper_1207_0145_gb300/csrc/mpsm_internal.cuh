@@ -49,7 +49,8 @@ enum DevErr : u32 {
   DERR_TMA_TIMEOUT = 4u,    // a bulk copy did not complete within the spin limit
   DERR_LEVELS = 8u,         // radix levels exhausted with big segments left
   DERR_HIST_OVERFLOW = 16u, // a pass needed more histogram entries than allocated
-  DERR_LEARN = 32u          // learned model invariant (prediction window) violated
+  DERR_LEARN = 32u,         // learned model invariant (prediction window) violated
+  DERR_BOUNDS = 64u         // an index check inside a kernel failed (the access was skipped)
 };
 
 struct Job {

@@ -34,9 +34,8 @@ void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st);
 // ---- splitters (k_split.cu)
 void launch_run_bounds(Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, cudaStream_t st);
 void launch_run_cdf(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, u64* rc, cudaStream_t st);
-void launch_log2_table(u16* tab, cudaStream_t st);
 void launch_splitters(Job* jobs, u32 njobs, const u64* fine_s, const u64* rc, u64* fine_r, u32* sp,
-                      u32* part_fstart, const u16* log2tab, cudaStream_t st);
+                      u32* part_fstart, u32* err, cudaStream_t st);
 void launch_fold(const Seg* segs, const u32* nseg, const LSeg* ls_fine, const LSeg* ls_split, const u64* totals,
                  const Job* jobs, const u32* hist_fine, const u32* part_fstart, u32* hist_split, cudaStream_t st,
                  int nsm);

@@ -19,6 +19,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_DEVICE, ERR_STATE = ra
 SPLIT_HIST, SPLIT_LEARNED = 0, 1
 SEARCH_BINARY, SEARCH_LEARNED = 0, 1
 FLAG_TIMING = 1
+FLAG_KERNEL_TIMING = 2
 
 _u64 = ctypes.c_uint64
 _u32 = ctypes.c_uint32
@@ -47,10 +48,14 @@ class Stats(ctypes.Structure):
                 ("partitions_s", _u32), ("nfine", _u32), ("fine_shift", _u32), ("s_kept", _u64),
                 ("part_max", _u64), ("imbalance", ctypes.c_double), ("mean_window", ctypes.c_double),
                 ("tiles", _u64), ("levels_r", _u32), ("levels_s", _u32), ("segments_r", _u64),
-                ("segments_s", _u64)]
+                ("segments_s", _u64), ("launches", _u32), ("pad", _u32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", _u32), ("ms", ctypes.c_float)]
 
 
 class View(ctypes.Structure):
@@ -87,6 +92,8 @@ def lib():
             "mpsm_plan_stats": ([_p, P(Stats)], ctypes.c_int),
             "mpsm_plan_view": ([_p, P(View)], ctypes.c_int),
             "mpsm_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "mpsm_plan_set_flags": ([_p, _u32], ctypes.c_int),
+            "mpsm_plan_kernel_times": ([_p, P(KernelTime), _u32, P(_u32)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -117,12 +124,12 @@ def _tuples(t) -> Tuple[int, int]:
 
 
 def make_options(runs_r=0, partitions_s=0, fine_bits=0, radix_bits=0, join_tile=0, splitter_mode=SPLIT_HIST,
-                 search_mode=SEARCH_BINARY, timing=False, seed=20120145) -> Options:
+                 search_mode=SEARCH_BINARY, timing=False, kernel_timing=False, seed=20120145) -> Options:
     o = Options()
     lib().mpsm_options_default(ctypes.byref(o))
     o.runs_r, o.partitions_s, o.fine_bits, o.radix_bits, o.join_tile = runs_r, partitions_s, fine_bits, radix_bits, join_tile
     o.splitter_mode, o.search_mode = splitter_mode, search_mode
-    o.flags = FLAG_TIMING if timing else 0
+    o.flags = (FLAG_TIMING if timing else 0) | (FLAG_KERNEL_TIMING if kernel_timing else 0)
     o.seed = seed
     return o
 
@@ -230,6 +237,17 @@ class Plan:
         s = Stats()
         _check(lib().mpsm_plan_stats(self.handle, ctypes.byref(s)), "mpsm_plan_stats")
         return s.as_dict()
+
+    def set_flags(self, timing: bool = False, kernel_timing: bool = False):
+        flags = (FLAG_TIMING if timing else 0) | (FLAG_KERNEL_TIMING if kernel_timing else 0)
+        _check(lib().mpsm_plan_set_flags(self.handle, flags), "mpsm_plan_set_flags")
+
+    def kernel_times(self) -> dict:
+        """{family: (launches, ms)} of the last call made with kernel timing on."""
+        arr = (KernelTime * 64)()
+        n = _u32()
+        _check(lib().mpsm_plan_kernel_times(self.handle, arr, 64, ctypes.byref(n)), "mpsm_plan_kernel_times")
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].ms) for i in range(min(n.value, 64))}
 
     def view(self) -> View:
         v = View()

@@ -55,6 +55,8 @@ int main(void) {
   printf("mpsm_pairs_t %zu\n", sizeof(mpsm_pairs_t));
   F(mpsm_options_t, seed); F(mpsm_options_t, flags);
   F(mpsm_stats_t, s_kept); F(mpsm_stats_t, imbalance); F(mpsm_stats_t, tiles); F(mpsm_stats_t, segments_s);
+  F(mpsm_stats_t, launches);
+  printf("mpsm_kernel_time_t %zu\n", sizeof(mpsm_kernel_time_t));
   F(mpsm_view_t, key_min); F(mpsm_view_t, fine_s); F(mpsm_view_t, s_chunks); F(mpsm_view_t, windows);
   F(mpsm_view_t, join_tile); F(mpsm_view_t, s_kept);
   return 0;
@@ -74,6 +76,7 @@ def test_ctypes_structs_match_header(tmp_path):
     assert int(got["mpsm_view_t"]) == ctypes.sizeof(M.View)
     assert int(got["mpsm_job_t"]) == ctypes.sizeof(M.JobDesc)
     assert int(got["mpsm_pairs_t"]) == ctypes.sizeof(M.Pairs)
+    assert int(got["mpsm_kernel_time_t"]) == ctypes.sizeof(M.KernelTime)
     for key, val in got.items():
         if "." not in key:
             continue

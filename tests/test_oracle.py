@@ -216,10 +216,10 @@ def test_log2_q16_against_math():
     for n in list(range(1, 3000)) + [2 ** k for k in range(1, 63)] + [3 ** 20, (1 << 40) - 1, 12345678901]:
         exact = math.log2(n) * 65536
         got = oracle.log2_q16(n)
-        # floor of the exact value below 2^17; leading 17 significant bits above
-        slack = 1.0 if n < (1 << 17) else 2.5
+        # floor of the exact value below 2^11; leading 11 significant bits above
+        slack = 1.0 if n < (1 << 11) else 65536 * math.log2(1 + 2 ** -10) + 1.0
         assert got <= exact + 1e-6 and exact - got < slack + 1e-6, n
-        if n < (1 << 17):
+        if n < (1 << 11):
             assert got == math.floor(exact + 1e-9), n
         if n & (n - 1) == 0:
             assert got == int(math.log2(n)) * 65536
