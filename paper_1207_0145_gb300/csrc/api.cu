@@ -28,9 +28,9 @@ namespace {
 
 constexpr u64 CH_RADIX = 131072;  // tuples per chunk in the sort passes
 // counters in d_cnt
-enum { C_BIG0 = 0, C_BIG1 = 1, C_FIN = 2, C_WORK = 3, C_ERR = 4, C_SPLIT = 5, C_NUM = 8 };
+enum { C_BIG0 = 0, C_BIG1 = 1, C_FIN = 2, C_WORK = 3, C_WORK2 = 4, C_ERR = 5, C_SPLIT = 6, C_NUM = 8 };
 // totals in d_tot
-enum { T_LEVEL = 0, T_FINE = 3, T_SPLIT = 6, T_TILES = 9, T_PAIRS = 12, T_NUM = 16 };
+enum { T_LEVEL = 0, T_FINE = 3, T_SPLIT = 6, T_TILES = 9, T_PAIRS = 13, T_NUM = 16 };
 enum Stage { ST_NONE = 0, ST_RUNS, ST_SPLIT, ST_SCATTER, ST_SORTED, ST_SEARCH, ST_DONE };
 enum { EV_START = 0, EV_RUNS, EV_SPLIT, EV_SCATTER, EV_SORTS, EV_SEARCH, EV_JOIN, EV_NUM };
 
@@ -175,8 +175,10 @@ u32 auto_runs(u64 nR) {
 }
 
 u32 auto_parts(u64 nS) {
+  // phase 2's scatter fans out to P partitions and phase 3's first pass to about
+  // nS / (P * N_LEAF) buckets; P near sqrt(nS / N_LEAF) keeps both fan-outs moderate
   u64 p = 32;
-  while (p < P_MAX && p * 1536ull * 1024ull < nS) p <<= 1;
+  while (p < P_MAX && (p * 2) * (p * 2) * N_LEAF <= nS * 2) p <<= 1;
   return (u32)p;
 }
 
@@ -195,7 +197,7 @@ void record(mpsm_plan* p, int i) {
 bool kernel_timing(const mpsm_plan* p) { return (p->opt.flags & MPSM_FLAG_KERNEL_TIMING) && p->kt_ev && !p->graph_mode; }
 
 void kt_begin(mpsm_plan* p, u32 id) {
-  ++p->launches;
+  p->launches += (id == K_SEG_SORT) ? 2u : 1u;  // the final sort is two kernels (size classes)
   if (kernel_timing(p) && p->kt_n < KT_POOL) {
     p->kt_id[p->kt_n] = id;
     cudaEventRecord(p->kt_ev[2 * p->kt_n], p->st);
@@ -359,7 +361,7 @@ int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels) {
                 nullptr, p->d_big[cur ^ 1], &p->d_cnt[C_BIG0 + (cur ^ 1)], p->big_cap, p->d_fin, &p->d_cnt[C_FIN],
                 p->fin_cap, dst, p->d_jobs, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm));
     LAUNCH(K_SCATTER_RADIX, launch_scatter(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs,
-                   src, dst, p->d_hist_a, nullptr, p->st, p->nsm));
+                   src, dst, p->d_hist_a, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm));
     CK(cudaGetLastError());
     src = dst;
     cur ^= 1;
@@ -381,7 +383,7 @@ int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels) {
 }
 
 int final_sort(mpsm_plan* p, u32 dst_where) {
-  CK(cudaMemsetAsync(&p->d_cnt[C_WORK], 0, sizeof(u32), p->st));
+  CK(cudaMemsetAsync(&p->d_cnt[C_WORK], 0, 2 * sizeof(u32), p->st));  // one work counter per size class
   LAUNCH(K_SEG_SORT, launch_seg_sort(p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, &p->d_cnt[C_WORK], bufs(p), p->d_jobs, dst_where,
                   &p->d_cnt[C_ERR], p->st, p->nsm));
   CK(cudaGetLastError());
@@ -435,7 +437,7 @@ int phase_splitters(mpsm_plan* p) {
 
 int phase_scatter(mpsm_plan* p) {
   LAUNCH(K_SCATTER_SPLIT, launch_scatter(MODE_SPLIT, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_tot + T_SPLIT, p->ch_s, bufs(p),
-                 p->d_jobs, W_SIN, W_XS, p->d_hist_a, p->d_sp, p->st, p->nsm));
+                 p->d_jobs, W_SIN, W_XS, p->d_hist_a, p->d_sp, &p->d_cnt[C_ERR], p->st, p->nsm));
   CK(cudaGetLastError());
   record(p, EV_SCATTER);
   p->stage = ST_SCATTER;

@@ -19,7 +19,7 @@ namespace mpsm {
 
 namespace {
 
-constexpr u32 NT_JOIN = 256;
+constexpr u32 NT_JOIN = 512;
 
 __device__ __forceinline__ u64 lower_bound_g(const Tuple* a, u64 n, u64 key) {
   u64 lo = 0;
@@ -62,78 +62,164 @@ __device__ __forceinline__ u32 find_job(const Job* jobs, u32 njobs, u64 q, F fie
 
 __global__ void __launch_bounds__(1024) k_tiles(Job* jobs, u32 njobs, u32 tile, u64* totals) {
   __shared__ u64 s_warp[33];
-  __shared__ u64 carry[2];
-  if (threadIdx.x == 0) carry[0] = carry[1] = 0;
+  __shared__ u64 carry[3];
+  if (threadIdx.x == 0) carry[0] = carry[1] = carry[2] = 0;
   __syncthreads();
   for (u32 base = 0; base < njobs; base += 1024) {
     const u32 i = base + threadIdx.x;
-    u64 nt = 0, nw = 0;
+    u64 nt = 0, nw = 0, ns = 0;
     if (i < njobs) {
       nt = (jobs[i].s_kept + tile - 1) / tile;
       nw = nt * jobs[i].runs;
+      ns = ((nt + SEARCH_TB - 1) / SEARCH_TB) * jobs[i].runs;
     }
-    u64 t0, t1;
+    u64 t0, t1, t2;
     const u64 p0 = block_exclusive_scan<u64, 1024>(nt, &t0, s_warp);
     const u64 p1 = block_exclusive_scan<u64, 1024>(nw, &t1, s_warp);
+    const u64 p2 = block_exclusive_scan<u64, 1024>(ns, &t2, s_warp);
     if (i < njobs) {
       jobs[i].ntiles = nt;
       jobs[i].tile_base = carry[0] + p0;
       jobs[i].win_base = carry[1] + p1;
+      jobs[i].search_base = carry[2] + p2;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       carry[0] += t0;
       carry[1] += t1;
+      carry[2] += t2;
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     totals[0] = carry[0];
     totals[1] = carry[1];
+    totals[2] = carry[2];
   }
 }
 
+// first i >= from with a[i].key >= key; the answer is known to be >= from
+__device__ __forceinline__ u64 gallop_lower(const Tuple* a, u64 n, u64 from, u64 key) {
+  if (from >= n || a[from].key >= key) return from;
+  u64 lo = from, step = 1;  // a[lo].key < key
+  while (lo + step < n && a[lo + step].key < key) {
+    lo += step;
+    step <<= 1;
+  }
+  const u64 hi = (lo + step < n) ? lo + step : n;
+  return lo + 1 + lower_bound_g(a + lo + 1, hi - lo - 1, key);
+}
+
+// first i >= from with a[i].key > key; the answer is known to be >= from
+__device__ __forceinline__ u64 gallop_upper(const Tuple* a, u64 n, u64 from, u64 key) {
+  if (from >= n || a[from].key > key) return from;
+  u64 lo = from, step = 1;  // a[lo].key <= key
+  while (lo + step < n && a[lo + step].key <= key) {
+    lo += step;
+    step <<= 1;
+  }
+  const u64 hi = (lo + step < n) ? lo + step : n;
+  return lo + 1 + upper_bound_g(a + lo + 1, hi - lo - 1, key);
+}
+
+// One thread per (job, run, block of SEARCH_TB consecutive tiles): a full binary
+// search for the block's first tile, then galloping forward from the previous
+// window, since tile key ranges are increasing (Sec. 3.2.2's start search,
+// reusing each result as the next one's lower limit).
 __global__ void k_search(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,
                          const u64* totals, u32* win) {
-  const u64 nwin = totals[1];
-  for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < nwin; q += (u64)gridDim.x * blockDim.x) {
-    const u32 ji = find_job(jobs, njobs, q, [](const Job& j) { return j.win_base; });
+  const u64 nitems = totals[2];
+  for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < nitems; q += (u64)gridDim.x * blockDim.x) {
+    const u32 ji = find_job(jobs, njobs, q, [](const Job& j) { return j.search_base; });
     const Job& J = jobs[ji];
-    const u64 local = q - J.win_base;
-    const u64 t = local / J.runs;
-    const u32 j = (u32)(local - t * J.runs);
-    const u64 s0 = J.s_base + t * tile;
-    const u64 s_end = J.s_base + J.s_kept;
-    const u64 s1 = (s0 + tile < s_end ? s0 + tile : s_end) - 1;
-    const u64 klo = xs[s0].key, khi = xs[s1].key;
+    const u64 nblk = (J.ntiles + SEARCH_TB - 1) / SEARCH_TB;
+    const u64 local = q - J.search_base;
+    const u32 j = (u32)(local / nblk);
+    const u64 k = local - (u64)j * nblk;
+    const u64 t0 = k * SEARCH_TB;
+    const u64 t1 = (t0 + SEARCH_TB < J.ntiles) ? t0 + SEARCH_TB : J.ntiles;
     const Run r = runs[J.run_base + j];
-    const u64 lb = lower_bound_g(xr + r.off, r.len, klo);
-    const u64 ub = lb + upper_bound_g(xr + r.off + lb, r.len - lb, khi);
-    win[2 * q] = (u32)lb;
-    win[2 * q + 1] = (u32)ub;
+    const Tuple* a = xr + r.off;
+    const u64 s_end = J.s_base + J.s_kept;
+    u64 lb = 0;
+    for (u64 t = t0; t < t1; ++t) {
+      const u64 s0 = J.s_base + t * tile;
+      const u64 s1 = (s0 + tile < s_end ? s0 + tile : s_end) - 1;
+      const u64 klo = xs[s0].key, khi = xs[s1].key;
+      lb = (t == t0) ? lower_bound_g(a, r.len, klo) : gallop_lower(a, r.len, lb, klo);
+      const u64 ub = gallop_upper(a, r.len, lb, khi);
+      const u64 w = J.win_base + t * J.runs + j;
+      win[2 * w] = (u32)lb;
+      win[2 * w + 1] = (u32)ub;
+    }
   }
 }
 
+// first index in [lb, n) whose key differs from `key` (keys[lb] == key): a short
+// forward scan, four independent probes at a time, then binary search for long runs
+__device__ __forceinline__ u32 equal_run_end(const u64* keys, u32 n, u32 lb, u64 key) {
+  u32 ub = lb + 1;
+#pragma unroll
+  for (int rep = 0; rep < 2; ++rep) {
+    const bool m0 = ub < n && keys[ub] == key;
+    const bool m1 = ub + 1 < n && keys[ub + 1] == key;
+    const bool m2 = ub + 2 < n && keys[ub + 2] == key;
+    const bool m3 = ub + 3 < n && keys[ub + 3] == key;
+    if (!m0) return ub;
+    if (!m1) return ub + 1;
+    if (!m2) return ub + 2;
+    if (!m3) return ub + 3;
+    ub += 4;
+  }
+  u32 m = n - ub;  // long run of equal keys: binary search for its end
+  while (m > 0) {
+    const u32 h = m >> 1;
+    if (keys[ub + h] <= key) {
+      ub += h + 1;
+      m -= h + 1;
+    } else {
+      m = h;
+    }
+  }
+  return ub;
+}
+
+__device__ __forceinline__ u32 lower_bound_s(const u64* keys, u32 n, u64 key) {
+  u32 a = 0, m = n;
+  while (m > 0) {
+    const u32 h = m >> 1;
+    if (keys[a + h] < key) {
+      a += h + 1;
+      m -= h + 1;
+    } else {
+      m = h;
+    }
+  }
+  return a;
+}
+
+// One S tile per iteration: keys and inclusive payload prefix sums in shared
+// memory (structure of arrays), then every R tuple of the tile's run windows
+// looks up its equal-key range [lb, ub) in the tile.
 template <u32 MODE>
-__global__ void __launch_bounds__(NT_JOIN) k_join(Job* jobs, u32 njobs, const Run* runs, const Tuple* xr,
-                                                  const Tuple* xs, u32 tile, const u64* totals, const u32* win,
-                                                  u64* tile_cnt, const u64* tile_out, Tuple* pairs, u32* err) {
+__global__ void __launch_bounds__(NT_JOIN, 2) k_join(Job* jobs, u32 njobs, const Run* runs, const Tuple* xr,
+                                                     const Tuple* xs, u32 tile, const u64* totals, const u32* win,
+                                                     u64* tile_cnt, const u64* tile_out, Tuple* pairs, u32* err) {
+  constexpr u32 IT = TILE_MAX / NT_JOIN;  // 8
+  constexpr u32 NW = NT_JOIN / 32;
   extern __shared__ __align__(128) unsigned char sm_raw[];
-  Tuple* tup = reinterpret_cast<Tuple*>(sm_raw);                 // TILE_MAX: key, payload prefix sum
-  u64* roff = reinterpret_cast<u64*>(tup + TILE_MAX);            // RUNS_MAX
-  u32* wl = reinterpret_cast<u32*>(roff + RUNS_MAX);             // RUNS_MAX window starts
-  u32* wpre = wl + RUNS_MAX;                                     // RUNS_MAX + 1 window prefix
-  __shared__ __align__(8) u64 mbar;
-  __shared__ u64 s_warp[NT_JOIN / 32 + 1];
-  __shared__ u32 s_warp32[NT_JOIN / 32 + 1];
+  u64* keys = reinterpret_cast<u64*>(sm_raw);          // TILE_MAX
+  u64* psum = keys + TILE_MAX;                         // TILE_MAX inclusive prefix sums of payloads
+  u64* roff = psum + TILE_MAX;                         // RUNS_MAX
+  u32* wl = reinterpret_cast<u32*>(roff + RUNS_MAX);   // RUNS_MAX window starts
+  u32* wpre = wl + RUNS_MAX;                           // RUNS_MAX + 1 window prefix
+  u16* dir = reinterpret_cast<u16*>(wpre + RUNS_MAX + 1);  // TILE_MAX + 1 bucket starts
+  __shared__ u64 s_warp[NW + 1];
+  __shared__ u32 s_warp32[NW + 1];
   __shared__ u32 s_job;
-  const u32 tid = threadIdx.x;
-  if (tid == 0) mbar_init(&mbar, 1);
-  __syncthreads();
-  u32 phase = 0;
+  const u32 tid = threadIdx.x, lane = lane_id(), wid = warp_id();
   const u64 ntiles = totals[0];
   for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (tid == 0) s_job = find_job(jobs, njobs, t, [](const Job& j) { return j.tile_base; });
     __syncthreads();
     const u32 ji = s_job;
@@ -142,8 +228,13 @@ __global__ void __launch_bounds__(NT_JOIN) k_join(Job* jobs, u32 njobs, const Ru
     const u64 s0 = lt * tile;
     const u32 n = (u32)((J.s_kept - s0) < tile ? (J.s_kept - s0) : tile);
     const u32 nruns = J.runs;
-    if (tid == 0) tma_load_1d(tup, xs + J.s_base + s0, n * (u32)sizeof(Tuple), &mbar);
-    // windows of this tile, one per run
+    const Tuple* stile = xs + J.s_base + s0;
+    Tuple v[IT];
+#pragma unroll
+    for (u32 i = 0; i < IT; ++i) {
+      const u32 k = i * NT_JOIN + tid;
+      if (k < n) v[i] = ld_stream(stile + k);
+    }
     const u32* w = win + 2 * (J.win_base + lt * nruns);
     for (u32 j = tid; j < nruns; j += NT_JOIN) {
       const u32 a = w[2 * j], b = w[2 * j + 1];
@@ -151,123 +242,153 @@ __global__ void __launch_bounds__(NT_JOIN) k_join(Job* jobs, u32 njobs, const Ru
       wpre[j] = b - a;
       roff[j] = runs[J.run_base + j].off;
     }
-    const bool ok = mbar_wait(&mbar, phase, SPIN_LIMIT);
-    phase ^= 1u;
-    if (!__syncthreads_and(ok)) {
-      if (tid == 0) atomicOr(err, (u32)DERR_TMA_TIMEOUT);
-      return;
+#pragma unroll
+    for (u32 i = 0; i < IT; ++i) {
+      const u32 k = i * NT_JOIN + tid;
+      if (k < n) {
+        keys[k] = v[i].key;
+        psum[k] = v[i].pay;
+      }
     }
-    // payloads -> inclusive prefix sums (mod 2^64): warp w scans tuples
-    // [w*512, (w+1)*512) 32 at a time (conflict-free), then warp offsets are added
+    __syncthreads();
+    // inclusive prefix sums (mod 2^64): warp w scans entries [w*PERW, (w+1)*PERW)
     {
-      constexpr u32 PERW = TILE_MAX / (NT_JOIN / 32);
-      const u32 wid = warp_id(), lane = lane_id();
+      constexpr u32 PERW = TILE_MAX / NW;
       u64 carry = 0;
-#pragma unroll 4
+#pragma unroll
       for (u32 i = 0; i < PERW / 32; ++i) {
         const u32 k = wid * PERW + i * 32 + lane;
-        u64 v = k < n ? tup[k].pay : 0ull;
+        u64 x = k < n ? psum[k] : 0ull;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-          const u64 y = __shfl_up_sync(0xffffffffu, v, d);
-          if (lane >= (u32)d) v += y;
+          const u64 y = __shfl_up_sync(0xffffffffu, x, d);
+          if (lane >= (u32)d) x += y;
         }
-        v += carry;
-        if (k < n) tup[k].pay = v;
-        carry = __shfl_sync(0xffffffffu, v, 31);
+        x += carry;
+        if (k < n) psum[k] = x;
+        carry = __shfl_sync(0xffffffffu, x, 31);
       }
       if (lane == 0) s_warp[wid] = carry;
       __syncthreads();
       u64 add = 0;
       for (u32 w2 = 0; w2 < wid; ++w2) add += s_warp[w2];
       if (add) {
+#pragma unroll
         for (u32 i = 0; i < PERW / 32; ++i) {
           const u32 k = wid * PERW + i * 32 + lane;
-          if (k < n) tup[k].pay += add;
+          if (k < n) psum[k] += add;
         }
       }
-      __syncthreads();
     }
-    const u32 W = smem_exclusive_scan<u32, NT_JOIN, RUNS_MAX / NT_JOIN>(wpre, nruns, s_warp32);
+    // order-preserving bucket directory over the tile's key range: bucket i of
+    // (key - kmin) >> dsh starts at dir[i]; dir[nbk] = n
+    const u64 kmin = keys[0], kmax = keys[n - 1];
+    const u32 rbits = bitlen64(kmax - kmin);
+    const u32 dsh = rbits > 12u ? rbits - 12u : 0u;
+    const u32 nbk = (u32)((kmax - kmin) >> dsh) + 1u;
+#pragma unroll
+    for (u32 i = 0; i < IT; ++i) {
+      const u32 k = i * NT_JOIN + tid;
+      if (k < n) {
+        const u32 b = (u32)((keys[k] - kmin) >> dsh);
+        const u32 bp = k ? (u32)((keys[k - 1] - kmin) >> dsh) : 0u;
+        for (u32 x = (k ? bp + 1u : 0u); x <= b; ++x) dir[x] = (u16)k;
+        if (k == n - 1)
+          for (u32 x = b + 1u; x <= nbk; ++x) dir[x] = (u16)n;
+      }
+    }
+    const u32 W = smem_exclusive_scan<u32, NT_JOIN, (RUNS_MAX + NT_JOIN - 1) / NT_JOIN>(wpre, nruns, s_warp32);
     if (tid == 0) wpre[nruns] = W;
     __syncthreads();
     u64 cnt = 0, chk = 0;
-    u64 out_pos = 0;
-    if (MODE == JOIN_WRITE) out_pos = J.pair_base + tile_out[t];
-    const u32 rounds = (W + NT_JOIN - 1) / NT_JOIN;
-    for (u32 rd = 0; rd < rounds; ++rd) {
-      const u32 q = rd * NT_JOIN + tid;
-      u32 lb = 0, ub = 0;
-      Tuple r{0, 0};
-      if (q < W) {
-        u32 lo = 0, hi = nruns;  // run j: last with wpre[j] <= q
-        while (hi - lo > 1) {
-          const u32 mid = (lo + hi) >> 1;
-          if (wpre[mid] <= q) lo = mid; else hi = mid;
-        }
-        const u64 pos = roff[lo] + wl[lo] + (q - wpre[lo]);
-        r = ld_stream(xr + pos);
-        // equal-key range of r.key in the tile
-        u32 a = 0, m = n;
-        while (m > 0) {
-          const u32 h = m >> 1;
-          if (tup[a + h].key < r.key) {
-            a += h + 1;
-            m -= h + 1;
-          } else {
-            m = h;
+    if (MODE != JOIN_WRITE) {
+      constexpr u32 U = 4;  // R loads in flight per thread before the tile lookups
+      for (u32 q0 = 0; q0 < W; q0 += NT_JOIN * U) {
+        Tuple r[U];
+#pragma unroll
+        for (u32 u = 0; u < U; ++u) {
+          const u32 q = q0 + u * NT_JOIN + tid;
+          r[u].key = 0;
+          r[u].pay = 0;
+          if (q < W) {
+            u32 lo = 0, hi = nruns;  // run j: last with wpre[j] <= q
+            while (hi - lo > 1) {
+              const u32 mid = (lo + hi) >> 1;
+              if (wpre[mid] <= q) lo = mid; else hi = mid;
+            }
+            r[u] = ld_stream(xr + roff[lo] + wl[lo] + (q - wpre[lo]));
           }
         }
-        lb = a;
-        m = n - a;
-        while (m > 0) {
-          const u32 h = m >> 1;
-          if (tup[a + h].key <= r.key) {
-            a += h + 1;
-            m -= h + 1;
-          } else {
-            m = h;
+#pragma unroll
+        for (u32 u = 0; u < U; ++u) {
+          const u32 q = q0 + u * NT_JOIN + tid;
+          if (q >= W) continue;
+          const u64 key = r[u].key;
+          if (key < kmin || key > kmax) continue;
+          const u32 bi = (u32)((key - kmin) >> dsh);
+          u32 lb = dir[bi], ub = dir[bi + 1];
+          if (dsh) {  // a bucket spans several keys: narrow [lb, ub) to `key`
+            lb += lower_bound_s(keys + lb, ub - lb, key);
+            if (lb >= ub || keys[lb] != key) continue;
+            ub = equal_run_end(keys, ub, lb, key);
           }
-        }
-        ub = a;
-        const u64 c = ub - lb;
-        if (c) {
-          const u64 ps_ub = tup[ub - 1].pay;
-          const u64 ps_lb = lb ? tup[lb - 1].pay : 0ull;
+          if (lb >= ub) continue;
+          const u64 c = ub - lb;
           cnt += c;
-          chk += c * r.pay + (ps_ub - ps_lb);
+          chk += c * r[u].pay + (psum[ub - 1] - (lb ? psum[lb - 1] : 0ull));
         }
       }
-      if (MODE == JOIN_WRITE) {
+    } else {
+      u64 out_pos = J.pair_base + tile_out[t];
+      const u32 rounds = (W + NT_JOIN - 1) / NT_JOIN;
+      for (u32 rd = 0; rd < rounds; ++rd) {
+        const u32 q = rd * NT_JOIN + tid;
+        u32 lb = 0, ub = 0;
+        Tuple r{0, 0};
+        if (q < W) {
+          u32 lo = 0, hi = nruns;
+          while (hi - lo > 1) {
+            const u32 mid = (lo + hi) >> 1;
+            if (wpre[mid] <= q) lo = mid; else hi = mid;
+          }
+          r = ld_stream(xr + roff[lo] + wl[lo] + (q - wpre[lo]));
+          if (r.key >= kmin && r.key <= kmax) {
+            const u32 bi = (u32)((r.key - kmin) >> dsh);
+            lb = dir[bi];
+            ub = dir[bi + 1];
+            if (dsh) {
+              lb += lower_bound_s(keys + lb, ub - lb, r.key);
+              ub = (lb < ub && keys[lb] == r.key) ? equal_run_end(keys, ub, lb, r.key) : lb;
+            }
+          }
+        }
         u32 tot;
         const u32 pre = block_exclusive_scan<u32, NT_JOIN>(ub - lb, &tot, s_warp32);
         Tuple* o = pairs + out_pos + pre;
         for (u32 i = lb; i < ub; ++i) {
-          const u64 sp = tup[i].pay - (i ? tup[i - 1].pay : 0ull);
+          const u64 sp = psum[i] - (i ? psum[i - 1] : 0ull);
           st_tuple(o + (i - lb), Tuple{r.pay, sp});
         }
         out_pos += tot;
       }
     }
-    cnt = warp_sum(cnt);
-    chk = warp_sum(chk);
-    if (lane_id() == 0) {
-      s_warp[warp_id()] = cnt;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      u64 c = 0;
-      for (u32 i = 0; i < NT_JOIN / 32; ++i) c += s_warp[i];
-      cnt = c;
-    }
-    __syncthreads();
-    if (lane_id() == 0) s_warp[warp_id()] = chk;
-    __syncthreads();
-    if (tid == 0) {
-      u64 k = 0;
-      for (u32 i = 0; i < NT_JOIN / 32; ++i) k += s_warp[i];
-      if (MODE == JOIN_COUNT) tile_cnt[t] = cnt;
-      if (MODE != JOIN_WRITE) {
+    if (MODE != JOIN_WRITE) {
+      cnt = warp_sum(cnt);
+      chk = warp_sum(chk);
+      if (lane == 0) s_warp[wid] = cnt;
+      __syncthreads();
+      if (tid == 0) {
+        u64 c = 0;
+        for (u32 i = 0; i < NW; ++i) c += s_warp[i];
+        cnt = c;
+      }
+      __syncthreads();
+      if (lane == 0) s_warp[wid] = chk;
+      __syncthreads();
+      if (tid == 0) {
+        u64 k = 0;
+        for (u32 i = 0; i < NW; ++i) k += s_warp[i];
+        if (MODE == JOIN_COUNT) tile_cnt[t] = cnt;
         atomicAdd(&jobs[ji].count, cnt);
         atomicAdd(&jobs[ji].checksum, k);
       }
@@ -300,7 +421,8 @@ __global__ void __launch_bounds__(1024) k_pair_offsets(Job* jobs, u32 njobs, con
   }
 }
 
-constexpr size_t SMEM_JOIN = TILE_MAX * sizeof(Tuple) + RUNS_MAX * sizeof(u64) + (2 * RUNS_MAX + 1) * sizeof(u32);
+constexpr size_t SMEM_JOIN = 2 * TILE_MAX * sizeof(u64) + RUNS_MAX * sizeof(u64) + (2 * RUNS_MAX + 1) * sizeof(u32) +
+                             (TILE_MAX + 8) * sizeof(u16);
 
 }  // namespace
 
@@ -308,6 +430,9 @@ void init_attrs_join() {
   cudaFuncSetAttribute(k_join<JOIN_AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_JOIN);
   cudaFuncSetAttribute(k_join<JOIN_COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_JOIN);
   cudaFuncSetAttribute(k_join<JOIN_WRITE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_JOIN);
+  cudaFuncSetAttribute(k_join<JOIN_AGG>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaFuncSetAttribute(k_join<JOIN_COUNT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaFuncSetAttribute(k_join<JOIN_WRITE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 void launch_tiles(Job* jobs, u32 njobs, u32 tile, u64* totals, cudaStream_t st) {
@@ -322,7 +447,7 @@ void launch_search(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr,
 void launch_join(u32 mode, Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,
                  const u64* totals, const u32* win, u64* tile_cnt, const u64* tile_out, Tuple* pairs, u32* err,
                  cudaStream_t st, int nsm) {
-  const int grid = nsm * 3;
+  const int grid = nsm * 2;
   if (mode == JOIN_AGG) {
     k_join<JOIN_AGG><<<grid, NT_JOIN, SMEM_JOIN, st>>>(jobs, njobs, runs, xr, xs, tile, totals, win, tile_cnt,
                                                        tile_out, pairs, err);

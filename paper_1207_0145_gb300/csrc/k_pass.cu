@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
   u64* bkmax = bkmin + F_MAX;                   // F_MAX
   __shared__ u64 s_warp[NT_PASS / 32 + 1];
   const u32 nseg = *nseg_ptr;
-  constexpr u64 HALF = NMAX / 2;
+  constexpr u64 HALF = NMAX / 4;  // packed groups stay <= NMAX/2 (the two-blocks-per-SM sort class)
   for (u32 s = blockIdx.x; s < nseg; s += gridDim.x) {
     const LSeg L = ls[s];
     const Seg S = segs[s];
@@ -299,8 +299,8 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
       for (u32 b = threadIdx.x; b <= F; b += NT_PASS) part_off[J.part_base + b] = start[b];
       if (threadIdx.x == 0) jobs[S.job].s_kept = total;
     }
-    // children: buckets of at most NMAX/2 tuples whose starts share a NMAX/2 window
-    // are packed into one final segment (<= NMAX); larger ones stand alone.
+    // children: buckets of at most NMAX/4 tuples whose starts share a NMAX/4 window
+    // are packed into one final segment (<= NMAX/2); larger ones stand alone.
     for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
       const u64 st = start[b], len = start[b + 1] - st;
       const bool pk = len <= HALF;
@@ -345,10 +345,17 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
 }
 
 // ---------------------------------------------------------------- scatter
+// Per chunk (worker): tiles of SC_TILE tuples arrive by bulk async copy into
+// shared memory (two blocks per SM, so one block's copy overlaps the other's
+// work).  Each tuple gets
+// (bucket, rank) from a shared-memory counter; an exclusive scan gives the
+// tile's bucket starts; a permutation index orders the tile by bucket so the
+// write-out stores runs of consecutive destinations (coalesced 16-byte stores).
 template <u32 MODE>
-__global__ void __launch_bounds__(NT_PASS) k_scatter(const Seg* segs, const u32* nseg_ptr, const LSeg* ls,
-                                                     const u64* totals, u64 chunk, Bufs bufs, const Job* jobs,
-                                                     u32 src_where, u32 dst_where, const u32* hist, const u32* sp) {
+__global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u32* nseg_ptr, const LSeg* ls,
+                                                        const u64* totals, u64 chunk, Bufs bufs, const Job* jobs,
+                                                        u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
+                                                        u32* err) {
   constexpr u32 IT = SC_TILE / NT_PASS;
   constexpr u32 DROP = 0xFFFFFFFFu;
   extern __shared__ __align__(128) unsigned char sm_raw[];
@@ -356,22 +363,28 @@ __global__ void __launch_bounds__(NT_PASS) k_scatter(const Seg* segs, const u32*
   u32* hcnt = reinterpret_cast<u32*>(stage + SC_TILE);             // F_MAX
   u32* hb = hcnt + F_MAX;                                          // F_MAX
   u32* cur = hb + F_MAX;                                           // F_MAX
-  u16* sb = reinterpret_cast<u16*>(cur + F_MAX);                   // SC_TILE
+  u16* sidx = reinterpret_cast<u16*>(cur + F_MAX);                 // SC_TILE
+  u16* sb = sidx + SC_TILE;                                        // SC_TILE
   u16* spl = sb + SC_TILE;                                         // FINE_MAX (MODE_SPLIT)
+  __shared__ __align__(8) u64 mbar;
   __shared__ u32 s_seg;
   __shared__ u32 s_warp[NT_PASS / 32 + 1];
+  const u32 tid = threadIdx.x;
+  if (tid == 0) mbar_init(&mbar, 1);
+  __syncthreads();
+  u32 phase = 0;
   const u64 nch = totals[0];
   const u32 nseg = *nseg_ptr;
   Tuple* dbase = dst_where == W_XR ? bufs.xr : (dst_where == W_XS ? bufs.xs : bufs.y);
   for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
-    if (threadIdx.x == 0) s_seg = find_seg(ls, nseg, c);
+    if (tid == 0) s_seg = find_seg(ls, nseg, c);
     __syncthreads();
     const LSeg L = ls[s_seg];
     const Seg S = segs[s_seg];
     const u32 F = L.F;
     const u64 ci = c - L.chunk_base;
     const u32* orow = hist + L.hist_base + ci * F;
-    for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
+    for (u32 b = tid; b < F; b += NT_PASS) {
       cur[b] = orow[b];
       hcnt[b] = 0;
     }
@@ -380,38 +393,42 @@ __global__ void __launch_bounds__(NT_PASS) k_scatter(const Seg* segs, const u32*
       const Job& J = jobs[S.job];
       kmin = J.kmin;
       kmax = J.kmax;
-      for (u32 f = threadIdx.x; f < J.nfine; f += NT_PASS) spl[f] = (u16)sp[J.fine_base + f];
+      for (u32 f = tid; f < J.nfine; f += NT_PASS) spl[f] = (u16)sp[J.fine_base + f];
     }
-    __syncthreads();
     const u64 a = ci * chunk;
     const u64 e = (a + chunk < S.len) ? a + chunk : S.len;
     const Tuple* src = seg_src(bufs, jobs, src_where, S.job, S.off);
     Tuple* dst = dbase + S.off;
-    for (u64 t0 = a; t0 < e; t0 += SC_TILE) {
-      Tuple v[IT];
-      u32 bk[IT], rk[IT];
-#pragma unroll
-      for (u32 i = 0; i < IT; ++i) {
-        const u64 t = t0 + i * NT_PASS + threadIdx.x;
-        bk[i] = DROP;
-        rk[i] = 0;
-        if (t < e) v[i] = ld_stream(src + t);
+    const u32 ntile = (u32)((e - a + SC_TILE - 1) / SC_TILE);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    for (u32 k = 0; k < ntile; ++k) {
+      const u64 t0 = a + (u64)k * SC_TILE;
+      const u32 n = (u32)((e - t0) < SC_TILE ? (e - t0) : SC_TILE);
+      if (tid == 0) tma_load_1d(stage, src + t0, n * (u32)sizeof(Tuple), &mbar);
+      const bool ok = mbar_wait(&mbar, phase, SPIN_LIMIT);
+      phase ^= 1u;
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicOr(err, (u32)DERR_TMA_TIMEOUT);
+        return;
       }
+      const Tuple* T = stage;
+      u32 br[IT];
 #pragma unroll
       for (u32 i = 0; i < IT; ++i) {
-        const u64 t = t0 + i * NT_PASS + threadIdx.x;
-        if (t >= e) continue;
-        const u64 k = v[i].key;
+        const u32 x = i * NT_PASS + tid;
+        br[i] = DROP;
+        if (x >= n) continue;
+        const u64 key = T[x].key;
         u32 b;
         if (MODE == MODE_RADIX) {
-          const u64 d = k < L.lo ? 0ull : (k - L.lo) >> L.shift;
+          const u64 d = key < L.lo ? 0ull : (key - L.lo) >> L.shift;
           b = d >= F ? F - 1u : (u32)d;
         } else {
-          if (k < kmin || k > kmax) continue;
-          b = spl[(k - kmin) >> L.shift];
+          if (key < kmin || key > kmax) continue;
+          b = spl[(key - kmin) >> L.shift];
         }
-        bk[i] = b;
-        rk[i] = atomicAdd(&hcnt[b], 1u);
+        br[i] = (b << 16) | atomicAdd(&hcnt[b], 1u);
       }
       __syncthreads();
       // hb = exclusive scan of hcnt
@@ -420,7 +437,7 @@ __global__ void __launch_bounds__(NT_PASS) k_scatter(const Seg* segs, const u32*
         u32 loc[PER], sum = 0;
 #pragma unroll
         for (u32 i = 0; i < PER; ++i) {
-          const u32 b = threadIdx.x * PER + i;
+          const u32 b = tid * PER + i;
           loc[i] = b < F ? hcnt[b] : 0u;
           sum += loc[i];
         }
@@ -428,7 +445,7 @@ __global__ void __launch_bounds__(NT_PASS) k_scatter(const Seg* segs, const u32*
         u32 pre = block_exclusive_scan<u32, NT_PASS>(sum, &tot, s_warp);
 #pragma unroll
         for (u32 i = 0; i < PER; ++i) {
-          const u32 b = threadIdx.x * PER + i;
+          const u32 b = tid * PER + i;
           if (b < F) hb[b] = pre;
           pre += loc[i];
         }
@@ -436,19 +453,21 @@ __global__ void __launch_bounds__(NT_PASS) k_scatter(const Seg* segs, const u32*
       __syncthreads();
 #pragma unroll
       for (u32 i = 0; i < IT; ++i) {
-        if (bk[i] == DROP) continue;
-        const u32 p = hb[bk[i]] + rk[i];
-        stage[p] = v[i];
-        sb[p] = (u16)bk[i];
+        if (br[i] == DROP) continue;
+        const u32 b = br[i] >> 16;
+        const u32 p = hb[b] + (br[i] & 0xFFFFu);
+        sidx[p] = (u16)(i * NT_PASS + tid);
+        sb[p] = (u16)b;
       }
       __syncthreads();
       const u32 kept = hb[F - 1] + hcnt[F - 1];
-      for (u32 p = threadIdx.x; p < kept; p += NT_PASS) {
+      for (u32 p = tid; p < kept; p += NT_PASS) {
         const u32 b = sb[p];
-        st_tuple(dst + cur[b] + (p - hb[b]), stage[p]);
+        st_tuple(dst + cur[b] + (p - hb[b]), T[sidx[p]]);
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
-      for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
+      for (u32 b = tid; b < F; b += NT_PASS) {
         cur[b] += hcnt[b];
         hcnt[b] = 0;
       }
@@ -458,14 +477,25 @@ __global__ void __launch_bounds__(NT_PASS) k_scatter(const Seg* segs, const u32*
 }
 
 // ---------------------------------------------------------------- final in-SMEM sort
-__global__ void __launch_bounds__(NT_SORT, 1) k_seg_sort(const Seg* segs, const u32* nseg_ptr, u32 cap, u32* work,
-                                                         Bufs bufs, const Job* jobs, u32 dst_where, u32* err) {
-  constexpr u32 IT = NMAX / NT_SORT;  // 16
+// One block per final segment: a bulk async copy stages the segment in shared
+// memory, its exact key range sets the number of radix digits, the lowest digit
+// is a counting pass (order within a digit is free there) and every further
+// 8-bit digit a stable pass ranked with warp ballots.  Only a permutation of
+// indices moves; the write-out reads tuples in sorted order from shared memory
+// and stores them coalesced.  Two instantiations share the work list: CAP =
+// 4096 (two blocks per SM, so one block's copy overlaps the other's sort)
+// takes segments of at most 4096 tuples and all constant-key segments; CAP =
+// 8192 (one block per SM) takes the rest.
+template <u32 CAP, u32 MINB>
+__global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, const u32* nseg_ptr, u32 cap, u32* work,
+                                                            Bufs bufs, const Job* jobs, u32 dst_where, u32* err) {
+  constexpr u32 IT = CAP / NT_SORT;
+  constexpr bool SMALL = CAP <= NMAX / 2;
   extern __shared__ __align__(128) unsigned char sm_raw[];
-  Tuple* tup = reinterpret_cast<Tuple*>(sm_raw);        // NMAX
-  u16* ia = reinterpret_cast<u16*>(tup + NMAX);         // NMAX
-  u16* ib = ia + NMAX;                                  // NMAX
-  u32* cnt = reinterpret_cast<u32*>(ib + NMAX);         // NW_SORT * 256 (>= 2048)
+  Tuple* tup = reinterpret_cast<Tuple*>(sm_raw);        // CAP
+  u16* ia = reinterpret_cast<u16*>(tup + CAP);          // CAP
+  u16* ib = ia + CAP;                                   // CAP
+  u32* cnt = reinterpret_cast<u32*>(ib + CAP);          // NW_SORT * 256 (>= 2048)
   __shared__ __align__(8) u64 mbar;
   __shared__ u32 s_item;
   __shared__ u32 s_warp[NT_SORT / 32 + 1];
@@ -486,16 +516,18 @@ __global__ void __launch_bounds__(NT_SORT, 1) k_seg_sort(const Seg* segs, const 
     __syncthreads();
     if (item >= n_items) break;
     const Seg sg = segs[item];
+    const bool constant = (sg.flags & SEG_EXACT) && sg.kmin == sg.kmax;
+    if (SMALL ? (!constant && sg.len > CAP) : (constant || sg.len <= NMAX / 2)) continue;  // the other class
     const Tuple* src = seg_src(bufs, jobs, sg.flags & 7u, sg.job, sg.off);
     Tuple* dst = dstb + sg.off;
     const u32 n = (u32)sg.len;
     const bool inplace = (src == dst);
-    if ((sg.flags & SEG_EXACT) && sg.kmin == sg.kmax) {
+    if (constant) {
       if (!inplace)
         for (u32 i = tid; i < n; i += NT_SORT) st_tuple(dst + i, src[i]);
       continue;
     }
-    if (sg.len > NMAX) {
+    if (sg.len > CAP) {
       if (tid == 0) atomicOr(err, (u32)DERR_SEG_TOO_BIG);
       continue;
     }
@@ -554,7 +586,7 @@ __global__ void __launch_bounds__(NT_SORT, 1) k_seg_sort(const Seg* segs, const 
       }
     }
     __syncthreads();
-    smem_exclusive_scan<u32, NT_SORT, 4>(cnt, F1, s_warp);
+    smem_exclusive_scan<u32, NT_SORT, 2048 / NT_SORT>(cnt, F1, s_warp);
 #pragma unroll
     for (u32 i = 0; i < IT; ++i) {
       const u32 e = tid + i * NT_SORT;
@@ -637,26 +669,31 @@ __global__ void k_check_empty(const u32* cnt, u32* err, u32 flag) {
   if (threadIdx.x == 0 && *cnt != 0) atomicOr(err, flag);
 }
 
-constexpr size_t SMEM_SCATTER = SC_TILE * sizeof(Tuple) + 3 * F_MAX * sizeof(u32) + SC_TILE * sizeof(u16) +
+constexpr size_t SMEM_SCATTER = SC_TILE * sizeof(Tuple) + 3 * F_MAX * sizeof(u32) + 2 * SC_TILE * sizeof(u16) +
                                 FINE_MAX * sizeof(u16);
-constexpr size_t SMEM_SORT = NMAX * sizeof(Tuple) + 2 * NMAX * sizeof(u16) + NW_SORT * 256 * sizeof(u32);
+constexpr size_t smem_sort(u32 cap) { return cap * sizeof(Tuple) + 2 * cap * sizeof(u16) + NW_SORT * 256 * sizeof(u32); }
 constexpr size_t SMEM_SCAN = (3 * F_MAX + 1) * sizeof(u64);
+
 
 template <class K>
 void set_smem(K kernel, size_t bytes) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // ask for the largest shared-memory carveout so several blocks fit per SM
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 }  // namespace
 
 void init_attrs_pass() {
+
   set_smem(k_hist<MODE_RADIX, F_MAX>, F_MAX * 20);
   set_smem(k_hist<MODE_FINE, FINE_MAX>, FINE_MAX * 20);
   set_smem(k_scan<MODE_RADIX>, SMEM_SCAN);
   set_smem(k_scan<MODE_SPLIT>, SMEM_SCAN);
   set_smem(k_scatter<MODE_RADIX>, SMEM_SCATTER);
   set_smem(k_scatter<MODE_SPLIT>, SMEM_SCATTER);
-  set_smem(k_seg_sort, SMEM_SORT);
+  set_smem(k_seg_sort<NMAX / 2, 2>, smem_sort(NMAX / 2));
+  set_smem(k_seg_sort<NMAX, 1>, smem_sort(NMAX));
 }
 
 namespace {
@@ -711,19 +748,22 @@ void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32
 
 void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                     Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
-                    cudaStream_t st, int nsm) {
+                    u32* err, cudaStream_t st, int nsm) {
   if (mode == MODE_SPLIT) {
     k_scatter<MODE_SPLIT><<<nsm * 2, NT_PASS, SMEM_SCATTER, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
-                                                                  src_where, dst_where, hist, sp);
+                                                                  src_where, dst_where, hist, sp, err);
   } else {
     k_scatter<MODE_RADIX><<<nsm * 2, NT_PASS, SMEM_SCATTER, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
-                                                                  src_where, dst_where, hist, sp);
+                                                                  src_where, dst_where, hist, sp, err);
   }
 }
 
 void launch_seg_sort(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs,
                      u32 dst_where, u32* err, cudaStream_t st, int nsm) {
-  k_seg_sort<<<nsm, NT_SORT, SMEM_SORT, st>>>(segs, nseg, cap, work, bufs, jobs, dst_where, err);
+  // small segments first (two blocks per SM), then the large ones; each kernel
+  // walks the whole list with its own work counter and skips the other class
+  k_seg_sort<NMAX / 2, 2><<<nsm * 2, NT_SORT, smem_sort(NMAX / 2), st>>>(segs, nseg, cap, work, bufs, jobs, dst_where, err);
+  k_seg_sort<NMAX, 1><<<nsm, NT_SORT, smem_sort(NMAX), st>>>(segs, nseg, cap, work + 1, bufs, jobs, dst_where, err);
 }
 
 void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st) {

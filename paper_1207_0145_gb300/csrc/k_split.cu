@@ -313,6 +313,7 @@ constexpr size_t SMEM_SPLITTERS = 2 * (FINE_MAX + 1) * sizeof(u64) + 1024 * size
 
 void init_attrs_split() {
   cudaFuncSetAttribute(k_splitters, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_SPLITTERS);
+  cudaFuncSetAttribute(k_splitters, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 void launch_run_bounds(Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, cudaStream_t st) {

@@ -33,6 +33,7 @@ constexpr u32 P_MAX = 2048;       // largest number of S partitions
 constexpr u32 RUNS_MAX = 1024;    // largest T_R per job
 constexpr u32 TILE_MAX = 4096;    // largest join tile
 constexpr u32 MAX_LEVELS = 16;    // radix passes of 4..11 bits cover any 64-bit key range
+constexpr u32 SEARCH_TB = 32;     // consecutive tiles one search thread walks through per run
 
 // where a segment's tuples live
 enum Where : u32 { W_RIN = 0, W_SIN = 1, W_XR = 2, W_XS = 3, W_Y = 4 };
@@ -69,6 +70,7 @@ struct Job {
   u64 s_kept;               // S tuples inside [kmin, kmax]
   u64 tile_base, ntiles;    // global index of the job's first join tile; its tile count
   u64 win_base;             // first window entry of the job (tiles * runs pairs before it)
+  u64 search_base;          // first search work item of the job (runs x tile blocks)
   u64 count, checksum;      // result
   u64 pair_base;            // first output pair of the job (pairs mode)
 };

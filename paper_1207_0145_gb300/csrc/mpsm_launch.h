@@ -26,7 +26,7 @@ void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32
                  int nsm);
 void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                     Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
-                    cudaStream_t st, int nsm);
+                    u32* err, cudaStream_t st, int nsm);
 void launch_seg_sort(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs,
                      u32 dst_where, u32* err, cudaStream_t st, int nsm);
 void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st);

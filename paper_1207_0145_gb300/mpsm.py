@@ -124,12 +124,13 @@ def _tuples(t) -> Tuple[int, int]:
 
 
 def make_options(runs_r=0, partitions_s=0, fine_bits=0, radix_bits=0, join_tile=0, splitter_mode=SPLIT_HIST,
-                 search_mode=SEARCH_BINARY, timing=False, kernel_timing=False, seed=20120145) -> Options:
+                 search_mode=SEARCH_BINARY, timing=False, kernel_timing=False, flags=0,
+                 seed=20120145) -> Options:
     o = Options()
     lib().mpsm_options_default(ctypes.byref(o))
     o.runs_r, o.partitions_s, o.fine_bits, o.radix_bits, o.join_tile = runs_r, partitions_s, fine_bits, radix_bits, join_tile
     o.splitter_mode, o.search_mode = splitter_mode, search_mode
-    o.flags = (FLAG_TIMING if timing else 0) | (FLAG_KERNEL_TIMING if kernel_timing else 0)
+    o.flags = (FLAG_TIMING if timing else 0) | (FLAG_KERNEL_TIMING if kernel_timing else 0) | flags
     o.seed = seed
     return o
 
@@ -238,8 +239,10 @@ class Plan:
         _check(lib().mpsm_plan_stats(self.handle, ctypes.byref(s)), "mpsm_plan_stats")
         return s.as_dict()
 
-    def set_flags(self, timing: bool = False, kernel_timing: bool = False):
-        flags = (FLAG_TIMING if timing else 0) | (FLAG_KERNEL_TIMING if kernel_timing else 0)
+    def set_flags(self, timing: bool = False, kernel_timing: bool = False, extra: Optional[int] = None):
+        if extra is None:
+            extra = 0
+        flags = (FLAG_TIMING if timing else 0) | (FLAG_KERNEL_TIMING if kernel_timing else 0) | extra
         _check(lib().mpsm_plan_set_flags(self.handle, flags), "mpsm_plan_set_flags")
 
     def kernel_times(self) -> dict:
