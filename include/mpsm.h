@@ -211,6 +211,26 @@ int mpsm_plan_view(mpsm_plan_t* plan, mpsm_view_t* view);
 
 const char* mpsm_strerror(int status);
 
+/* ---- allocation-free run sort ------------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory -- code that runs under a memory pool owned by
+ * someone else (a framework's caching allocator, a fixed budget), or on a path
+ * where cudaMalloc's implicit device-wide synchronisation is not acceptable.
+ * It does phase 1 alone for a small input: R (nR tuples, device) is cut into
+ * `runs` chunks [floor(j nR/runs), floor((j+1) nR/runs)) exactly like
+ * mpsm_sort_runs, and each chunk is sorted by key into `out` (device, nR
+ * tuples; may equal R) at the same positions.  No plan is needed and nothing is
+ * allocated: the scratch lives in one fixed device array of about 41 KB inside
+ * the library, which every GPU that loads the library keeps until exit.
+ * Limits: 1 <= runs <= 1024 and every run at most 8192 tuples
+ * (ceil(nR / runs) <= 8192); larger sizes return MPSM_ERR_INVALID_ARG.  Pointers
+ * must be 16-byte aligned.  Work goes on `stream` (a cudaStream_t, NULL = legacy
+ * default stream); the call synchronises it before returning.  The first call on
+ * a device looks up the array's address and sets kernel attributes, so make that
+ * first call before any stream capture.  Every call shares the array: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race. */
+int mpsm_sort_runs_noalloc(const mpsm_tuple_t* R, uint64_t nR, uint32_t runs, mpsm_tuple_t* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

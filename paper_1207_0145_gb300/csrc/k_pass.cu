@@ -20,6 +20,9 @@
 // segment with a bulk async copy (TMA) into shared memory and radix-sorts it
 // there (first digit by an unstable counting pass, further digits by stable
 // warp-ballot ranking), then writes it out in order.
+#include <mutex>
+
+#include "mpsm.h"
 #include "mpsm_internal.cuh"
 #include "mpsm_launch.h"
 
@@ -770,4 +773,101 @@ void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st) {
   k_check_empty<<<1, 32, 0, st>>>(cnt, err, flag);
 }
 
+
+// ---------------------------------------------------------------- allocation-free run sort
+// Sorts the runs of R into a caller buffer with all scratch -- the job record,
+// the list of runs, the two work counters of the sort kernels and the error
+// flag -- in one file-scope device array instead of cudaMalloc'ed memory.
+
+namespace {
+
+constexpr u32 NOALLOC_MAX_RUNS = 1024;
+
+struct NoAllocScratch {
+  Job job;
+  u32 counters[8];  // [0] runs listed, [1] [2] work counters, [3] error flags
+  Seg segs[NOALLOC_MAX_RUNS];
+};
+
+// Shared by every call on this device; it keeps the last call's contents.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+__global__ void k_noalloc_init(NoAllocScratch* sc, const Tuple* R, u64 nR, u32 runs) {
+  if (threadIdx.x == 0) {
+    Job J{};
+    J.R = R;
+    J.nR = nR;
+    J.runs = runs;
+    sc->job = J;
+    sc->counters[1] = 0;
+    sc->counters[2] = 0;
+    sc->counters[3] = 0;
+  }
+  __syncthreads();
+  for (u32 j = threadIdx.x; j < runs; j += blockDim.x) {
+    const u64 a = (u64)(((unsigned __int128)nR * j) / runs);
+    const u64 b = (u64)(((unsigned __int128)nR * (j + 1)) / runs);
+    if (b > a)
+      sc->segs[j] = Seg{a, b - a, 0ull, ~0ull, 0u, W_RIN};
+    else
+      sc->segs[j] = Seg{a, 0ull, 0ull, 0ull, 0u, W_RIN | SEG_EXACT};  // empty run: nothing to move
+  }
+  if (threadIdx.x == 0) sc->counters[0] = runs;
+}
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[128];  // device address of the scratch array, per device ordinal
+
+}  // namespace
+
 }  // namespace mpsm
+
+/* See include/mpsm.h.  The first call on a device looks up the scratch array's
+ * device address (cudaGetSymbolAddress, with that device current) and sets the
+ * sort kernels' shared-memory limits; make that first call before any stream
+ * capture.  Calls whose work overlaps on the GPU share the array and race. */
+extern "C" __attribute__((visibility("default"))) int mpsm_sort_runs_noalloc(const mpsm_tuple_t* R, uint64_t nR,
+                                                                             uint32_t runs, mpsm_tuple_t* out,
+                                                                             void* stream) {
+  using namespace mpsm;
+  if (runs == 0 || runs > NOALLOC_MAX_RUNS) return MPSM_ERR_INVALID_ARG;
+  if (nR && (!R || !out)) return MPSM_ERR_INVALID_ARG;
+  if ((((uintptr_t)R) | ((uintptr_t)out)) & 15u) return MPSM_ERR_INVALID_ARG;
+  if ((nR + runs - 1) / runs > NMAX) return MPSM_ERR_INVALID_ARG;  // every run must fit one block
+  if (nR == 0) return MPSM_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+    cudaGetLastError();
+    return MPSM_ERR_CUDA;
+  }
+  NoAllocScratch* sc = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return MPSM_ERR_CUDA;
+      }
+      init_attrs_pass();
+      g_noalloc_addr[dev] = ptr;
+    }
+    sc = reinterpret_cast<NoAllocScratch*>(g_noalloc_addr[dev]);
+  }
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (nsm <= 0) nsm = 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_noalloc_init<<<1, 1024, 0, st>>>(sc, reinterpret_cast<const Tuple*>(R), nR, runs);
+  Bufs b{reinterpret_cast<Tuple*>(out), nullptr, nullptr};
+  launch_seg_sort(sc->segs, &sc->counters[0], NOALLOC_MAX_RUNS, &sc->counters[1], b, &sc->job, W_XR,
+                  &sc->counters[3], st, nsm);
+  if (cudaGetLastError() != cudaSuccess) return MPSM_ERR_CUDA;
+  u32 err = 0;
+  if (cudaMemcpyAsync(&err, &sc->counters[3], sizeof(u32), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return MPSM_ERR_CUDA;
+  }
+  return err ? MPSM_ERR_DEVICE : MPSM_OK;
+}

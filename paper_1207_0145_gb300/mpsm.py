@@ -94,6 +94,7 @@ def lib():
             "mpsm_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "mpsm_plan_set_flags": ([_p, _u32], ctypes.c_int),
             "mpsm_plan_kernel_times": ([_p, P(KernelTime), _u32, P(_u32)], ctypes.c_int),
+            "mpsm_sort_runs_noalloc": ([_p, _u64, _u32, _p, _p], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -256,6 +257,16 @@ class Plan:
         v = View()
         _check(lib().mpsm_plan_view(self.handle, ctypes.byref(v)), "mpsm_plan_view")
         return v
+
+
+def sort_runs_noalloc(R, runs: int, out, stream: Optional[int] = None):
+    """Phase 1 for a small input without any device allocation (include/mpsm.h):
+    the runs of R (up to 1024 runs of at most 8192 tuples) sorted into `out`."""
+    rp, nr = _tuples(R)
+    op, no = _tuples(out)
+    if no < nr:
+        raise ValueError("out is smaller than R")
+    _check(lib().mpsm_sort_runs_noalloc(rp, nr, runs, op, stream or None), "mpsm_sort_runs_noalloc")
 
 
 def strerror(status: int) -> str:
