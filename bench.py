@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--runs", type=int, default=0, help="T_R (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=32, help="CPU baseline runs 1/this of the workload")
+    ap.add_argument("--cpu-sample", type=int, default=16, help="CPU baseline runs 1/this of the workload")
     return ap.parse_args()
 
 
@@ -160,16 +160,18 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(files=None):
+    """Hash of the CUDA sources a kernel is built from (all of csrc when not named)."""
+    d = os.path.join(ROOT, "paper_1207_0145_gb300", "csrc")
     h = hashlib.sha256()
-    for fn in sorted(os.listdir(os.path.join(ROOT, "paper_1207_0145_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_1207_0145_gb300", "csrc", fn), "rb") as f:
+    for fn in sorted(files or os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str, config: str):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current sources."""
+    """DRAM bytes per launch from a committed ncu summary, if its kernel's sources are unchanged."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{config}_traffic.txt")
     try:
         vals = {}
@@ -178,7 +180,8 @@ def recorded_traffic(kernel: str, config: str):
                 if ":" in line:
                     k, v = line.split(":", 1)
                     vals[k.strip()] = v.strip()
-        if vals.get("source_hash") != kernel_source_hash():
+        files = vals.get("sources", "").split() or None
+        if vals.get("source_hash") != kernel_source_hash(files):
             return None
         return int(float(vals["dram_bytes_per_launch"]))
     except (OSError, KeyError, ValueError):
