@@ -72,8 +72,9 @@ typedef struct {
   int32_t splitter_mode;   /* MPSM_SPLIT_*                                                   */
   int32_t search_mode;     /* MPSM_SEARCH_*                                                  */
   uint32_t flags;          /* MPSM_FLAG_*                                                    */
-  uint64_t seed;           /* initialisation seed of the learned model                      */
-  uint32_t reserved[6];    /* must be zero                                                   */
+  uint64_t seed;           /* seed of the hash that spreads hot keys over learned partitions */
+  uint32_t learn_steps;    /* Adam steps of the learned model; 0 = 200                       */
+  uint32_t reserved[5];    /* must be zero                                                   */
 } mpsm_options_t;
 
 /* Fills *opt with the defaults (all automatic, histogram splitters, binary search). */
@@ -105,6 +106,8 @@ int mpsm_join_host(mpsm_plan_t* plan, const mpsm_tuple_t* R_host, uint64_t nR,
                    uint64_t* out_checksum);
 
 /* ---- phase entry points: mpsm_join == these five in order ---------------- */
+/* They run the plain modes; on a plan created with a learned mode,
+ * mpsm_sort_runs returns MPSM_ERR_INVALID_ARG. */
 
 /* Phase 1 (Sec. 2.1, 3.2): R cut into T_R chunks [floor(j nR/T_R), floor((j+1) nR/T_R)),
  * each sorted by key into a run, kept in plan scratch (see mpsm_plan_view). */
@@ -164,6 +167,12 @@ typedef struct {
   uint64_t segments_r, segments_s; /* final in-shared-memory sort segments                   */
   uint32_t launches;            /* kernels launched by the last call                         */
   uint32_t pad;
+  /* learned model (job 0; zero for the parts that ran in plain mode)                          */
+  float loss_s0, loss_s;        /* S-side model: training loss (MSE of the CDF) at the first and */
+  float loss_r0, loss_r;        /* the last Adam step; R-side model likewise                    */
+  double part_probes;           /* boundary probes per partitioned S key (learned splitters)    */
+  double search_probes;         /* probes per run-start search (binary or learned)              */
+  double search_err;            /* mean |predicted - exact| run-start position (learned search) */
 } mpsm_stats_t;
 
 /* Statistics of the last join (job 0 of a batch).  Synchronises. */
@@ -190,6 +199,56 @@ typedef struct {
   uint32_t join_tile;              /* S tuples per tile (tile t = [t*join_tile, ...) of s_buffer) */
   const uint32_t* windows;         /* device: tiles x T_R x 2 (start, end) relative to the run    */
 } mpsm_view_t;
+
+/* ---- learned CDF model (two-stage recursive model index) ----------------------
+ * The learned modes (MPSM_SPLIT_LEARNED, MPSM_SEARCH_LEARNED) train, inside
+ * every join, one model per job and side: a root MLP over the normalised key
+ * (1 -> 32 -> 32 -> 1, ReLU, FP32 weights; Adam, 200 full-batch steps, learning
+ * rate 3e-3, on up to 16384 points) and 4096 linear leaves (least squares on
+ * the key's exact offset from the leaf's smallest key).  It stands in for the
+ * paper's CDF of the runs (Sec. 4.1-4.2, Fig. 8): the S-side model is trained on
+ * a sorted sample of S (1/64 of it, at most 2^21 keys) and its quantiles give
+ * the partition boundaries; it predicts each S tuple's partition, which an exact
+ * search over the boundaries then corrects (tuples of a key equal to several
+ * boundaries spread over those partitions by a hash of their row).  The R-side
+ * model is trained on positions of the sorted runs (exact ranks) and predicts
+ * where each S tile's keys start in every run (Sec. 3.2.2), corrected by an
+ * exponential then binary search.  Results are bit-identical to the plain modes.
+ *
+ * The entry points below run the same kernels on caller data, using model slot
+ * 0 of the plan (slot 1 holds job 0's R-side model after a learned join).  All
+ * pointers are DEVICE pointers unless marked HOST; x, y are FP32, n <= 16384
+ * for the gradient and training calls.  The parameter vector theta has 1153
+ * floats: W1[32], b1[32], W2[32][32] (row = output unit), b2[32], W3[32], b3. */
+
+/* Loss (HOST *loss) = mean over i of (root(x_i) - y_i)^2 and its gradient (grad,
+ * 1153 floats) at theta. */
+int mpsm_rmi_loss_grad(mpsm_plan_t* plan, const float* x, const float* y, uint32_t n, const float* theta,
+                       float* grad, float* loss);
+/* `steps` full-batch Adam steps (beta 0.9 / 0.999, eps 1e-8) from theta, which is
+ * updated in place; HOST losses[t] (may be NULL) = loss before step t + 1. */
+int mpsm_rmi_train(mpsm_plan_t* plan, const float* x, const float* y, uint32_t n, uint32_t steps, float lr,
+                   float* theta, float* losses);
+/* Builds a whole model in slot 0 from n fit points (keys with their CDF values
+ * y, n <= the plan's sample capacity): range [kmin, kmax], initial weights,
+ * `steps` Adam steps on up to 16384 evenly spaced points, tabulation, leaves. */
+int mpsm_rmi_fit(mpsm_plan_t* plan, const uint64_t* keys, const float* y, uint32_t n, uint64_t kmin, uint64_t kmax,
+                 uint32_t steps, float lr);
+/* Predicted CDF values (yhat, n floats) and leaves (leaf, n u32, may be NULL) of
+ * `keys` under the model in `slot` (0 or 1). */
+int mpsm_rmi_predict(mpsm_plan_t* plan, uint32_t slot, const uint64_t* keys, uint64_t n, float* yhat, uint32_t* leaf);
+
+typedef struct {
+  uint64_t kmin, kmax;          /* normalisation range                                       */
+  uint32_t cshift, ncell;       /* cell = min((key - kmin) >> cshift, ncell - 1)             */
+  uint32_t fit_n, train_n;      /* fit points, training points                               */
+  float loss0, loss;            /* loss at the first and the last Adam step                  */
+} mpsm_rmi_info_t;
+/* Copies the model in `slot` to HOST buffers (each may be NULL): theta (1153
+ * floats), cell_leaf (65536 u16: the tabulated root), leaf_base (4096 u64),
+ * leaf_a, leaf_b (4096 floats each).  Synchronises. */
+int mpsm_rmi_export(mpsm_plan_t* plan, uint32_t slot, mpsm_rmi_info_t* info, float* theta, uint16_t* cell_leaf,
+                    uint64_t* leaf_base, float* leaf_a, float* leaf_b);
 
 /* Replaces the plan's MPSM_FLAG_* flags (timing on/off) for later calls. */
 int mpsm_plan_set_flags(mpsm_plan_t* plan, uint32_t flags);

@@ -32,7 +32,7 @@ enum { C_BIG0 = 0, C_BIG1 = 1, C_FIN = 2, C_WORK = 3, C_WORK2 = 4, C_ERR = 5, C_
 // totals in d_tot
 enum { T_LEVEL = 0, T_FINE = 3, T_SPLIT = 6, T_TILES = 9, T_PAIRS = 13, T_NUM = 16 };
 enum Stage { ST_NONE = 0, ST_RUNS, ST_SPLIT, ST_SCATTER, ST_SORTED, ST_SEARCH, ST_DONE };
-enum { EV_START = 0, EV_RUNS, EV_SPLIT, EV_SCATTER, EV_SORTS, EV_SEARCH, EV_JOIN, EV_NUM };
+enum { EV_START = 0, EV_RUNS, EV_LEARN, EV_SPLIT, EV_SCATTER, EV_SORTS, EV_SEARCH, EV_JOIN, EV_NUM };
 
 struct Jobh {
   const Tuple* R;
@@ -44,13 +44,24 @@ struct Jobh {
 enum Kid {
   K_SAMPLE, K_PLAN, K_INIT, K_HIST_RADIX, K_SCAN_RADIX, K_SCATTER_RADIX, K_SEG_SORT, K_RUN_BOUNDS, K_HIST_FINE,
   K_RUN_CDF, K_SPLITTERS, K_FOLD, K_SCAN_SPLIT, K_SCATTER_SPLIT, K_TILES, K_SEARCH, K_JOIN, K_PAIR_OFFSETS, K_CHECK,
-  K_NUM
+  K_SAMPLE_S, K_RMI_DATA, K_RMI_GRAD, K_RMI_ADAM, K_RMI_TAB, K_RMI_LEAF, K_LEARN_BOUNDS, K_HIST_LEARN, K_SCAN_LEARN,
+  K_SCATTER_LEARN, K_NUM
 };
 const char* const KNAME[K_NUM] = {"sample_bounds", "level_plan", "init_buckets", "hist_radix", "scan_radix",
                                   "scatter_radix", "seg_sort", "run_bounds", "hist_fine", "run_cdf", "splitters",
                                   "fold", "scan_split", "scatter_split", "tiles", "search", "join", "pair_offsets",
-                                  "check_empty"};
-constexpr u32 KT_POOL = 512;
+                                  "check_empty", "sample_s", "rmi_data", "rmi_grad", "rmi_adam", "rmi_tabulate",
+                                  "rmi_leaves", "learn_bounds", "hist_learn", "scan_learn", "scatter_learn"};
+// learned model: sample and training sizes
+constexpr u32 RMI_SAMPLE_MAX = 1u << 21;  // largest sample per model
+constexpr u32 RMI_STEPS = 200;            // full-batch Adam steps
+constexpr float RMI_LR = 3e-3f;
+u32 rmi_sample_size(u64 n) {
+  if (n == 0) return 0;
+  u64 m = std::max<u64>(std::min<u64>(n, 1024), n / 64);
+  return (u32)std::min<u64>(m, RMI_SAMPLE_MAX);
+}
+constexpr u32 KT_POOL = 1024;
 
 }  // namespace
 
@@ -110,6 +121,23 @@ struct mpsm_plan {
   // batched graph
   cudaGraphExec_t gexec = nullptr;
   std::vector<u64> gsig;
+  // learned CDF model (allocated on first use)
+  bool learn = false;               // the current call uses a learned mode
+  RmiModel* d_models = nullptr;     // 2 per job
+  RmiTask *d_tasks = nullptr, *h_tasks = nullptr;
+  void* d_leafacc = nullptr;
+  float *d_tx = nullptr, *d_ty = nullptr, *d_partial = nullptr;
+  u64* d_fitk = nullptr;
+  float* d_fity = nullptr;
+  u64 fit_cap = 0;
+  Tuple* d_samp = nullptr;          // unsorted S samples (the sub-plan's R input)
+  u64 samp_cap = 0;
+  u64 *d_samp_off = nullptr, *h_samp_off = nullptr;
+  u32 *d_samp_n = nullptr, *h_samp_n = nullptr;
+  u64* d_bnd = nullptr;             // learned partition boundaries, P_MAX per job
+  u32* d_brank = nullptr;           // their sample ranks, 2 P_MAX per job
+  u64* d_lstat = nullptr;           // learned-path counters (LearnCtx::stat)
+  mpsm_plan* sub = nullptr;         // sorts the S samples (one run per job)
 };
 
 namespace {
@@ -190,6 +218,19 @@ u32 runs_for(const mpsm_plan* p, u64 nR) {
 
 Bufs bufs(const mpsm_plan* p) { return Bufs{p->xr, p->xs, p->y}; }
 
+bool split_learned(const mpsm_plan* p) { return p->opt.splitter_mode == MPSM_SPLIT_LEARNED; }
+bool search_learned(const mpsm_plan* p) { return p->opt.search_mode == MPSM_SEARCH_LEARNED; }
+
+LearnCtx lctx(const mpsm_plan* p, bool models) {
+  LearnCtx c{};
+  c.models = models ? p->d_models : nullptr;
+  c.bnd = p->d_bnd;
+  c.brank = p->d_brank;
+  c.seed = p->opt.seed;
+  c.stat = p->d_lstat;
+  return c;
+}
+
 void record(mpsm_plan* p, int i) {
   if (p->timing) cudaEventRecord(p->ev[i], p->st);
 }
@@ -242,6 +283,65 @@ int debug_check(mpsm_plan* p, u32 id) {
     kt_end(p);                            \
     if (debug_check(p, id)) return MPSM_ERR_CUDA; \
   } while (0)
+
+int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs);
+
+// ---------------------------------------------------------------- learned model state
+int alloc_learn(mpsm_plan* p) {
+  if (p->d_models) return MPSM_OK;
+  const u64 nm = 2ull * p->max_jobs;
+  p->samp_cap = p->max_nS / 64 + 1024ull * p->max_jobs + 16;
+  p->fit_cap = p->samp_cap + p->max_nR / 64 + 1024ull * p->max_jobs + 16;
+  if (dalloc(&p->d_models, nm) || dalloc(&p->d_tasks, nm) || halloc(&p->h_tasks, nm)) return MPSM_ERR_OOM;
+  if (cudaMalloc(&p->d_leafacc, leaf_acc_bytes() * nm) != cudaSuccess) {
+    cudaGetLastError();
+    p->d_leafacc = nullptr;
+    return MPSM_ERR_OOM;
+  }
+  if (dalloc(&p->d_tx, nm * RMI_TRAIN_MAX) || dalloc(&p->d_ty, nm * RMI_TRAIN_MAX) ||
+      dalloc(&p->d_partial, nm * RMI_GMAX * RMI_NPAD) || dalloc(&p->d_fitk, p->fit_cap) ||
+      dalloc(&p->d_fity, p->fit_cap) || dalloc(&p->d_samp, p->samp_cap) || dalloc(&p->d_samp_off, p->max_jobs) ||
+      halloc(&p->h_samp_off, p->max_jobs) || dalloc(&p->d_samp_n, p->max_jobs) || halloc(&p->h_samp_n, p->max_jobs) ||
+      dalloc(&p->d_bnd, (u64)p->max_jobs * P_MAX) || dalloc(&p->d_brank, 2ull * p->max_jobs * P_MAX))
+    return MPSM_ERR_OOM;
+  CK(cudaMemsetAsync(p->d_models, 0, nm * sizeof(RmiModel), p->st));
+  mpsm_options_t so;
+  mpsm_options_default(&so);
+  so.runs_r = 1;  // each job's sample is one run
+  mpsm_plan_t* sub = nullptr;
+  const int rc = mpsm_plan_create(&sub, p->samp_cap, 16, p->max_jobs, &so, p->st);
+  if (rc) return rc;
+  p->sub = sub;
+  return MPSM_OK;
+}
+
+// sample sizes, model tasks and the sample sort's jobs of a learned call
+int setup_learn(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
+  int rc = alloc_learn(p);
+  if (rc) return rc;
+  const bool sl = split_learned(p), rl = search_learned(p);
+  std::vector<Jobh> sj(njobs);
+  u64 so = 0, fo = 0;
+  for (u32 i = 0; i < njobs; ++i) {
+    const u32 ms = sl ? rmi_sample_size(jobs[i].nS) : 0u;
+    const u32 mr = rl ? rmi_sample_size(jobs[i].nR) : 0u;
+    p->h_samp_off[i] = so;
+    p->h_samp_n[i] = ms;
+    sj[i] = Jobh{p->d_samp + so, nullptr, ms, 0};
+    p->h_tasks[2 * i] = RmiTask{fo, so, 0, 0, i, RMI_KIND_SAMPLE, ms, (u32)(ms > 0)};
+    fo += ms;
+    so += ms;
+    p->h_tasks[2 * i + 1] = RmiTask{fo, 0, 0, 0, i, RMI_KIND_RUNS, mr, (u32)(mr > 0)};
+    fo += mr;
+  }
+  if (so > p->samp_cap || fo > p->fit_cap) return MPSM_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(p->d_tasks, p->h_tasks, 2ull * njobs * sizeof(RmiTask), cudaMemcpyHostToDevice, p->st));
+  CK(cudaMemcpyAsync(p->d_samp_off, p->h_samp_off, njobs * sizeof(u64), cudaMemcpyHostToDevice, p->st));
+  CK(cudaMemcpyAsync(p->d_samp_n, p->h_samp_n, njobs * sizeof(u32), cudaMemcpyHostToDevice, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  if (sl) return setup_jobs(p->sub, sj.data(), njobs);
+  return MPSM_OK;
+}
 
 // ---------------------------------------------------------------- per-call setup
 int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
@@ -335,6 +435,9 @@ int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
   p->levels_r = p->levels_s = 0;
   p->launches = 0;
   p->kt_n = 0;
+  p->learn = split_learned(p) || search_learned(p);
+  CK(cudaMemsetAsync(p->d_lstat, 0, 8 * sizeof(u64), p->st));
+  if (p->learn) return setup_learn(p, jobs, njobs);
   return MPSM_OK;
 }
 
@@ -356,12 +459,12 @@ int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels) {
                       p->d_jobs, p->hist_a_cap, p->bucket_cap, &p->d_cnt[C_ERR], p->st));
     LAUNCH(K_INIT, launch_init_buckets(p->d_bmin, p->d_bmax, nullptr, tot, p->st, p->nsm));
     LAUNCH(K_HIST_RADIX, launch_hist(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs, src,
-                p->d_hist_a, p->d_bmin, p->d_bmax, nullptr, p->st, p->nsm));
+                p->d_hist_a, p->d_bmin, p->d_bmax, nullptr, lctx(p, false), p->st, p->nsm));
     LAUNCH(K_SCAN_RADIX, launch_scan(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, p->d_hist_a, p->d_bmin, p->d_bmax,
                 nullptr, p->d_big[cur ^ 1], &p->d_cnt[C_BIG0 + (cur ^ 1)], p->big_cap, p->d_fin, &p->d_cnt[C_FIN],
                 p->fin_cap, dst, p->d_jobs, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm));
     LAUNCH(K_SCATTER_RADIX, launch_scatter(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs,
-                   src, dst, p->d_hist_a, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm));
+                   src, dst, p->d_hist_a, nullptr, &p->d_cnt[C_ERR], lctx(p, false), p->st, p->nsm));
     CK(cudaGetLastError());
     src = dst;
     cur ^= 1;
@@ -406,7 +509,63 @@ int phase_runs(mpsm_plan* p) {
   return MPSM_OK;
 }
 
+// Learned model of each job: S sample sorted by the sub-plan (the same sort
+// kernels as phase 1), fit data, training, tabulation and leaves.
+int phase_learn(mpsm_plan* p) {
+  if (!p->learn) {
+    record(p, EV_LEARN);
+    return MPSM_OK;
+  }
+  const u32 nm = 2 * p->njobs;
+  if (split_learned(p)) {
+    LAUNCH(K_SAMPLE_S, launch_sample_s(p->d_jobs, p->njobs, p->d_samp_off, p->d_samp_n, p->d_samp, p->st, p->nsm));
+    p->sub->graph_mode = p->graph_mode;
+    p->sub->opt.flags = p->opt.flags & MPSM_FLAG_KERNEL_TIMING;
+    const int rc = phase_runs(p->sub);
+    p->launches += p->sub->launches;
+    if (rc) return rc;
+  }
+  LAUNCH(K_RMI_DATA, launch_rmi_setup(p->d_models, p->d_tasks, nm, p->d_jobs, true, p->st));
+  LAUNCH(K_RMI_DATA, launch_fit_data(p->d_models, p->d_tasks, nm, p->d_jobs, p->d_runs, p->xr,
+                                     p->sub ? p->sub->xr : nullptr, p->d_fitk, p->d_fity, p->st, p->nsm));
+  LAUNCH(K_RMI_DATA, launch_train_data(p->d_models, nm, p->d_fitk, p->d_fity, p->d_tx, p->d_ty, p->st));
+  const u32 steps = p->opt.learn_steps ? p->opt.learn_steps : RMI_STEPS;
+  for (u32 t = 1; t <= steps; ++t) {
+    LAUNCH(K_RMI_GRAD, launch_rmi_grad(p->d_models, nm, p->d_tx, p->d_ty, p->d_partial, p->st));
+    LAUNCH(K_RMI_ADAM, launch_rmi_adam(p->d_models, nm, p->d_partial, t, RMI_LR, p->st));
+  }
+  LAUNCH(K_RMI_TAB, launch_rmi_tabulate(p->d_models, nm, p->st));
+  LAUNCH(K_RMI_LEAF, launch_leaf_fit(p->d_models, nm, p->d_leafacc, p->d_fitk, p->d_fity, p->st, p->nsm));
+  CK(cudaGetLastError());
+  record(p, EV_LEARN);
+  return MPSM_OK;
+}
+
+// Learned splitters: partition boundaries at the quantiles of the sorted S
+// sample, then one counting pass in which the model predicts each S tuple's
+// partition and an exact search over the boundaries corrects it.
+int phase_splitters_learned(mpsm_plan* p) {
+  u64* ts = p->d_tot + T_SPLIT;
+  LAUNCH(K_LEARN_BOUNDS, launch_learn_bounds(p->d_jobs, p->njobs, p->d_models, p->d_fitk, p->d_bnd, p->d_brank, p->st));
+  LAUNCH(K_PLAN, launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls2, ts, MODE_LEARN, p->ch_s, 11,
+                                   p->d_jobs, p->hist_a_cap, p->bucket_cap, &p->d_cnt[C_ERR], p->st));
+  LAUNCH(K_INIT, launch_init_buckets(p->d_bmin, p->d_bmax, nullptr, ts, p->st, p->nsm));
+  LAUNCH(K_HIST_LEARN, launch_hist(MODE_LEARN, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, ts, p->ch_s, bufs(p), p->d_jobs,
+                                   W_SIN, p->d_hist_a, p->d_bmin, p->d_bmax, nullptr, lctx(p, true), p->st, p->nsm));
+  CK(cudaMemsetAsync(&p->d_cnt[C_BIG0], 0, sizeof(u32), p->st));
+  CK(cudaMemsetAsync(&p->d_cnt[C_FIN], 0, sizeof(u32), p->st));
+  LAUNCH(K_SCAN_LEARN, launch_scan(MODE_LEARN, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_hist_a, p->d_bmin,
+                                   p->d_bmax, nullptr, p->d_big[0], &p->d_cnt[C_BIG0], p->big_cap, p->d_fin,
+                                   &p->d_cnt[C_FIN], p->fin_cap, W_XS, p->d_jobs, p->d_part_off, &p->d_cnt[C_ERR],
+                                   p->st, p->nsm));
+  CK(cudaGetLastError());
+  record(p, EV_SPLIT);
+  p->stage = ST_SPLIT;
+  return MPSM_OK;
+}
+
 int phase_splitters(mpsm_plan* p) {
+  if (split_learned(p)) return phase_splitters_learned(p);
   const u32 nj = p->njobs;
   CK(cudaMemsetAsync(p->d_rc, 0, (u64)nj * (FINE_MAX + 1) * sizeof(u64), p->st));
   CK(cudaMemsetAsync(p->d_fine_s, 0, (u64)nj * FINE_MAX * sizeof(u64), p->st));
@@ -417,7 +576,7 @@ int phase_splitters(mpsm_plan* p) {
   LAUNCH(K_PLAN, launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls, tf, MODE_FINE, p->ch_s, 11, p->d_jobs,
                     p->hist_b_cap, ~0ull, &p->d_cnt[C_ERR], p->st));
   LAUNCH(K_HIST_FINE, launch_hist(MODE_FINE, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls, tf, p->ch_s, bufs(p), p->d_jobs, W_SIN,
-              p->d_hist_b, p->d_fine_min, p->d_fine_max, p->d_fine_s, p->st, p->nsm));
+              p->d_hist_b, p->d_fine_min, p->d_fine_max, p->d_fine_s, lctx(p, false), p->st, p->nsm));
   LAUNCH(K_RUN_CDF, launch_run_cdf(p->d_jobs, nj, p->d_runs, p->xr, p->d_rc, p->st));
   LAUNCH(K_SPLITTERS, launch_splitters(p->d_jobs, nj, p->d_fine_s, p->d_rc, p->d_fine_r, p->d_sp, p->d_fstart, &p->d_cnt[C_ERR], p->st));
   LAUNCH(K_PLAN, launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls2, ts, MODE_SPLIT, p->ch_s, 11, p->d_jobs,
@@ -436,8 +595,11 @@ int phase_splitters(mpsm_plan* p) {
 }
 
 int phase_scatter(mpsm_plan* p) {
-  LAUNCH(K_SCATTER_SPLIT, launch_scatter(MODE_SPLIT, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_tot + T_SPLIT, p->ch_s, bufs(p),
-                 p->d_jobs, W_SIN, W_XS, p->d_hist_a, p->d_sp, &p->d_cnt[C_ERR], p->st, p->nsm));
+  const bool sl = split_learned(p);
+  LAUNCH(sl ? K_SCATTER_LEARN : K_SCATTER_SPLIT,
+         launch_scatter(sl ? MODE_LEARN : MODE_SPLIT, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_tot + T_SPLIT,
+                        p->ch_s, bufs(p), p->d_jobs, W_SIN, W_XS, p->d_hist_a, p->d_sp, &p->d_cnt[C_ERR],
+                        lctx(p, sl), p->st, p->nsm));
   CK(cudaGetLastError());
   record(p, EV_SCATTER);
   p->stage = ST_SCATTER;
@@ -456,7 +618,8 @@ int phase_sort_parts(mpsm_plan* p) {
 
 int phase_search(mpsm_plan* p) {
   LAUNCH(K_TILES, launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, p->st));
-  LAUNCH(K_SEARCH, launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win, p->st, p->nsm));
+  LAUNCH(K_SEARCH, launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win,
+                                 lctx(p, search_learned(p)), p->st, p->nsm));
   CK(cudaGetLastError());
   record(p, EV_SEARCH);
   p->stage = ST_SEARCH;
@@ -465,7 +628,11 @@ int phase_search(mpsm_plan* p) {
 
 int read_err(mpsm_plan* p) {
   CK(cudaMemcpyAsync(&p->h_cnt[C_ERR], &p->d_cnt[C_ERR], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
+  const bool sub = p->learn && split_learned(p) && p->sub;
+  if (sub)
+    CK(cudaMemcpyAsync(&p->sub->h_cnt[C_ERR], &p->sub->d_cnt[C_ERR], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
   CK(cudaStreamSynchronize(p->st));
+  if (sub && p->sub->h_cnt[C_ERR]) return MPSM_ERR_DEVICE;
   return p->h_cnt[C_ERR] ? MPSM_ERR_DEVICE : MPSM_OK;
 }
 
@@ -561,6 +728,24 @@ MPSM_API void mpsm_plan_destroy(mpsm_plan_t* p) {
   dfree(p->d_tile_out);
   dfree(p->d_chunk_off);
   hfree(p->h_scalar);
+  dfree(p->d_lstat);
+  dfree(p->d_models);
+  dfree(p->d_tasks);
+  hfree(p->h_tasks);
+  if (p->d_leafacc) cudaFree(p->d_leafacc);
+  dfree(p->d_tx);
+  dfree(p->d_ty);
+  dfree(p->d_partial);
+  dfree(p->d_fitk);
+  dfree(p->d_fity);
+  dfree(p->d_samp);
+  dfree(p->d_samp_off);
+  hfree(p->h_samp_off);
+  dfree(p->d_samp_n);
+  hfree(p->h_samp_n);
+  dfree(p->d_bnd);
+  dfree(p->d_brank);
+  if (p->sub) mpsm_plan_destroy(p->sub);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
@@ -581,13 +766,13 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   mpsm_options_t o;
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
       if (o.reserved[i]) return MPSM_ERR_INVALID_ARG;
   } else {
     mpsm_options_default(&o);
   }
   if (o.fine_bits > 12 || (o.radix_bits && (o.radix_bits < 4 || o.radix_bits > 11))) return MPSM_ERR_INVALID_ARG;
-  if (o.partitions_s > P_MAX || o.runs_r > RUNS_MAX) return MPSM_ERR_INVALID_ARG;
+  if (o.partitions_s > P_MAX || o.runs_r > RUNS_MAX || o.learn_steps > 100000) return MPSM_ERR_INVALID_ARG;
   if (o.join_tile && (o.join_tile < 256 || o.join_tile > TILE_MAX || o.join_tile % 256)) return MPSM_ERR_INVALID_ARG;
   if (o.splitter_mode != MPSM_SPLIT_HIST && o.splitter_mode != MPSM_SPLIT_LEARNED) return MPSM_ERR_INVALID_ARG;
   if (o.search_mode != MPSM_SEARCH_BINARY && o.search_mode != MPSM_SEARCH_LEARNED) return MPSM_ERR_INVALID_ARG;
@@ -627,6 +812,7 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   init_attrs_pass();
   init_attrs_split();
   init_attrs_join();
+  init_attrs_learn();
   const u64 nside = std::max(max_nR, max_nS);
   TRY(dalloc(&p->xr, max_nR));
   TRY(dalloc(&p->xs, max_nS));
@@ -665,6 +851,8 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   TRY(dalloc(&p->d_fstart, (u64)max_jobs * (P_MAX + 1)));
   TRY(dalloc(&p->d_part_off, (u64)max_jobs * (P_MAX + 1)));
   TRY(halloc(&p->h_scalar, 16));
+  TRY(dalloc(&p->d_lstat, 8));
+  if (o.splitter_mode == MPSM_SPLIT_LEARNED || o.search_mode == MPSM_SEARCH_LEARNED) TRY(alloc_learn(p));
   {
     const u32 fl = o.flags;
     p->opt.flags = 0;
@@ -678,6 +866,7 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
 MPSM_API int mpsm_sort_runs(mpsm_plan_t* p, const mpsm_tuple_t* R, uint64_t nR) {
   int rc = check_inputs(p, R, nR, nullptr, 0);
   if (rc) return rc;
+  if (split_learned(p) || search_learned(p)) return MPSM_ERR_INVALID_ARG;
   Jobh j{reinterpret_cast<const Tuple*>(R), nullptr, nR, 0};
   rc = setup_jobs(p, &j, 1);
   if (rc) return rc;
@@ -754,6 +943,7 @@ static int join_device(mpsm_plan_t* p, const mpsm_tuple_t* R, uint64_t nR, const
   int rc = setup_jobs(p, &j, 1);
   if (rc) return rc;
   if ((rc = phase_runs(p))) return rc;
+  if ((rc = phase_learn(p))) return rc;
   if ((rc = phase_splitters(p))) return rc;
   if ((rc = phase_scatter(p))) return rc;
   if ((rc = phase_sort_parts(p))) return rc;
@@ -818,13 +1008,14 @@ MPSM_API int mpsm_join_batch(mpsm_plan_t* p, const mpsm_job_t* jobs, uint32_t nj
     CK(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
     int prc = MPSM_OK;
     if (!prc) prc = phase_runs(p);
+    if (!prc) prc = phase_learn(p);
     if (!prc) prc = phase_splitters(p);
     if (!prc) prc = phase_scatter(p);
     if (!prc) prc = phase_sort_parts(p);
     if (!prc) {
       LAUNCH(K_TILES, launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, p->st));
-      LAUNCH(K_SEARCH, launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win, p->st,
-                    p->nsm));
+      LAUNCH(K_SEARCH, launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win,
+                                     lctx(p, search_learned(p)), p->st, p->nsm));
       LAUNCH(K_JOIN, launch_join(JOIN_AGG, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win,
                   nullptr, nullptr, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm));
     }
@@ -887,6 +1078,22 @@ MPSM_API int mpsm_plan_stats(mpsm_plan_t* p, mpsm_stats_t* s) {
     for (u64 i = 0; i < nw; ++i) sum += (double)(w[2 * i + 1] - w[2 * i]);
     s->mean_window = sum / (double)nw;
   }
+  {
+    u64 ls[8];
+    CK(cudaMemcpy(ls, p->d_lstat, sizeof(ls), cudaMemcpyDeviceToHost));
+    s->part_probes = ls[1] ? (double)ls[0] / (double)ls[1] : 0.0;
+    s->search_probes = ls[3] ? (double)ls[2] / (double)ls[3] : 0.0;
+    s->search_err = (ls[3] && search_learned(p)) ? (double)ls[4] / (double)ls[3] : 0.0;
+    if (p->d_models && p->learn) {
+      float l[2];
+      CK(cudaMemcpy(l, &p->d_models[0].loss0, sizeof(l), cudaMemcpyDeviceToHost));
+      s->loss_s0 = l[0];
+      s->loss_s = l[1];
+      CK(cudaMemcpy(l, &p->d_models[1].loss0, sizeof(l), cudaMemcpyDeviceToHost));
+      s->loss_r0 = l[0];
+      s->loss_r = l[1];
+    }
+  }
   if (p->timing) {
     auto el = [&](int a, int b) {
       float ms = 0;
@@ -897,7 +1104,8 @@ MPSM_API int mpsm_plan_stats(mpsm_plan_t* p, mpsm_stats_t* s) {
       return ms;
     };
     s->ms_sort_runs = el(EV_START, EV_RUNS);
-    s->ms_splitters = el(EV_RUNS, EV_SPLIT);
+    s->ms_learn = el(EV_RUNS, EV_LEARN);
+    s->ms_splitters = el(EV_LEARN, EV_SPLIT);
     s->ms_scatter = el(EV_SPLIT, EV_SCATTER);
     s->ms_sort_partitions = el(EV_SCATTER, EV_SORTS);
     s->ms_search = el(EV_SORTS, EV_SEARCH);
@@ -921,6 +1129,10 @@ MPSM_API int mpsm_plan_set_flags(mpsm_plan_t* p, uint32_t flags) {
   }
   p->opt.flags = flags;
   p->timing = (flags & MPSM_FLAG_TIMING) != 0;
+  if (p->sub) {
+    const int rc = mpsm_plan_set_flags(p->sub, flags & MPSM_FLAG_KERNEL_TIMING);
+    if (rc) return rc;
+  }
   return MPSM_OK;
 }
 
@@ -929,15 +1141,19 @@ MPSM_API int mpsm_plan_kernel_times(mpsm_plan_t* p, mpsm_kernel_time_t* out, uin
   CK(cudaStreamSynchronize(p->st));
   float ms[K_NUM] = {};
   u32 cnt[K_NUM] = {};
-  for (u32 i = 0; i < p->kt_n; ++i) {
-    float t = 0;
-    if (cudaEventElapsedTime(&t, p->kt_ev[2 * i], p->kt_ev[2 * i + 1]) != cudaSuccess) {
-      cudaGetLastError();
-      t = 0;
+  auto add = [&](const mpsm_plan* q) {
+    for (u32 i = 0; i < q->kt_n; ++i) {
+      float t = 0;
+      if (cudaEventElapsedTime(&t, q->kt_ev[2 * i], q->kt_ev[2 * i + 1]) != cudaSuccess) {
+        cudaGetLastError();
+        t = 0;
+      }
+      ms[q->kt_id[i]] += t;
+      cnt[q->kt_id[i]] += 1;
     }
-    ms[p->kt_id[i]] += t;
-    cnt[p->kt_id[i]] += 1;
-  }
+  };
+  add(p);
+  if (p->learn && split_learned(p) && p->sub && p->sub->kt_ev) add(p->sub);  // the sample sort
   u32 k = 0;
   for (u32 id = 0; id < K_NUM; ++id) {
     if (!cnt[id]) continue;
@@ -1007,4 +1223,137 @@ MPSM_API const char* mpsm_strerror(int status) {
     case MPSM_ERR_STATE: return "phase called out of order";
     default: return "unknown status";
   }
+}
+
+// ============================================================== learned model on caller data
+
+namespace {
+
+// model slot 0 takes caller data (slot 1 is switched off)
+int rmi_slot0(mpsm_plan* p, u32 n, u64 kmin, u64 kmax, bool init) {
+  int rc = alloc_learn(p);
+  if (rc) return rc;
+  p->learn = false;  // the last join's learned state is gone
+  p->h_tasks[0] = RmiTask{0, 0, kmin, kmax, 0, RMI_KIND_GIVEN, n, 1};
+  p->h_tasks[1] = RmiTask{0, 0, 0, 0, 0, RMI_KIND_GIVEN, 0, 0};
+  CK(cudaMemcpyAsync(p->d_tasks, p->h_tasks, 2 * sizeof(RmiTask), cudaMemcpyHostToDevice, p->st));
+  launch_rmi_setup(p->d_models, p->d_tasks, 2, p->d_jobs, init, p->st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->st));
+  return MPSM_OK;
+}
+
+// caller's training points into slot 0
+int rmi_points(mpsm_plan* p, const float* x, const float* y, u32 n, const float* theta) {
+  int rc = rmi_slot0(p, n, 0, 1, false);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(p->d_tx, x, n * sizeof(float), cudaMemcpyDeviceToDevice, p->st));
+  CK(cudaMemcpyAsync(p->d_ty, y, n * sizeof(float), cudaMemcpyDeviceToDevice, p->st));
+  CK(cudaMemcpyAsync(p->d_models[0].theta, theta, RMI_NP * sizeof(float), cudaMemcpyDeviceToDevice, p->st));
+  u32* hn = reinterpret_cast<u32*>(p->h_scalar);
+  hn[0] = n;
+  CK(cudaMemcpyAsync(&p->d_models[0].train_n, hn, sizeof(u32), cudaMemcpyHostToDevice, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  return MPSM_OK;
+}
+
+}  // namespace
+
+MPSM_API int mpsm_rmi_loss_grad(mpsm_plan_t* p, const float* x, const float* y, uint32_t n, const float* theta,
+                                float* grad, float* loss) {
+  if (!p || !x || !y || !theta || !grad || !loss || n == 0 || n > RMI_TRAIN_MAX) return MPSM_ERR_INVALID_ARG;
+  int rc = rmi_points(p, x, y, n, theta);
+  if (rc) return rc;
+  launch_rmi_grad(p->d_models, 1, p->d_tx, p->d_ty, p->d_partial, p->st);
+  launch_rmi_reduce(p->d_partial, grad, &p->d_models[0].loss, p->st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(loss, &p->d_models[0].loss, sizeof(float), cudaMemcpyDeviceToHost, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  return MPSM_OK;
+}
+
+MPSM_API int mpsm_rmi_train(mpsm_plan_t* p, const float* x, const float* y, uint32_t n, uint32_t steps, float lr,
+                            float* theta, float* losses) {
+  if (!p || !x || !y || !theta || n == 0 || n > RMI_TRAIN_MAX || !(lr > 0.0f)) return MPSM_ERR_INVALID_ARG;
+  int rc = rmi_points(p, x, y, n, theta);
+  if (rc) return rc;
+  if (losses && steps > p->fit_cap) return MPSM_ERR_INVALID_ARG;
+  for (u32 t = 1; t <= steps; ++t) {
+    launch_rmi_grad(p->d_models, 1, p->d_tx, p->d_ty, p->d_partial, p->st);
+    launch_rmi_adam(p->d_models, 1, p->d_partial, t, lr, p->st);
+    if (losses)
+      CK(cudaMemcpyAsync(p->d_fity + (t - 1), &p->d_models[0].loss, sizeof(float), cudaMemcpyDeviceToDevice, p->st));
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(theta, p->d_models[0].theta, RMI_NP * sizeof(float), cudaMemcpyDeviceToDevice, p->st));
+  if (losses && steps) CK(cudaMemcpyAsync(losses, p->d_fity, steps * sizeof(float), cudaMemcpyDeviceToHost, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  return MPSM_OK;
+}
+
+MPSM_API int mpsm_rmi_fit(mpsm_plan_t* p, const uint64_t* keys, const float* y, uint32_t n, uint64_t kmin,
+                          uint64_t kmax, uint32_t steps, float lr) {
+  if (!p || !keys || !y || kmax < kmin || !(lr > 0.0f)) return MPSM_ERR_INVALID_ARG;
+  int rc = alloc_learn(p);
+  if (rc) return rc;
+  if (n > p->fit_cap) return MPSM_ERR_INVALID_ARG;
+  rc = rmi_slot0(p, n, kmin, kmax, true);
+  if (rc) return rc;
+  if (n) {
+    CK(cudaMemcpyAsync(p->d_fitk, keys, n * sizeof(u64), cudaMemcpyDeviceToDevice, p->st));
+    CK(cudaMemcpyAsync(p->d_fity, y, n * sizeof(float), cudaMemcpyDeviceToDevice, p->st));
+  }
+  launch_fit_data(p->d_models, p->d_tasks, 1, p->d_jobs, p->d_runs, p->xr, nullptr, p->d_fitk, p->d_fity, p->st, p->nsm);
+  launch_train_data(p->d_models, 1, p->d_fitk, p->d_fity, p->d_tx, p->d_ty, p->st);
+  for (u32 t = 1; t <= steps; ++t) {
+    launch_rmi_grad(p->d_models, 1, p->d_tx, p->d_ty, p->d_partial, p->st);
+    launch_rmi_adam(p->d_models, 1, p->d_partial, t, lr, p->st);
+  }
+  launch_rmi_tabulate(p->d_models, 1, p->st);
+  launch_leaf_fit(p->d_models, 1, p->d_leafacc, p->d_fitk, p->d_fity, p->st, p->nsm);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->st));
+  return MPSM_OK;
+}
+
+MPSM_API int mpsm_rmi_predict(mpsm_plan_t* p, uint32_t slot, const uint64_t* keys, uint64_t n, float* yhat,
+                              uint32_t* leaf) {
+  if (!p || slot > 1 || (n && (!keys || !yhat))) return MPSM_ERR_INVALID_ARG;
+  if (!p->d_models) return MPSM_ERR_STATE;
+  launch_rmi_predict(p->d_models + slot, reinterpret_cast<const u64*>(keys), n, yhat, leaf, p->st, p->nsm);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->st));
+  return MPSM_OK;
+}
+
+MPSM_API int mpsm_rmi_export(mpsm_plan_t* p, uint32_t slot, mpsm_rmi_info_t* info, float* theta, uint16_t* cell_leaf,
+                             uint64_t* leaf_base, float* leaf_a, float* leaf_b) {
+  if (!p || slot > 1) return MPSM_ERR_INVALID_ARG;
+  if (!p->d_models) return MPSM_ERR_STATE;
+  RmiModel* h = new (std::nothrow) RmiModel;
+  if (!h) return MPSM_ERR_OOM;
+  CK(cudaStreamSynchronize(p->st));
+  if (cudaMemcpy(h, p->d_models + slot, sizeof(RmiModel), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    delete h;
+    return MPSM_ERR_CUDA;
+  }
+  if (info) {
+    info->kmin = h->kmin;
+    info->kmax = h->kmax;
+    info->cshift = h->cshift;
+    info->ncell = h->ncell;
+    info->fit_n = h->fit_n;
+    info->train_n = h->train_n;
+    info->loss0 = h->loss0;
+    info->loss = h->loss;
+  }
+  if (theta) memcpy(theta, h->theta, RMI_NP * sizeof(float));
+  if (cell_leaf) memcpy(cell_leaf, h->tab, sizeof(h->tab));
+  for (u32 l = 0; l < RMI_LEAVES; ++l) {
+    if (leaf_base) leaf_base[l] = h->leaf[l].base;
+    if (leaf_a) leaf_a[l] = h->leaf[l].a;
+    if (leaf_b) leaf_b[l] = h->leaf[l].b;
+  }
+  delete h;
+  return MPSM_OK;
 }

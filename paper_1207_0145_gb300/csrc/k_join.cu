@@ -13,6 +13,7 @@
 // whose key range covers it and each S tuple once, so the S side is never
 // rescanned per run (the T*|S| term of the paper's cost is avoided by staging).
 #include "mpsm_internal.cuh"
+#include "learn.cuh"
 #include "mpsm_launch.h"
 
 namespace mpsm {
@@ -127,8 +128,10 @@ __device__ __forceinline__ u64 gallop_upper(const Tuple* a, u64 n, u64 from, u64
 // window, since tile key ranges are increasing (Sec. 3.2.2's start search,
 // reusing each result as the next one's lower limit).
 __global__ void k_search(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,
-                         const u64* totals, u32* win) {
+                         const u64* totals, u32* win, LearnCtx lc) {
   const u64 nitems = totals[2];
+  u32 probes = 0, nsearch = 0;
+  u64 err_sum = 0;
   for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < nitems; q += (u64)gridDim.x * blockDim.x) {
     const u32 ji = find_job(jobs, njobs, q, [](const Job& j) { return j.search_base; });
     const Job& J = jobs[ji];
@@ -146,11 +149,35 @@ __global__ void k_search(const Job* jobs, u32 njobs, const Run* runs, const Tupl
       const u64 s0 = J.s_base + t * tile;
       const u64 s1 = (s0 + tile < s_end ? s0 + tile : s_end) - 1;
       const u64 klo = xs[s0].key, khi = xs[s1].key;
-      lb = (t == t0) ? lower_bound_g(a, r.len, klo) : gallop_lower(a, r.len, lb, klo);
+      if (t != t0) {
+        lb = gallop_lower(a, r.len, lb, klo);
+      } else if (lc.models) {
+        // learned start: the R-side model's CDF value times the run length, then an
+        // exact exponential + binary search from there
+        u64 g = (u64)(rmi_predict(&lc.models[2 * ji + 1], klo) * (float)r.len);
+        if (g > r.len) g = r.len;
+        auto at = [&](u64 i) { return a[i].key; };
+        lb = gallop_from(at, r.len, g, klo, probes);
+        err_sum += g > lb ? g - lb : lb - g;
+        ++nsearch;
+      } else {
+        lb = lower_bound_g(a, r.len, klo);
+        probes += bitlen64(r.len);
+        ++nsearch;
+      }
       const u64 ub = gallop_upper(a, r.len, lb, khi);
       const u64 w = J.win_base + t * J.runs + j;
       win[2 * w] = (u32)lb;
       win[2 * w + 1] = (u32)ub;
+    }
+  }
+  if (lc.stat) {
+    const u32 wp = warp_sum(probes), wn = warp_sum(nsearch);
+    const u64 we = warp_sum(err_sum);
+    if (lane_id() == 0 && wn) {
+      atomicAdd(&lc.stat[2], (u64)wp);
+      atomicAdd(&lc.stat[3], (u64)wn);
+      atomicAdd(&lc.stat[4], we);
     }
   }
 }
@@ -440,8 +467,8 @@ void launch_tiles(Job* jobs, u32 njobs, u32 tile, u64* totals, cudaStream_t st) 
 }
 
 void launch_search(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,
-                   const u64* totals, u32* win, cudaStream_t st, int nsm) {
-  k_search<<<nsm * 8, 256, 0, st>>>(jobs, njobs, runs, xr, xs, tile, totals, win);
+                   const u64* totals, u32* win, const LearnCtx& lc, cudaStream_t st, int nsm) {
+  k_search<<<nsm * 8, 256, 0, st>>>(jobs, njobs, runs, xr, xs, tile, totals, win, lc);
 }
 
 void launch_join(u32 mode, Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,

@@ -1,0 +1,547 @@
+// k_learn.cu -- training and tabulation of the learned CDF model on the GPU.
+//
+// Per model (two per job: one over a sorted sample of S, one over positions of
+// the sorted R runs, whose ranks are exact), on the plan's stream:
+//   k_rmi_setup     normalisation range, cell geometry, initial weights
+//   k_fit_data      the model's sample as (key, CDF value) pairs
+//   k_train_data    up to 16384 of them, evenly spaced, as (x, y) in FP32
+//   k_rmi_grad      forward and backward pass of the root MLP, one partial
+//                   gradient per block (128 points)            } x steps
+//   k_rmi_adam      sum of the partials in a fixed order, Adam  }
+//   k_rmi_tabulate  root evaluated at every cell centre -> leaf index
+//   k_leaf_pass<0..2>, k_leaf_solve   least-squares line per leaf
+// The forward/backward pass restates the chain rule of the root
+// h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), yhat = W3 . h2 + b3 under the
+// mean squared error; Adam follows Kingma & Ba (2015) with bias correction.
+#include "learn.cuh"
+#include "mpsm_launch.h"
+
+namespace mpsm {
+
+namespace {
+
+struct LeafAcc {
+  u64 base;
+  u32 cnt, pad;
+  double sd, sy, sdd, sdy;
+};
+
+__device__ __forceinline__ float norm_key(u64 key, u64 kmin, u64 kmax) {
+  if (kmax <= kmin) return 0.0f;
+  const u64 off = key > kmin ? key - kmin : 0ull;
+  const double x = (double)off / (double)(kmax - kmin);
+  return (float)(x < 1.0 ? x : 1.0);
+}
+
+__device__ __forceinline__ u32 key_cell(const RmiModel& M, u64 key) {
+  const u64 off = key > M.kmin ? key - M.kmin : 0ull;
+  const u64 c = off >> M.cshift;
+  return c >= (u64)M.ncell ? M.ncell - 1u : (u32)c;
+}
+
+__device__ __forceinline__ u32 leaf_index(float yhat) {
+  const float f = yhat * (float)RMI_LEAVES;
+  if (f >= (float)(RMI_LEAVES - 1)) return RMI_LEAVES - 1;
+  return f > 0.0f ? (u32)f : 0u;  // NaN lands in leaf 0
+}
+
+// root output at x with the weights in shared (or global) memory
+__device__ __forceinline__ float root_forward(const float* th, float x) {
+  float h1[RMI_H];
+#pragma unroll
+  for (u32 k = 0; k < RMI_H; ++k) h1[k] = fmaxf(fmaf(th[RO_W1 + k], x, th[RO_B1 + k]), 0.0f);
+  float y = th[RO_B3];
+#pragma unroll 4
+  for (u32 j = 0; j < RMI_H; ++j) {
+    float a = th[RO_B2 + j];
+#pragma unroll
+    for (u32 k = 0; k < RMI_H; ++k) a = fmaf(th[RO_W2 + j * RMI_H + k], h1[k], a);
+    y = fmaf(th[RO_W3 + j], fmaxf(a, 0.0f), y);
+  }
+  return y;
+}
+
+__global__ void k_rmi_setup(RmiModel* models, const RmiTask* tasks, const Job* jobs, u32 init) {
+  RmiModel& M = models[blockIdx.x];
+  const RmiTask T = tasks[blockIdx.x];
+  if (threadIdx.x == 0) {
+    u64 lo = T.kmin, hi = T.kmax;
+    if (T.kind != RMI_KIND_GIVEN) {
+      const Job& J = jobs[T.job];
+      lo = J.has_range ? J.kmin : 0ull;
+      hi = J.has_range ? J.kmax : 0ull;
+    }
+    M.kmin = lo;
+    M.kmax = hi;
+    const u32 bits = bitlen64(hi - lo);
+    M.cshift = bits > RMI_CELL_BITS ? bits - RMI_CELL_BITS : 0u;
+    M.ncell = (u32)((hi - lo) >> M.cshift) + 1u;
+    M.fit_off = T.fit_off;
+    M.fit_n = 0;
+    M.train_n = 0;
+    M.loss0 = M.loss = 0.0f;
+    M.active = T.active;
+  }
+  if (init) {
+    for (u32 p = threadIdx.x; p < RMI_NPAD; p += blockDim.x) {
+      float w = 0.0f;  // start at yhat = x: hinges relu(x - k/32), identity middle layer, read out by unit 0
+      if (p < RO_B1) w = 1.0f;
+      else if (p < RO_W2) w = -(float)(p - RO_B1) / (float)RMI_H;
+      else if (p < RO_B2) w = ((p - RO_W2) / RMI_H == (p - RO_W2) % RMI_H) ? 1.0f : 0.0f;
+      else if (p == RO_W3) w = 1.0f;
+      M.theta[p] = w;
+    }
+  }
+  for (u32 p = threadIdx.x; p < RMI_NPAD; p += blockDim.x) {
+    M.m[p] = 0.0f;
+    M.v[p] = 0.0f;
+  }
+}
+
+template <typename KeyAt>
+__device__ __forceinline__ u64 lower_bound_at(KeyAt at, u64 n, u64 key) {
+  u64 a = 0, m = n;
+  while (m > 0) {
+    const u64 h = m >> 1;
+    if (at(a + h) < key) {
+      a += h + 1;
+      m -= h + 1;
+    } else {
+      m = h;
+    }
+  }
+  return a;
+}
+
+__global__ void k_fit_data(RmiModel* models, const RmiTask* tasks, const Job* jobs, const Run* runs, const Tuple* xr,
+                           const Tuple* samp, u64* fitk, float* fity) {
+  RmiModel& M = models[blockIdx.y];
+  const RmiTask T = tasks[blockIdx.y];
+  if (!T.active) return;
+  if (T.kind == RMI_KIND_GIVEN) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) M.fit_n = T.cap;
+    return;
+  }
+  const Job& J = jobs[T.job];
+  u64* fk = fitk + T.fit_off;
+  float* fy = fity + T.fit_off;
+  if (T.kind == RMI_KIND_SAMPLE) {
+    // the in-range slice [a, b) of the sorted sample of S
+    const Tuple* s = samp + T.src_off;
+    auto at = [&](u64 i) { return s[i].key; };
+    u64 a = 0, b = 0;
+    if (J.has_range) {
+      a = lower_bound_at(at, T.cap, J.kmin);
+      b = J.kmax == ~0ull ? T.cap : lower_bound_at(at, T.cap, J.kmax + 1ull);
+    }
+    const u64 n = b - a;
+    if (blockIdx.x == 0 && threadIdx.x == 0) M.fit_n = (u32)n;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+      fk[i] = s[a + i].key;
+      fy[i] = (float)(((double)i + 0.5) / (double)n);
+    }
+  } else {
+    // evenly spaced positions of the job's runs (back to back in xr); a run's rank is exact
+    const u64 m = J.nR ? T.cap : 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) M.fit_n = (u32)m;
+    const Run* rj = runs + J.run_base;
+    for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (u64)gridDim.x * blockDim.x) {
+      const u64 g = ((2 * t + 1) * J.nR) / (2 * m);
+      // run holding position g: last run whose start is <= g
+      u32 lo = 0, hi = J.runs - 1;
+      while (lo < hi) {
+        const u32 mid = (lo + hi + 1) >> 1;
+        if (rj[mid].off - J.r_base <= g) lo = mid;
+        else hi = mid - 1;
+      }
+      const Run r = rj[lo];
+      const u64 q = g - (r.off - J.r_base);
+      fk[t] = xr[J.r_base + g].key;
+      fy[t] = (float)(((double)q + 0.5) / (double)r.len);
+    }
+  }
+}
+
+__global__ void k_train_data(RmiModel* models, const u64* fitk, const float* fity, float* X, float* Y) {
+  RmiModel& M = models[blockIdx.y];
+  if (!M.active) return;
+  const u64 n = M.fit_n;
+  const u32 tn = (u32)(n < RMI_TRAIN_MAX ? n : RMI_TRAIN_MAX);
+  if (blockIdx.x == 0 && threadIdx.x == 0) M.train_n = tn;
+  float* x = X + (u64)blockIdx.y * RMI_TRAIN_MAX;
+  float* y = Y + (u64)blockIdx.y * RMI_TRAIN_MAX;
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < tn; i += gridDim.x * blockDim.x) {
+    const u64 idx = ((2ull * i + 1ull) * n) / (2ull * tn);
+    x[i] = norm_key(fitk[M.fit_off + idx], M.kmin, M.kmax);
+    y[i] = fity[M.fit_off + idx];
+  }
+}
+
+// Forward and backward pass over one block of RMI_GT points.  Shared memory:
+// th[RMI_NPAD] | h1, h2, da2, da1 [RMI_GT][33] | x, g, l [RMI_GT]
+constexpr u32 GP = 33;
+constexpr size_t SMEM_GRAD = (RMI_NPAD + 4 * RMI_GT * GP + 3 * RMI_GT) * sizeof(float);
+
+__global__ void __launch_bounds__(RMI_GT) k_rmi_grad(const RmiModel* models, const float* X, const float* Y,
+                                                     float* partial) {
+  extern __shared__ __align__(16) float gsm[];
+  float* th = gsm;
+  float* sh1 = th + RMI_NPAD;
+  float* sh2 = sh1 + RMI_GT * GP;
+  float* sda2 = sh2 + RMI_GT * GP;
+  float* sda1 = sda2 + RMI_GT * GP;
+  float* sx = sda1 + RMI_GT * GP;
+  float* sg = sx + RMI_GT;
+  float* sl = sg + RMI_GT;
+  const RmiModel& M = models[blockIdx.y];
+  float* out = partial + ((u64)blockIdx.y * RMI_GMAX + blockIdx.x) * RMI_NPAD;
+  const u32 tid = threadIdx.x;
+  const u32 n = M.active ? M.train_n : 0u;
+  if (blockIdx.x * RMI_GT >= n) {  // no points in this block: a zero partial
+    for (u32 p = tid; p < RMI_NPAD; p += RMI_GT) out[p] = 0.0f;
+    return;
+  }
+  for (u32 p = tid; p < RMI_NPAD; p += RMI_GT) th[p] = M.theta[p];
+  __syncthreads();
+  const u32 q = blockIdx.x * RMI_GT + tid;
+  const bool valid = q < n;
+  const float x = valid ? X[(u64)blockIdx.y * RMI_TRAIN_MAX + q] : 0.0f;
+  const float yv = valid ? Y[(u64)blockIdx.y * RMI_TRAIN_MAX + q] : 0.0f;
+  float a1[RMI_H], h2[RMI_H];
+#pragma unroll
+  for (u32 k = 0; k < RMI_H; ++k) a1[k] = fmaf(th[RO_W1 + k], x, th[RO_B1 + k]);
+  float yh = th[RO_B3];
+#pragma unroll 4
+  for (u32 j = 0; j < RMI_H; ++j) {
+    float a = th[RO_B2 + j];
+#pragma unroll
+    for (u32 k = 0; k < RMI_H; ++k) a = fmaf(th[RO_W2 + j * RMI_H + k], fmaxf(a1[k], 0.0f), a);
+    h2[j] = a;  // pre-activation for now
+    yh = fmaf(th[RO_W3 + j], fmaxf(a, 0.0f), yh);
+  }
+  const float r = yh - yv;
+  const float g = valid ? 2.0f * r / (float)n : 0.0f;
+  sx[tid] = x;
+  sg[tid] = g;
+  sl[tid] = valid ? r * r / (float)n : 0.0f;
+  // dL/da2 = g W3 [a2 > 0]; store h2 = relu(a2) and da2
+#pragma unroll
+  for (u32 j = 0; j < RMI_H; ++j) {
+    const bool on = h2[j] > 0.0f;
+    sda2[tid * GP + j] = on ? g * th[RO_W3 + j] : 0.0f;
+    sh2[tid * GP + j] = on ? h2[j] : 0.0f;
+  }
+  // dL/da1 = [a1 > 0] W2^T da2
+#pragma unroll
+  for (u32 k = 0; k < RMI_H; ++k) {
+    float s = 0.0f;
+#pragma unroll 8
+    for (u32 j = 0; j < RMI_H; ++j) s = fmaf(th[RO_W2 + j * RMI_H + k], sda2[tid * GP + j], s);
+    sda1[tid * GP + k] = a1[k] > 0.0f ? (valid ? s : 0.0f) : 0.0f;
+    sh1[tid * GP + k] = valid ? fmaxf(a1[k], 0.0f) : 0.0f;
+  }
+  __syncthreads();
+  // dW2[j][k] = sum_i da2[i][j] h1[i][k]: 8 entries per thread (warp: fixed j, k = lane)
+#pragma unroll
+  for (u32 r8 = 0; r8 < (RMI_H * RMI_H) / RMI_GT; ++r8) {
+    const u32 e = tid + r8 * RMI_GT;
+    const u32 j = e >> 5, k = e & 31u;
+    float s = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) s = fmaf(sda2[i * GP + j], sh1[i * GP + k], s);
+    out[RO_W2 + e] = s;
+  }
+  if (tid < 32) {
+    float w = 0.0f, b = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) {
+      const float d = sda1[i * GP + tid];
+      w = fmaf(d, sx[i], w);
+      b += d;
+    }
+    out[RO_W1 + tid] = w;
+    out[RO_B1 + tid] = b;
+  } else if (tid < 64) {
+    const u32 j = tid - 32;
+    float b = 0.0f, w = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) {
+      b += sda2[i * GP + j];
+      w = fmaf(sg[i], sh2[i * GP + j], w);
+    }
+    out[RO_B2 + j] = b;
+    out[RO_W3 + j] = w;
+  } else if (tid == 64) {
+    float b = 0.0f, l = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) {
+      b += sg[i];
+      l += sl[i];
+    }
+    out[RO_B3] = b;
+    out[RMI_NP] = l;
+  } else if (tid < 64 + 1 + (RMI_NPAD - RMI_NP - 1)) {
+    out[RMI_NP + (tid - 64)] = 0.0f;  // padding slots
+  }
+}
+
+// sum of the block partials of one model, in block order (deterministic)
+__device__ __forceinline__ float sum_partial(const float* partial, u32 mdl, u32 p) {
+  const float* base = partial + (u64)mdl * RMI_GMAX * RMI_NPAD + p;
+  float s = 0.0f;
+  for (u32 b = 0; b < RMI_GMAX; ++b) s += base[(u64)b * RMI_NPAD];
+  return s;
+}
+
+__global__ void __launch_bounds__(1024) k_rmi_adam(RmiModel* models, const float* partial, u32 step, float lr) {
+  RmiModel& M = models[blockIdx.x];
+  if (!M.active || M.train_n == 0) return;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.0f - powf(b1, (float)step);
+  const float c2 = 1.0f - powf(b2, (float)step);
+  for (u32 p = threadIdx.x; p < RMI_NP; p += blockDim.x) {
+    const float g = sum_partial(partial, blockIdx.x, p);
+    const float m = b1 * M.m[p] + (1.0f - b1) * g;
+    const float v = b2 * M.v[p] + (1.0f - b2) * g * g;
+    M.m[p] = m;
+    M.v[p] = v;
+    M.theta[p] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+  }
+  if (threadIdx.x == 0) {
+    const float l = sum_partial(partial, blockIdx.x, RMI_NP);
+    M.loss = l;
+    if (step == 1) M.loss0 = l;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_rmi_reduce(const float* partial, float* grad, float* loss) {
+  for (u32 p = threadIdx.x; p < RMI_NP; p += blockDim.x) grad[p] = sum_partial(partial, 0, p);
+  if (threadIdx.x == 0) *loss = sum_partial(partial, 0, RMI_NP);
+}
+
+__global__ void k_rmi_tabulate(RmiModel* models) {
+  __shared__ float th[RMI_NPAD];
+  RmiModel& M = models[blockIdx.y];
+  if (!M.active) return;
+  for (u32 p = threadIdx.x; p < RMI_NPAD; p += blockDim.x) th[p] = M.theta[p];
+  __syncthreads();
+  const u64 range = M.kmax - M.kmin;
+  for (u32 c = blockIdx.x * blockDim.x + threadIdx.x; c < M.ncell; c += gridDim.x * blockDim.x) {
+    // centre of cell c, clamped to the range
+    const u64 lo = (u64)c << M.cshift;
+    u64 mid = lo + ((1ull << M.cshift) >> 1);
+    if (mid > range) mid = range;
+    const float x = range ? (float)((double)mid / (double)range) : 0.0f;
+    M.tab[c] = (u16)leaf_index(root_forward(th, x));
+  }
+}
+
+__global__ void k_leaf_init(RmiModel* models, LeafAcc* acc) {
+  if (!models[blockIdx.y].active) return;
+  LeafAcc* A = acc + (u64)blockIdx.y * RMI_LEAVES;
+  for (u32 l = blockIdx.x * blockDim.x + threadIdx.x; l < RMI_LEAVES; l += gridDim.x * blockDim.x) {
+    A[l].base = ~0ull;
+    A[l].cnt = 0;
+    A[l].sd = A[l].sy = A[l].sdd = A[l].sdy = 0.0;
+  }
+}
+
+// Pass 0: smallest key and count per leaf; pass 1: sums of d = key - base and y;
+// pass 2: centred sums of d^2 and d*y.  Each thread walks LEAF_CH consecutive fit
+// points (consecutive points mostly share a leaf) and flushes its running sums
+// with one set of atomics per leaf change.
+constexpr u32 LEAF_CH = 16;
+
+template <u32 PASS>
+__global__ void k_leaf_pass(const RmiModel* models, LeafAcc* acc, const u64* fitk, const float* fity) {
+  const RmiModel& M = models[blockIdx.y];
+  if (!M.active) return;
+  LeafAcc* A = acc + (u64)blockIdx.y * RMI_LEAVES;
+  const u64 n = M.fit_n;
+  const u64* fk = fitk + M.fit_off;
+  const float* fy = fity + M.fit_off;
+  for (u64 i0 = ((u64)blockIdx.x * blockDim.x + threadIdx.x) * LEAF_CH; i0 < n;
+       i0 += (u64)gridDim.x * blockDim.x * LEAF_CH) {
+    const u64 i1 = i0 + LEAF_CH < n ? i0 + LEAF_CH : n;
+    u32 cur = 0xFFFFFFFFu;
+    u64 mn = ~0ull;
+    u32 cnt = 0;
+    double s0 = 0.0, s1 = 0.0;
+    u64 base = 0;
+    double dm = 0.0, ym = 0.0;
+    auto flush = [&]() {
+      if (cur == 0xFFFFFFFFu) return;
+      if (PASS == 0) {
+        atomicMin(&A[cur].base, mn);
+        atomicAdd(&A[cur].cnt, cnt);
+      } else if (PASS == 1) {
+        atomicAdd(&A[cur].sd, s0);
+        atomicAdd(&A[cur].sy, s1);
+      } else {
+        atomicAdd(&A[cur].sdd, s0);
+        atomicAdd(&A[cur].sdy, s1);
+      }
+    };
+    for (u64 i = i0; i < i1; ++i) {
+      const u64 key = fk[i];
+      const u32 l = M.tab[key_cell(M, key)];
+      if (l != cur) {
+        flush();
+        cur = l;
+        mn = ~0ull;
+        cnt = 0;
+        s0 = s1 = 0.0;
+        if (PASS > 0) {
+          base = A[l].base;
+          if (PASS == 2) {
+            dm = A[l].sd / (double)A[l].cnt;
+            ym = A[l].sy / (double)A[l].cnt;
+          }
+        }
+      }
+      if (PASS == 0) {
+        mn = key < mn ? key : mn;
+        ++cnt;
+      } else {
+        const double d = (double)(key - base);
+        if (PASS == 1) {
+          s0 += d;
+          s1 += (double)fy[i];
+        } else {
+          const double dd = d - dm;
+          s0 += dd * dd;
+          s1 += dd * ((double)fy[i] - ym);
+        }
+      }
+    }
+    flush();
+  }
+}
+
+__global__ void k_leaf_solve(RmiModel* models, const LeafAcc* acc) {
+  RmiModel& M = models[blockIdx.y];
+  if (!M.active) return;
+  const LeafAcc* A = acc + (u64)blockIdx.y * RMI_LEAVES;
+  for (u32 l = blockIdx.x * blockDim.x + threadIdx.x; l < RMI_LEAVES; l += gridDim.x * blockDim.x) {
+    RmiLeaf L;
+    if (A[l].cnt == 0) {
+      L.base = 0;
+      L.a = 0.0f;
+      L.b = ((float)l + 0.5f) / (float)RMI_LEAVES;
+    } else {
+      const double n = (double)A[l].cnt, dm = A[l].sd / n, ym = A[l].sy / n;
+      const double a = A[l].sdd > 0.0 ? A[l].sdy / A[l].sdd : 0.0;
+      L.base = A[l].base;
+      L.a = (float)a;
+      L.b = (float)(ym - a * dm);
+    }
+    M.leaf[l] = L;
+  }
+}
+
+// Learned partition boundaries: the P - 1 quantiles p/P of the model's sorted
+// in-range sample of S (the empirical inverse CDF the model was trained on),
+// with the sample ranks (#keys < and <= the boundary) of each.
+__global__ void k_learn_bounds(Job* jobs, const RmiModel* models, const u64* fitk, u64* bnd, u32* brank) {
+  Job& J = jobs[blockIdx.x];
+  const RmiModel& M = models[2 * blockIdx.x];
+  const u64 n = M.fit_n;
+  u32 P = J.parts_req ? J.parts_req : 1u;
+  if (P > P_MAX) P = P_MAX;
+  if ((u64)P > n) P = n ? (u32)n : 1u;
+  const u64* fk = fitk + M.fit_off;
+  u64* b = bnd + (u64)blockIdx.x * P_MAX;
+  u32* r = brank + (u64)blockIdx.x * 2 * P_MAX;
+  auto at = [&](u64 i) { return fk[i]; };
+  for (u32 p = threadIdx.x + 1; p < P; p += blockDim.x) {
+    const u64 key = fk[((u64)p * n) / P];
+    b[p - 1] = key;
+    r[2 * (p - 1)] = (u32)lower_bound_at(at, n, key);
+    r[2 * (p - 1) + 1] = key == ~0ull ? (u32)n : (u32)lower_bound_at(at, n, key + 1ull);
+  }
+  if (threadIdx.x == 0) J.parts = P;
+}
+
+// Evenly spaced rows of each job's S, gathered for the sample sort (payload 0).
+__global__ void k_sample_s(const Job* jobs, const u64* samp_off, const u32* samp_n, Tuple* samp) {
+  const Job& J = jobs[blockIdx.y];
+  const u64 m = samp_n[blockIdx.y];
+  Tuple* out = samp + samp_off[blockIdx.y];
+  for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (u64)gridDim.x * blockDim.x) {
+    const u64 row = ((2 * t + 1) * J.nS) / (2 * m);
+    Tuple v;
+    v.key = J.S[row].key;
+    v.pay = 0;
+    out[t] = v;
+  }
+}
+
+__global__ void k_rmi_predict(const RmiModel* M, const u64* keys, u64 n, float* yhat, u32* leaf) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+    const u64 k = keys[i];
+    yhat[i] = rmi_predict(M, k);
+    if (leaf) leaf[i] = M->tab[key_cell(*M, k)];
+  }
+}
+
+}  // namespace
+
+void launch_sample_s(const Job* jobs, u32 njobs, const u64* samp_off, const u32* samp_n, Tuple* samp,
+                     cudaStream_t st, int nsm) {
+  k_sample_s<<<dim3(nsm, njobs), 256, 0, st>>>(jobs, samp_off, samp_n, samp);
+}
+
+void launch_rmi_predict(const RmiModel* M, const u64* keys, u64 n, float* yhat, u32* leaf, cudaStream_t st, int nsm) {
+  if (n) k_rmi_predict<<<nsm * 4, 256, 0, st>>>(M, keys, n, yhat, leaf);
+}
+
+void init_attrs_learn() {
+  cudaFuncSetAttribute(k_rmi_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GRAD);
+}
+
+size_t leaf_acc_bytes() { return sizeof(LeafAcc) * RMI_LEAVES; }
+
+void launch_rmi_setup(RmiModel* models, const RmiTask* tasks, u32 nmodels, const Job* jobs, bool init,
+                      cudaStream_t st) {
+  k_rmi_setup<<<nmodels, 256, 0, st>>>(models, tasks, jobs, init ? 1u : 0u);
+}
+
+void launch_fit_data(RmiModel* models, const RmiTask* tasks, u32 nmodels, const Job* jobs, const Run* runs,
+                     const Tuple* xr, const Tuple* samp, u64* fitk, float* fity, cudaStream_t st, int nsm) {
+  k_fit_data<<<dim3(nsm, nmodels), 256, 0, st>>>(models, tasks, jobs, runs, xr, samp, fitk, fity);
+}
+
+void launch_train_data(RmiModel* models, u32 nmodels, const u64* fitk, const float* fity, float* X, float* Y,
+                       cudaStream_t st) {
+  k_train_data<<<dim3(16, nmodels), 256, 0, st>>>(models, fitk, fity, X, Y);
+}
+
+void launch_rmi_grad(const RmiModel* models, u32 nmodels, const float* X, const float* Y, float* partial,
+                     cudaStream_t st) {
+  k_rmi_grad<<<dim3(RMI_GMAX, nmodels), RMI_GT, SMEM_GRAD, st>>>(models, X, Y, partial);
+}
+
+void launch_rmi_adam(RmiModel* models, u32 nmodels, const float* partial, u32 step, float lr, cudaStream_t st) {
+  k_rmi_adam<<<nmodels, 1024, 0, st>>>(models, partial, step, lr);
+}
+
+void launch_rmi_reduce(const float* partial, float* grad, float* loss, cudaStream_t st) {
+  k_rmi_reduce<<<1, 1024, 0, st>>>(partial, grad, loss);
+}
+
+void launch_rmi_tabulate(RmiModel* models, u32 nmodels, cudaStream_t st) {
+  k_rmi_tabulate<<<dim3(RMI_CELLS / 256, nmodels), 256, 0, st>>>(models);
+}
+
+void launch_leaf_fit(RmiModel* models, u32 nmodels, void* acc, const u64* fitk, const float* fity, cudaStream_t st,
+                     int nsm) {
+  LeafAcc* A = reinterpret_cast<LeafAcc*>(acc);
+  k_leaf_init<<<dim3(16, nmodels), 256, 0, st>>>(models, A);
+  k_leaf_pass<0><<<dim3(nsm, nmodels), 256, 0, st>>>(models, A, fitk, fity);
+  k_leaf_pass<1><<<dim3(nsm, nmodels), 256, 0, st>>>(models, A, fitk, fity);
+  k_leaf_pass<2><<<dim3(nsm, nmodels), 256, 0, st>>>(models, A, fitk, fity);
+  k_leaf_solve<<<dim3(16, nmodels), 256, 0, st>>>(models, A);
+}
+
+void launch_learn_bounds(Job* jobs, u32 njobs, const RmiModel* models, const u64* fitk, u64* bnd, u32* brank,
+                         cudaStream_t st) {
+  k_learn_bounds<<<njobs, 256, 0, st>>>(jobs, models, fitk, bnd, brank);
+}
+
+}  // namespace mpsm

@@ -24,6 +24,7 @@
 
 #include "mpsm.h"
 #include "mpsm_internal.cuh"
+#include "learn.cuh"
 #include "mpsm_launch.h"
 
 namespace mpsm {
@@ -178,7 +179,8 @@ __global__ void k_init_buckets(u64* bmin, u64* bmax, u64* btot, const u64* total
 template <u32 MODE, u32 FCAP>
 __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* nseg_ptr, const LSeg* ls,
                                                   const u64* totals, u64 chunk, Bufs bufs, const Job* jobs,
-                                                  u32 src_where, u32* hist, u64* bmin, u64* bmax, u64* btot) {
+                                                  u32 src_where, u32* hist, u64* bmin, u64* bmax, u64* btot,
+                                                  LearnCtx lc) {
   extern __shared__ __align__(128) unsigned char sm_raw[];
   u64* smin = reinterpret_cast<u64*>(sm_raw);
   u64* smax = smin + FCAP;
@@ -203,10 +205,12 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
     const u64 e = (a + chunk < S.len) ? a + chunk : S.len;
     const Tuple* src = seg_src(bufs, jobs, src_where, S.job, S.off);
     u64 kmin = 0, kmax = ~0ull;
-    if (MODE == MODE_FINE) {
+    if (MODE == MODE_FINE || MODE == MODE_LEARN) {
       kmin = jobs[S.job].kmin;
       kmax = jobs[S.job].kmax;
     }
+    const u64 row0 = S.off - jobs[S.job].s_base;  // MODE_LEARN: row of the tuple in the job's S
+    u32 probes = 0, keys = 0;
     for (u64 t0 = a + threadIdx.x; t0 < e; t0 += NT_PASS * 4) {
       u64 k[4];
 #pragma unroll
@@ -222,6 +226,11 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
         if (MODE == MODE_RADIX) {
           const u64 d = k[i] < L.lo ? 0ull : (k[i] - L.lo) >> L.shift;
           b = d >= F ? F - 1u : (u32)d;
+        } else if (MODE == MODE_LEARN) {
+          if (k[i] < kmin || k[i] > kmax) continue;
+          b = learned_part(&lc.models[2 * S.job], lc.bnd + (u64)S.job * P_MAX, lc.brank + (u64)S.job * 2 * P_MAX, F, k[i],
+                           row0 + t, lc.seed, probes);
+          ++keys;
         } else {
           if (k[i] < kmin || k[i] > kmax) continue;
           b = (u32)((k[i] - kmin) >> L.shift);
@@ -230,6 +239,14 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
         atomicMin(&smin[b], k[i]);
         atomicMax(&smax[b], k[i]);
       }
+    }
+    if (MODE == MODE_LEARN && lc.stat) {
+      const u32 wp = warp_sum(probes), wk = warp_sum(keys);
+      if (lane_id() == 0 && wk) {
+        atomicAdd(&lc.stat[0], (u64)wp);
+        atomicAdd(&lc.stat[1], (u64)wk);
+      }
+      probes = keys = 0;
     }
     __syncthreads();
     u32* hrow = hist + L.hist_base + ci * F;
@@ -298,7 +315,7 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
       const u32 base = (u32)start[b];
       for (u64 c = 0; c < C; ++c) h[c * F + b] += base;
     }
-    if (MODE == MODE_SPLIT) {
+    if (MODE == MODE_SPLIT || MODE == MODE_LEARN) {
       for (u32 b = threadIdx.x; b <= F; b += NT_PASS) part_off[J.part_base + b] = start[b];
       if (threadIdx.x == 0) jobs[S.job].s_kept = total;
     }
@@ -358,7 +375,7 @@ template <u32 MODE>
 __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u32* nseg_ptr, const LSeg* ls,
                                                         const u64* totals, u64 chunk, Bufs bufs, const Job* jobs,
                                                         u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
-                                                        u32* err) {
+                                                        u32* err, LearnCtx lc) {
   constexpr u32 IT = SC_TILE / NT_PASS;
   constexpr u32 DROP = 0xFFFFFFFFu;
   extern __shared__ __align__(128) unsigned char sm_raw[];
@@ -392,12 +409,15 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
       hcnt[b] = 0;
     }
     u64 kmin = 0, kmax = ~0ull;
-    if (MODE == MODE_SPLIT) {
+    if (MODE == MODE_SPLIT || MODE == MODE_LEARN) {
       const Job& J = jobs[S.job];
       kmin = J.kmin;
       kmax = J.kmax;
-      for (u32 f = tid; f < J.nfine; f += NT_PASS) spl[f] = (u16)sp[J.fine_base + f];
+      if (MODE == MODE_SPLIT)
+        for (u32 f = tid; f < J.nfine; f += NT_PASS) spl[f] = (u16)sp[J.fine_base + f];
     }
+    const u64 row0 = S.off - jobs[S.job].s_base;  // MODE_LEARN: row of the segment's first tuple in the job's S
+    u32 probes = 0;
     const u64 a = ci * chunk;
     const u64 e = (a + chunk < S.len) ? a + chunk : S.len;
     const Tuple* src = seg_src(bufs, jobs, src_where, S.job, S.off);
@@ -427,6 +447,10 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
         if (MODE == MODE_RADIX) {
           const u64 d = key < L.lo ? 0ull : (key - L.lo) >> L.shift;
           b = d >= F ? F - 1u : (u32)d;
+        } else if (MODE == MODE_LEARN) {
+          if (key < kmin || key > kmax) continue;
+          b = learned_part(&lc.models[2 * S.job], lc.bnd + (u64)S.job * P_MAX, lc.brank + (u64)S.job * 2 * P_MAX, F, key,
+                           row0 + t0 + x, lc.seed, probes);
         } else {
           if (key < kmin || key > kmax) continue;
           b = spl[(key - kmin) >> L.shift];
@@ -691,6 +715,9 @@ void init_attrs_pass() {
 
   set_smem(k_hist<MODE_RADIX, F_MAX>, F_MAX * 20);
   set_smem(k_hist<MODE_FINE, FINE_MAX>, FINE_MAX * 20);
+  set_smem(k_hist<MODE_LEARN, F_MAX>, F_MAX * 20);
+  set_smem(k_scan<MODE_LEARN>, SMEM_SCAN);
+  set_smem(k_scatter<MODE_LEARN>, SMEM_SCATTER);
   set_smem(k_scan<MODE_RADIX>, SMEM_SCAN);
   set_smem(k_scan<MODE_SPLIT>, SMEM_SCAN);
   set_smem(k_scatter<MODE_RADIX>, SMEM_SCATTER);
@@ -721,15 +748,19 @@ void launch_init_buckets(u64* bmin, u64* bmax, u64* btot, const u64* totals, cud
 
 void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                  Bufs bufs, const Job* jobs, u32 src_where, u32* hist, u64* bmin, u64* bmax, u64* btot,
-                 cudaStream_t st, int nsm) {
+                 const LearnCtx& lc, cudaStream_t st, int nsm) {
   if (mode == MODE_RADIX) {
     const size_t sm = F_MAX * 20;
     k_hist<MODE_RADIX, F_MAX><<<nsm * 4, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs, src_where,
-                                                             hist, bmin, bmax, btot);
+                                                             hist, bmin, bmax, btot, lc);
+  } else if (mode == MODE_LEARN) {
+    const size_t sm = F_MAX * 20;
+    k_hist<MODE_LEARN, F_MAX><<<nsm * 4, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs, src_where,
+                                                             hist, bmin, bmax, btot, lc);
   } else {
     const size_t sm = FINE_MAX * 20;
     k_hist<MODE_FINE, FINE_MAX><<<nsm * 2, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
-                                                               src_where, hist, bmin, bmax, btot);
+                                                               src_where, hist, bmin, bmax, btot, lc);
   }
 }
 
@@ -742,6 +773,10 @@ void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32
     k_scan<MODE_SPLIT><<<nsm * 2, NT_PASS, SMEM_SCAN, st>>>(segs, nseg, ls, hist, bmin, bmax, part_fstart, big_out,
                                                             big_cnt, big_cap, fin_out, fin_cnt, fin_cap, dst_where,
                                                             final_where, jobs, part_off, err);
+  } else if (mode == MODE_LEARN) {
+    k_scan<MODE_LEARN><<<nsm * 2, NT_PASS, SMEM_SCAN, st>>>(segs, nseg, ls, hist, bmin, bmax, part_fstart, big_out,
+                                                            big_cnt, big_cap, fin_out, fin_cnt, fin_cap, dst_where,
+                                                            final_where, jobs, part_off, err);
   } else {
     k_scan<MODE_RADIX><<<nsm * 2, NT_PASS, SMEM_SCAN, st>>>(segs, nseg, ls, hist, bmin, bmax, part_fstart, big_out,
                                                             big_cnt, big_cap, fin_out, fin_cnt, fin_cap, dst_where,
@@ -751,13 +786,16 @@ void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32
 
 void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                     Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
-                    u32* err, cudaStream_t st, int nsm) {
+                    u32* err, const LearnCtx& lc, cudaStream_t st, int nsm) {
   if (mode == MODE_SPLIT) {
     k_scatter<MODE_SPLIT><<<nsm * 2, NT_PASS, SMEM_SCATTER, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
-                                                                  src_where, dst_where, hist, sp, err);
+                                                                  src_where, dst_where, hist, sp, err, lc);
+  } else if (mode == MODE_LEARN) {
+    k_scatter<MODE_LEARN><<<nsm * 2, NT_PASS, SMEM_SCATTER, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
+                                                                  src_where, dst_where, hist, sp, err, lc);
   } else {
     k_scatter<MODE_RADIX><<<nsm * 2, NT_PASS, SMEM_SCATTER, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
-                                                                  src_where, dst_where, hist, sp, err);
+                                                                  src_where, dst_where, hist, sp, err, lc);
   }
 }
 

@@ -41,7 +41,7 @@ enum Where : u32 { W_RIN = 0, W_SIN = 1, W_XR = 2, W_XS = 3, W_Y = 4 };
 constexpr u32 SEG_EXACT = 8u;     // kmin/kmax are the exact extremes of the segment
 
 // bucket functions of a partitioning pass
-enum PassMode : u32 { MODE_RADIX = 0, MODE_FINE = 1, MODE_SPLIT = 2 };
+enum PassMode : u32 { MODE_RADIX = 0, MODE_FINE = 1, MODE_SPLIT = 2, MODE_LEARN = 3 };
 
 // device-side error flags (bit set)
 enum DevErr : u32 {

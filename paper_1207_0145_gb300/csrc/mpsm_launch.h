@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "learn.cuh"
 #include "mpsm_internal.cuh"
 
 namespace mpsm {
@@ -11,6 +12,7 @@ namespace mpsm {
 void init_attrs_pass();
 void init_attrs_split();
 void init_attrs_join();
+void init_attrs_learn();
 
 // ---- partitioning passes (k_pass.cu)
 void launch_sample_bounds(Seg* segs, const u32* nseg, u32 max_segs, Bufs bufs, const Job* jobs, cudaStream_t st);
@@ -19,14 +21,14 @@ void launch_level_plan(const Seg* segs, u32* nseg, u32 seg_cap, LSeg* ls, u64* t
 void launch_init_buckets(u64* bmin, u64* bmax, u64* btot, const u64* totals, cudaStream_t st, int nsm);
 void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                  Bufs bufs, const Job* jobs, u32 src_where, u32* hist, u64* bmin, u64* bmax, u64* btot,
-                 cudaStream_t st, int nsm);
+                 const LearnCtx& lc, cudaStream_t st, int nsm);
 void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32* hist, const u64* bmin,
                  const u64* bmax, const u32* part_fstart, Seg* big_out, u32* big_cnt, u32 big_cap, Seg* fin_out,
                  u32* fin_cnt, u32 fin_cap, u32 dst_where, Job* jobs, u64* part_off, u32* err, cudaStream_t st,
                  int nsm);
 void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                     Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
-                    u32* err, cudaStream_t st, int nsm);
+                    u32* err, const LearnCtx& lc, cudaStream_t st, int nsm);
 void launch_seg_sort(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs,
                      u32 dst_where, u32* err, cudaStream_t st, int nsm);
 void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st);
@@ -43,12 +45,46 @@ void launch_fold(const Seg* segs, const u32* nseg, const LSeg* ls_fine, const LS
 // ---- join (k_join.cu)
 void launch_tiles(Job* jobs, u32 njobs, u32 tile, u64* totals, cudaStream_t st);
 void launch_search(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,
-                   const u64* totals, u32* win, cudaStream_t st, int nsm);
+                   const u64* totals, u32* win, const LearnCtx& lc, cudaStream_t st, int nsm);
 void launch_join(u32 mode, Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,
                  const u64* totals, const u32* win, u64* tile_cnt, const u64* tile_out, Tuple* pairs,
                  u32* err, cudaStream_t st, int nsm);
 void launch_pair_offsets(Job* jobs, u32 njobs, const u64* totals, const u64* tile_cnt, u64* tile_out,
                          u64* pair_total, cudaStream_t st);
+
+// ---- learned CDF model (k_learn.cu)
+enum RmiKind : u32 {
+  RMI_KIND_SAMPLE = 0,  // a sorted sample of S (the sub-plan's runs); fit points = its slice inside R's range
+  RMI_KIND_RUNS = 1,    // evenly spaced positions of the job's sorted R runs
+  RMI_KIND_GIVEN = 2    // fit points written by the caller; range given in the task
+};
+struct RmiTask {
+  u64 fit_off;          // first fit point (keys / CDF values) of the model
+  u64 src_off;          // RMI_KIND_SAMPLE: first tuple of the job's sorted sample
+  u64 kmin, kmax;       // RMI_KIND_GIVEN: normalisation range
+  u32 job, kind;
+  u32 cap;              // sample size / fit points
+  u32 active;
+};
+size_t leaf_acc_bytes();
+void launch_rmi_setup(RmiModel* models, const RmiTask* tasks, u32 nmodels, const Job* jobs, bool init,
+                      cudaStream_t st);
+void launch_fit_data(RmiModel* models, const RmiTask* tasks, u32 nmodels, const Job* jobs, const Run* runs,
+                     const Tuple* xr, const Tuple* samp, u64* fitk, float* fity, cudaStream_t st, int nsm);
+void launch_train_data(RmiModel* models, u32 nmodels, const u64* fitk, const float* fity, float* X, float* Y,
+                       cudaStream_t st);
+void launch_rmi_grad(const RmiModel* models, u32 nmodels, const float* X, const float* Y, float* partial,
+                     cudaStream_t st);
+void launch_rmi_adam(RmiModel* models, u32 nmodels, const float* partial, u32 step, float lr, cudaStream_t st);
+void launch_rmi_reduce(const float* partial, float* grad, float* loss, cudaStream_t st);
+void launch_rmi_tabulate(RmiModel* models, u32 nmodels, cudaStream_t st);
+void launch_leaf_fit(RmiModel* models, u32 nmodels, void* acc, const u64* fitk, const float* fity, cudaStream_t st,
+                     int nsm);
+void launch_learn_bounds(Job* jobs, u32 njobs, const RmiModel* models, const u64* fitk, u64* bnd, u32* brank,
+                         cudaStream_t st);
+void launch_sample_s(const Job* jobs, u32 njobs, const u64* samp_off, const u32* samp_n, Tuple* samp,
+                     cudaStream_t st, int nsm);
+void launch_rmi_predict(const RmiModel* M, const u64* keys, u64 n, float* yhat, u32* leaf, cudaStream_t st, int nsm);
 
 enum JoinMode : u32 { JOIN_AGG = 0, JOIN_COUNT = 1, JOIN_WRITE = 2 };
 

@@ -30,7 +30,7 @@ _p = ctypes.c_void_p
 class Options(ctypes.Structure):
     _fields_ = [("runs_r", _u32), ("partitions_s", _u32), ("fine_bits", _u32), ("radix_bits", _u32),
                 ("join_tile", _u32), ("splitter_mode", _i32), ("search_mode", _i32), ("flags", _u32),
-                ("seed", _u64), ("reserved", _u32 * 6)]
+                ("seed", _u64), ("learn_steps", _u32), ("reserved", _u32 * 5)]
 
 
 class Pairs(ctypes.Structure):
@@ -48,10 +48,21 @@ class Stats(ctypes.Structure):
                 ("partitions_s", _u32), ("nfine", _u32), ("fine_shift", _u32), ("s_kept", _u64),
                 ("part_max", _u64), ("imbalance", ctypes.c_double), ("mean_window", ctypes.c_double),
                 ("tiles", _u64), ("levels_r", _u32), ("levels_s", _u32), ("segments_r", _u64),
-                ("segments_s", _u64), ("launches", _u32), ("pad", _u32)]
+                ("segments_s", _u64), ("launches", _u32), ("pad", _u32),
+                ("loss_s0", ctypes.c_float), ("loss_s", ctypes.c_float), ("loss_r0", ctypes.c_float),
+                ("loss_r", ctypes.c_float), ("part_probes", ctypes.c_double), ("search_probes", ctypes.c_double),
+                ("search_err", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RmiInfo(ctypes.Structure):
+    _fields_ = [("kmin", _u64), ("kmax", _u64), ("cshift", _u32), ("ncell", _u32), ("fit_n", _u32),
+                ("train_n", _u32), ("loss0", ctypes.c_float), ("loss", ctypes.c_float)]
+
+
+RMI_NPARAM, RMI_LEAVES, RMI_CELLS = 1153, 4096, 65536
 
 
 class KernelTime(ctypes.Structure):
@@ -95,6 +106,11 @@ def lib():
             "mpsm_plan_set_flags": ([_p, _u32], ctypes.c_int),
             "mpsm_plan_kernel_times": ([_p, P(KernelTime), _u32, P(_u32)], ctypes.c_int),
             "mpsm_sort_runs_noalloc": ([_p, _u64, _u32, _p, _p], ctypes.c_int),
+            "mpsm_rmi_loss_grad": ([_p, _p, _p, _u32, _p, _p, P(ctypes.c_float)], ctypes.c_int),
+            "mpsm_rmi_train": ([_p, _p, _p, _u32, _u32, ctypes.c_float, _p, P(ctypes.c_float)], ctypes.c_int),
+            "mpsm_rmi_fit": ([_p, _p, _p, _u32, _u64, _u64, _u32, ctypes.c_float], ctypes.c_int),
+            "mpsm_rmi_predict": ([_p, _u32, _p, _u64, _p, _p], ctypes.c_int),
+            "mpsm_rmi_export": ([_p, _u32, P(RmiInfo), _p, _p, _p, _p, _p], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -126,17 +142,66 @@ def _tuples(t) -> Tuple[int, int]:
 
 def make_options(runs_r=0, partitions_s=0, fine_bits=0, radix_bits=0, join_tile=0, splitter_mode=SPLIT_HIST,
                  search_mode=SEARCH_BINARY, timing=False, kernel_timing=False, flags=0,
-                 seed=20120145) -> Options:
+                 seed=20120145, learn_steps=0) -> Options:
     o = Options()
     lib().mpsm_options_default(ctypes.byref(o))
     o.runs_r, o.partitions_s, o.fine_bits, o.radix_bits, o.join_tile = runs_r, partitions_s, fine_bits, radix_bits, join_tile
     o.splitter_mode, o.search_mode = splitter_mode, search_mode
     o.flags = (FLAG_TIMING if timing else 0) | (FLAG_KERNEL_TIMING if kernel_timing else 0) | flags
     o.seed = seed
+    o.learn_steps = learn_steps
     return o
 
 
-class Plan:
+class _RmiMixin:
+    """The learned CDF model's entry points on caller data (device float32 / uint64 tensors)."""
+
+    def rmi_loss_grad(self, x, y, theta):
+        import torch
+
+        grad = torch.empty(RMI_NPARAM, dtype=torch.float32, device=x.device)
+        loss = ctypes.c_float()
+        _check(lib().mpsm_rmi_loss_grad(self.handle, x.data_ptr(), y.data_ptr(), x.numel(), theta.data_ptr(),
+                                        grad.data_ptr(), ctypes.byref(loss)), "mpsm_rmi_loss_grad")
+        return loss.value, grad
+
+    def rmi_train(self, x, y, theta, steps: int, lr: float):
+        """Adam steps from theta (updated in place); returns the loss before each step."""
+        losses = (ctypes.c_float * max(steps, 1))()
+        _check(lib().mpsm_rmi_train(self.handle, x.data_ptr(), y.data_ptr(), x.numel(), steps, lr, theta.data_ptr(),
+                                    losses), "mpsm_rmi_train")
+        return list(losses)[:steps]
+
+    def rmi_fit(self, keys, y, kmin: int, kmax: int, steps: int = 200, lr: float = 3e-3):
+        _check(lib().mpsm_rmi_fit(self.handle, keys.data_ptr(), y.data_ptr(), keys.numel(), kmin, kmax, steps, lr),
+               "mpsm_rmi_fit")
+
+    def rmi_predict(self, keys, slot: int = 0):
+        import torch
+
+        yhat = torch.empty(keys.numel(), dtype=torch.float32, device=keys.device)
+        leaf = torch.empty(keys.numel(), dtype=torch.int32, device=keys.device)
+        _check(lib().mpsm_rmi_predict(self.handle, slot, keys.data_ptr(), keys.numel(), yhat.data_ptr(), leaf.data_ptr()),
+               "mpsm_rmi_predict")
+        return yhat, leaf
+
+    def rmi_export(self, slot: int = 0) -> dict:
+        import numpy as np
+
+        info = RmiInfo()
+        theta = np.empty(RMI_NPARAM, dtype=np.float32)
+        tab = np.empty(RMI_CELLS, dtype=np.uint16)
+        base = np.empty(RMI_LEAVES, dtype=np.uint64)
+        a = np.empty(RMI_LEAVES, dtype=np.float32)
+        b = np.empty(RMI_LEAVES, dtype=np.float32)
+        _check(lib().mpsm_rmi_export(self.handle, slot, ctypes.byref(info), theta.ctypes.data, tab.ctypes.data,
+                                     base.ctypes.data, a.ctypes.data, b.ctypes.data), "mpsm_rmi_export")
+        d = {k: getattr(info, k) for k, _ in info._fields_}
+        d.update(theta=theta, cell_leaf=tab, leaf_base=base, leaf_a=a, leaf_b=b)
+        return d
+
+
+class Plan(_RmiMixin):
     """A join plan: owns the device scratch for joins up to (max_nR, max_nS)."""
 
     def __init__(self, max_nR: int, max_nS: int, max_jobs: int = 1, stream: Optional[int] = None, **options):

@@ -53,7 +53,9 @@ int main(void) {
   printf("mpsm_view_t %zu\n", sizeof(mpsm_view_t));
   printf("mpsm_job_t %zu\n", sizeof(mpsm_job_t));
   printf("mpsm_pairs_t %zu\n", sizeof(mpsm_pairs_t));
-  F(mpsm_options_t, seed); F(mpsm_options_t, flags);
+  F(mpsm_options_t, seed); F(mpsm_options_t, flags); F(mpsm_options_t, learn_steps);
+  printf("mpsm_rmi_info_t %zu\n", sizeof(mpsm_rmi_info_t));
+  F(mpsm_stats_t, loss_s0); F(mpsm_stats_t, part_probes); F(mpsm_stats_t, search_err);
   F(mpsm_stats_t, s_kept); F(mpsm_stats_t, imbalance); F(mpsm_stats_t, tiles); F(mpsm_stats_t, segments_s);
   F(mpsm_stats_t, launches);
   printf("mpsm_kernel_time_t %zu\n", sizeof(mpsm_kernel_time_t));
@@ -77,6 +79,7 @@ def test_ctypes_structs_match_header(tmp_path):
     assert int(got["mpsm_job_t"]) == ctypes.sizeof(M.JobDesc)
     assert int(got["mpsm_pairs_t"]) == ctypes.sizeof(M.Pairs)
     assert int(got["mpsm_kernel_time_t"]) == ctypes.sizeof(M.KernelTime)
+    assert int(got["mpsm_rmi_info_t"]) == ctypes.sizeof(M.RmiInfo)
     for key, val in got.items():
         if "." not in key:
             continue
