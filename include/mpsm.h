@@ -74,7 +74,8 @@ typedef struct {
   uint32_t flags;          /* MPSM_FLAG_*                                                    */
   uint64_t seed;           /* seed of the hash that spreads hot keys over learned partitions */
   uint32_t learn_steps;    /* Adam steps of the learned model; 0 = 200                       */
-  uint32_t reserved[5];    /* must be zero                                                   */
+  uint32_t run_len;        /* target R tuples per run when runs_r = 0; 0 = automatic          */
+  uint32_t reserved[4];    /* must be zero                                                   */
 } mpsm_options_t;
 
 /* Fills *opt with the defaults (all automatic, histogram splitters, binary search). */
@@ -149,6 +150,28 @@ typedef struct {
  * replay.  jobs: HOST array.  out_counts / out_checksums: HOST arrays of njobs. */
 int mpsm_join_batch(mpsm_plan_t* plan, const mpsm_job_t* jobs, uint32_t njobs,
                     uint64_t* out_counts, uint64_t* out_checksums);
+
+/* ---- tuning ------------------------------------------------------------------
+ * The knobs the autotuner sets (0 = automatic, as in mpsm_options_t): the
+ * largest radix fan-out (log2), S tuples per join tile, target R tuples per run,
+ * and the number of S partitions. */
+typedef struct {
+  uint32_t radix_bits, join_tile, run_len, partitions_s;
+} mpsm_tuning_t;
+
+/* Replaces the plan's tunable options for later calls (invalid values:
+ * MPSM_ERR_INVALID_ARG).  A captured batch graph is dropped. */
+int mpsm_plan_set_tuning(mpsm_plan_t* plan, const mpsm_tuning_t* tuning);
+
+/* Autotuner for batched joins (no counterpart in the paper): runs `jobs` through
+ * mpsm_join_batch under each candidate tuning -- radix fan-out 2^9 or 2^11, join
+ * tile 2048 or 4096, automatic runs or runs of about 2^23 tuples -- once to warm
+ * up (capturing its graph) and `reps` times timed on the host clock, checks that
+ * every candidate returns the same per-job results, and leaves the fastest set
+ * on the plan.  Writes it to *best and its mean time per batch to *best_ms
+ * (HOST).  Returns MPSM_ERR_DEVICE if two candidates disagree. */
+int mpsm_autotune(mpsm_plan_t* plan, const mpsm_job_t* jobs, uint32_t njobs, uint32_t reps, mpsm_tuning_t* best,
+                  float* best_ms);
 
 /* ---- introspection --------------------------------------------------------- */
 

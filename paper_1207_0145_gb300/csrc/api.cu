@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <new>
 #include <vector>
 
@@ -121,6 +122,7 @@ struct mpsm_plan {
   // batched graph
   cudaGraphExec_t gexec = nullptr;
   std::vector<u64> gsig;
+  u32 graph_launches = 0;           // kernels in the captured graph
   // learned CDF model (allocated on first use)
   bool learn = false;               // the current call uses a learned mode
   RmiModel* d_models = nullptr;     // 2 per job
@@ -211,7 +213,9 @@ u32 auto_parts(u64 nS) {
 }
 
 u32 runs_for(const mpsm_plan* p, u64 nR) {
-  u32 t = p->opt.runs_r ? p->opt.runs_r : auto_runs(nR);
+  u32 t = p->opt.runs_r ? p->opt.runs_r
+                        : (p->opt.run_len ? (u32)std::min<u64>((nR + p->opt.run_len - 1) / p->opt.run_len, RUNS_MAX)
+                                          : auto_runs(nR));
   if (nR && t > nR) t = (u32)nR;
   return std::max<u32>(1, std::min<u32>(t, RUNS_MAX));
 }
@@ -226,6 +230,7 @@ LearnCtx lctx(const mpsm_plan* p, bool models) {
   c.models = models ? p->d_models : nullptr;
   c.bnd = p->d_bnd;
   c.brank = p->d_brank;
+  c.cell = p->d_sp;  // the fine bucket -> partition array doubles as the learned cell table
   c.seed = p->opt.seed;
   c.stat = p->d_lstat;
   return c;
@@ -547,6 +552,7 @@ int phase_learn(mpsm_plan* p) {
 int phase_splitters_learned(mpsm_plan* p) {
   u64* ts = p->d_tot + T_SPLIT;
   LAUNCH(K_LEARN_BOUNDS, launch_learn_bounds(p->d_jobs, p->njobs, p->d_models, p->d_fitk, p->d_bnd, p->d_brank, p->st));
+  LAUNCH(K_LEARN_BOUNDS, launch_learn_cells(p->d_jobs, p->njobs, p->d_bnd, p->d_sp, p->st));
   LAUNCH(K_PLAN, launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls2, ts, MODE_LEARN, p->ch_s, 11,
                                    p->d_jobs, p->hist_a_cap, p->bucket_cap, &p->d_cnt[C_ERR], p->st));
   LAUNCH(K_INIT, launch_init_buckets(p->d_bmin, p->d_bmax, nullptr, ts, p->st, p->nsm));
@@ -766,7 +772,7 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   mpsm_options_t o;
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
       if (o.reserved[i]) return MPSM_ERR_INVALID_ARG;
   } else {
     mpsm_options_default(&o);
@@ -1027,6 +1033,7 @@ MPSM_API int mpsm_join_batch(mpsm_plan_t* p, const mpsm_job_t* jobs, uint32_t nj
       return prc;
     }
     if (ce != cudaSuccess) return MPSM_ERR_CUDA;
+    p->graph_launches = p->launches;
     ce = cudaGraphInstantiate(&p->gexec, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return MPSM_ERR_CUDA;
@@ -1034,6 +1041,7 @@ MPSM_API int mpsm_join_batch(mpsm_plan_t* p, const mpsm_job_t* jobs, uint32_t nj
   }
   record(p, EV_START);
   CK(cudaGraphLaunch(p->gexec, p->st));
+  p->launches = p->graph_launches;
   record(p, EV_JOIN);
   CK(cudaMemcpyAsync(p->h_jobs, p->d_jobs, njobs * sizeof(Job), cudaMemcpyDeviceToHost, p->st));
   rc = read_err(p);
@@ -1356,4 +1364,63 @@ MPSM_API int mpsm_rmi_export(mpsm_plan_t* p, uint32_t slot, mpsm_rmi_info_t* inf
   }
   delete h;
   return MPSM_OK;
+}
+
+// ============================================================== tuning
+
+MPSM_API int mpsm_plan_set_tuning(mpsm_plan_t* p, const mpsm_tuning_t* t) {
+  if (!p || !t) return MPSM_ERR_INVALID_ARG;
+  if (t->radix_bits && (t->radix_bits < 4 || t->radix_bits > 11)) return MPSM_ERR_INVALID_ARG;
+  if (t->join_tile && (t->join_tile < 256 || t->join_tile > TILE_MAX || t->join_tile % 256)) return MPSM_ERR_INVALID_ARG;
+  if (t->partitions_s > P_MAX) return MPSM_ERR_INVALID_ARG;
+  p->opt.radix_bits = t->radix_bits;
+  p->opt.join_tile = t->join_tile;
+  p->opt.run_len = t->run_len;
+  p->opt.partitions_s = t->partitions_s;
+  p->tile = t->join_tile ? t->join_tile : TILE_MAX;
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  p->gsig.clear();
+  return MPSM_OK;
+}
+
+MPSM_API int mpsm_autotune(mpsm_plan_t* p, const mpsm_job_t* jobs, uint32_t njobs, uint32_t reps, mpsm_tuning_t* best,
+                           float* best_ms) {
+  if (!p || !jobs || !njobs || !best || !best_ms) return MPSM_ERR_INVALID_ARG;
+  if (reps == 0) reps = 1;
+  std::vector<mpsm_tuning_t> cand;
+  for (u32 rb : {11u, 9u})
+    for (u32 tile : {4096u, 2048u})
+      for (u32 rl : {0u, 1u << 23}) cand.push_back(mpsm_tuning_t{rb, tile, rl, p->opt.partitions_s});
+  std::vector<uint64_t> c0(njobs), s0(njobs), c(njobs), s(njobs);
+  float best_t = 0;
+  int best_i = -1;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    int rc = mpsm_plan_set_tuning(p, &cand[i]);
+    if (rc) return rc;
+    rc = mpsm_join_batch(p, jobs, njobs, c.data(), s.data());  // capture + warm-up
+    if (rc) return rc;
+    if (i == 0) {
+      c0 = c;
+      s0 = s;
+    } else if (c != c0 || s != s0) {
+      return MPSM_ERR_DEVICE;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (u32 r = 0; r < reps; ++r) {
+      rc = mpsm_join_batch(p, jobs, njobs, c.data(), s.data());
+      if (rc) return rc;
+    }
+    const float ms =
+        std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count() / (float)reps;
+    if (best_i < 0 || ms < best_t) {
+      best_t = ms;
+      best_i = (int)i;
+    }
+  }
+  *best = cand[best_i];
+  *best_ms = best_t;
+  return mpsm_plan_set_tuning(p, best);
 }

@@ -458,6 +458,24 @@ __global__ void k_learn_bounds(Job* jobs, const RmiModel* models, const u64* fit
   if (threadIdx.x == 0) J.parts = P;
 }
 
+// Fine-cell table: for each fine bucket [lo, hi] of the job's key range, the
+// partition its keys fall in when no boundary lies in [lo, hi], else the first
+// partition it reaches, marked LCELL_SPLIT (those keys search the boundaries).
+__global__ void k_learn_cells(const Job* jobs, const u64* bnd, u32* cell) {
+  const Job& J = jobs[blockIdx.x];
+  const u32 nb = J.parts ? J.parts - 1u : 0u;
+  const u64* b = bnd + (u64)blockIdx.x * P_MAX;
+  auto at = [&](u64 i) { return b[i]; };
+  for (u32 f = threadIdx.x; f < J.nfine; f += blockDim.x) {
+    const u64 lo = J.kmin + ((u64)f << J.fine_shift);
+    const u64 w = (J.fine_shift >= 64) ? ~0ull : ((1ull << J.fine_shift) - 1ull);
+    const u64 hi = (J.kmax - lo < w) ? J.kmax : lo + w;
+    const u32 plo = (u32)lower_bound_at(at, nb, lo);                                    // #bnd < lo
+    const u32 phi = hi == ~0ull ? nb : (u32)lower_bound_at(at, nb, hi + 1ull);          // #bnd <= hi
+    cell[J.fine_base + f] = plo == phi ? plo : (plo | LCELL_SPLIT);
+  }
+}
+
 // Evenly spaced rows of each job's S, gathered for the sample sort (payload 0).
 __global__ void k_sample_s(const Job* jobs, const u64* samp_off, const u32* samp_n, Tuple* samp) {
   const Job& J = jobs[blockIdx.y];
@@ -485,6 +503,10 @@ __global__ void k_rmi_predict(const RmiModel* M, const u64* keys, u64 n, float* 
 void launch_sample_s(const Job* jobs, u32 njobs, const u64* samp_off, const u32* samp_n, Tuple* samp,
                      cudaStream_t st, int nsm) {
   k_sample_s<<<dim3(nsm, njobs), 256, 0, st>>>(jobs, samp_off, samp_n, samp);
+}
+
+void launch_learn_cells(const Job* jobs, u32 njobs, const u64* bnd, u32* cell, cudaStream_t st) {
+  k_learn_cells<<<njobs, 1024, 0, st>>>(jobs, bnd, cell);
 }
 
 void launch_rmi_predict(const RmiModel* M, const u64* keys, u64 n, float* yhat, u32* leaf, cudaStream_t st, int nsm) {

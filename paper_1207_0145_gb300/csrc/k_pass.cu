@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
   u64* smin = reinterpret_cast<u64*>(sm_raw);
   u64* smax = smin + FCAP;
   u32* scnt = reinterpret_cast<u32*>(smax + FCAP);
+  u16* scell = reinterpret_cast<u16*>(scnt + FCAP);  // MODE_LEARN: fine cell -> partition (FINE_MAX)
   __shared__ u32 s_seg;
   const u64 nch = totals[0];
   const u32 nseg = *nseg_ptr;
@@ -211,6 +212,11 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
     }
     const u64 row0 = S.off - jobs[S.job].s_base;  // MODE_LEARN: row of the tuple in the job's S
     u32 probes = 0, keys = 0;
+    if (MODE == MODE_LEARN) {
+      const Job& J = jobs[S.job];
+      for (u32 f = threadIdx.x; f < J.nfine; f += NT_PASS) scell[f] = (u16)lc.cell[J.fine_base + f];
+      __syncthreads();
+    }
     for (u64 t0 = a + threadIdx.x; t0 < e; t0 += NT_PASS * 4) {
       u64 k[4];
 #pragma unroll
@@ -228,8 +234,11 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
           b = d >= F ? F - 1u : (u32)d;
         } else if (MODE == MODE_LEARN) {
           if (k[i] < kmin || k[i] > kmax) continue;
-          b = learned_part(&lc.models[2 * S.job], lc.bnd + (u64)S.job * P_MAX, lc.brank + (u64)S.job * 2 * P_MAX, F, k[i],
-                           row0 + t, lc.seed, probes);
+          const u32 e = scell[(k[i] - kmin) >> L.shift];
+          b = e;
+          if (e & LCELL_SPLIT)
+            b = learned_part(&lc.models[2 * S.job], lc.bnd + (u64)S.job * P_MAX, lc.brank + (u64)S.job * 2 * P_MAX, F,
+                             k[i], row0 + t, lc.seed, probes, e & ~LCELL_SPLIT);
           ++keys;
         } else {
           if (k[i] < kmin || k[i] > kmax) continue;
@@ -413,8 +422,7 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
       const Job& J = jobs[S.job];
       kmin = J.kmin;
       kmax = J.kmax;
-      if (MODE == MODE_SPLIT)
-        for (u32 f = tid; f < J.nfine; f += NT_PASS) spl[f] = (u16)sp[J.fine_base + f];
+      for (u32 f = tid; f < J.nfine; f += NT_PASS) spl[f] = (u16)(MODE == MODE_SPLIT ? sp : lc.cell)[J.fine_base + f];
     }
     const u64 row0 = S.off - jobs[S.job].s_base;  // MODE_LEARN: row of the segment's first tuple in the job's S
     u32 probes = 0;
@@ -449,8 +457,11 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
           b = d >= F ? F - 1u : (u32)d;
         } else if (MODE == MODE_LEARN) {
           if (key < kmin || key > kmax) continue;
-          b = learned_part(&lc.models[2 * S.job], lc.bnd + (u64)S.job * P_MAX, lc.brank + (u64)S.job * 2 * P_MAX, F, key,
-                           row0 + t0 + x, lc.seed, probes);
+          const u32 e = spl[(key - kmin) >> L.shift];
+          b = e;
+          if (e & LCELL_SPLIT)
+            b = learned_part(&lc.models[2 * S.job], lc.bnd + (u64)S.job * P_MAX, lc.brank + (u64)S.job * 2 * P_MAX, F,
+                             key, row0 + t0 + x, lc.seed, probes, e & ~LCELL_SPLIT);
         } else {
           if (key < kmin || key > kmax) continue;
           b = spl[(key - kmin) >> L.shift];
@@ -715,7 +726,7 @@ void init_attrs_pass() {
 
   set_smem(k_hist<MODE_RADIX, F_MAX>, F_MAX * 20);
   set_smem(k_hist<MODE_FINE, FINE_MAX>, FINE_MAX * 20);
-  set_smem(k_hist<MODE_LEARN, F_MAX>, F_MAX * 20);
+  set_smem(k_hist<MODE_LEARN, F_MAX>, F_MAX * 20 + FINE_MAX * 2);
   set_smem(k_scan<MODE_LEARN>, SMEM_SCAN);
   set_smem(k_scatter<MODE_LEARN>, SMEM_SCATTER);
   set_smem(k_scan<MODE_RADIX>, SMEM_SCAN);
@@ -754,7 +765,7 @@ void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, con
     k_hist<MODE_RADIX, F_MAX><<<nsm * 4, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs, src_where,
                                                              hist, bmin, bmax, btot, lc);
   } else if (mode == MODE_LEARN) {
-    const size_t sm = F_MAX * 20;
+    const size_t sm = F_MAX * 20 + FINE_MAX * 2;
     k_hist<MODE_LEARN, F_MAX><<<nsm * 4, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs, src_where,
                                                              hist, bmin, bmax, btot, lc);
   } else {

@@ -131,11 +131,12 @@ __device__ __forceinline__ u64 mix64(u64 z) {
 // each tuple takes the partition of a point drawn from that share by a hash of its
 // row -- a hot key fills its partitions to the mean instead of making one huge.
 // The model's prediction floor(P * yhat) is the starting guess of the exact search.
+// `hint` (< P) replaces the model's guess when the caller knows a closer one.
 __device__ __forceinline__ u32 learned_part(const RmiModel* M, const u64* bnd, const u32* rank, u32 P, u64 key,
-                                             u64 row, u64 seed, u32& probes) {
+                                             u64 row, u64 seed, u32& probes, u32 hint = 0xFFFFFFFFu) {
   const u32 nb = P - 1u;
   if (nb == 0) return 0u;
-  u32 g = (u32)(rmi_predict(M, key) * (float)P);
+  u32 g = hint != 0xFFFFFFFFu ? hint : (u32)(rmi_predict(M, key) * (float)P);
   if (g > nb) g = nb;
   auto at = [&](u64 i) { return __ldg(&bnd[i]); };
   const u32 lb = (u32)gallop_from(at, nb, g, key, probes);
@@ -149,10 +150,16 @@ __device__ __forceinline__ u32 learned_part(const RmiModel* M, const u64* bnd, c
   return q > ub ? ub : q;
 }
 
+// Fine-cell table of the learned partitions (one u16 per fine bucket of the job):
+// the partition of every key in the cell, or -- with LCELL_SPLIT set -- the first
+// partition the cell reaches when a boundary falls inside it.
+constexpr u32 LCELL_SPLIT = 0x8000u;
+
 struct LearnCtx {
   const RmiModel* models;   // 2 per job: [2 j] = S-side model, [2 j + 1] = R-side model
   const u64* bnd;           // per job P_MAX learned partition boundaries
   const u32* brank;         // per job 2 P_MAX sample ranks of the boundaries (< and <=)
+  const u32* cell;          // per job FINE_MAX fine-cell table (LCELL_SPLIT marks cells a boundary cuts)
   u64 seed;                 // seed of the hot-key spreading hash
   u64* stat;                // [0] partition probes, [1] keys partitioned, [2] search probes,
                             // [3] searches, [4] sum of |prediction - exact| start positions

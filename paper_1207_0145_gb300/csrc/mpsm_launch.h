@@ -84,6 +84,7 @@ void launch_learn_bounds(Job* jobs, u32 njobs, const RmiModel* models, const u64
                          cudaStream_t st);
 void launch_sample_s(const Job* jobs, u32 njobs, const u64* samp_off, const u32* samp_n, Tuple* samp,
                      cudaStream_t st, int nsm);
+void launch_learn_cells(const Job* jobs, u32 njobs, const u64* bnd, u32* cell, cudaStream_t st);
 void launch_rmi_predict(const RmiModel* M, const u64* keys, u64 n, float* yhat, u32* leaf, cudaStream_t st, int nsm);
 
 enum JoinMode : u32 { JOIN_AGG = 0, JOIN_COUNT = 1, JOIN_WRITE = 2 };

@@ -30,7 +30,11 @@ _p = ctypes.c_void_p
 class Options(ctypes.Structure):
     _fields_ = [("runs_r", _u32), ("partitions_s", _u32), ("fine_bits", _u32), ("radix_bits", _u32),
                 ("join_tile", _u32), ("splitter_mode", _i32), ("search_mode", _i32), ("flags", _u32),
-                ("seed", _u64), ("learn_steps", _u32), ("reserved", _u32 * 5)]
+                ("seed", _u64), ("learn_steps", _u32), ("run_len", _u32), ("reserved", _u32 * 4)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("radix_bits", _u32), ("join_tile", _u32), ("run_len", _u32), ("partitions_s", _u32)]
 
 
 class Pairs(ctypes.Structure):
@@ -106,6 +110,8 @@ def lib():
             "mpsm_plan_set_flags": ([_p, _u32], ctypes.c_int),
             "mpsm_plan_kernel_times": ([_p, P(KernelTime), _u32, P(_u32)], ctypes.c_int),
             "mpsm_sort_runs_noalloc": ([_p, _u64, _u32, _p, _p], ctypes.c_int),
+            "mpsm_plan_set_tuning": ([_p, P(Tuning)], ctypes.c_int),
+            "mpsm_autotune": ([_p, P(JobDesc), _u32, _u32, P(Tuning), P(ctypes.c_float)], ctypes.c_int),
             "mpsm_rmi_loss_grad": ([_p, _p, _p, _u32, _p, _p, P(ctypes.c_float)], ctypes.c_int),
             "mpsm_rmi_train": ([_p, _p, _p, _u32, _u32, ctypes.c_float, _p, P(ctypes.c_float)], ctypes.c_int),
             "mpsm_rmi_fit": ([_p, _p, _p, _u32, _u64, _u64, _u32, ctypes.c_float], ctypes.c_int),
@@ -142,7 +148,7 @@ def _tuples(t) -> Tuple[int, int]:
 
 def make_options(runs_r=0, partitions_s=0, fine_bits=0, radix_bits=0, join_tile=0, splitter_mode=SPLIT_HIST,
                  search_mode=SEARCH_BINARY, timing=False, kernel_timing=False, flags=0,
-                 seed=20120145, learn_steps=0) -> Options:
+                 seed=20120145, learn_steps=0, run_len=0) -> Options:
     o = Options()
     lib().mpsm_options_default(ctypes.byref(o))
     o.runs_r, o.partitions_s, o.fine_bits, o.radix_bits, o.join_tile = runs_r, partitions_s, fine_bits, radix_bits, join_tile
@@ -150,6 +156,7 @@ def make_options(runs_r=0, partitions_s=0, fine_bits=0, radix_bits=0, join_tile=
     o.flags = (FLAG_TIMING if timing else 0) | (FLAG_KERNEL_TIMING if kernel_timing else 0) | flags
     o.seed = seed
     o.learn_steps = learn_steps
+    o.run_len = run_len
     return o
 
 
@@ -298,6 +305,27 @@ class Plan(_RmiMixin):
         sums = (_u64 * n)()
         _check(lib().mpsm_join_batch(self.handle, arr, n, counts, sums), "mpsm_join_batch")
         return list(counts), list(sums)
+
+    @staticmethod
+    def _descs(jobs):
+        arr = (JobDesc * len(jobs))()
+        for i, (R, S) in enumerate(jobs):
+            rp, nr = _tuples(R)
+            sp, ns = _tuples(S)
+            arr[i] = JobDesc(rp, nr, sp, ns)
+        return arr
+
+    def set_tuning(self, radix_bits=0, join_tile=0, run_len=0, partitions_s=0):
+        t = Tuning(radix_bits, join_tile, run_len, partitions_s)
+        _check(lib().mpsm_plan_set_tuning(self.handle, ctypes.byref(t)), "mpsm_plan_set_tuning")
+
+    def autotune(self, jobs, reps: int = 2):
+        """Times the candidate tunings on this batch; keeps and returns the fastest (dict, ms)."""
+        best = Tuning()
+        ms = ctypes.c_float()
+        _check(lib().mpsm_autotune(self.handle, self._descs(jobs), len(jobs), reps, ctypes.byref(best),
+                                   ctypes.byref(ms)), "mpsm_autotune")
+        return {k: getattr(best, k) for k, _ in best._fields_}, ms.value
 
     # ---- introspection
     def stats(self) -> dict:
