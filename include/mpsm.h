@@ -59,8 +59,12 @@ enum { MPSM_SPLIT_HIST = 0, MPSM_SPLIT_LEARNED = 1 };
 enum { MPSM_SEARCH_BINARY = 0, MPSM_SEARCH_LEARNED = 1 };
 enum {
   MPSM_FLAG_TIMING = 1u,          /* record per-phase CUDA events (read by mpsm_plan_stats)        */
-  MPSM_FLAG_KERNEL_TIMING = 2u    /* record CUDA events around every kernel launch (read by
+  MPSM_FLAG_KERNEL_TIMING = 2u,   /* record CUDA events around every kernel launch (read by
                                      mpsm_plan_kernel_times); adds a few microseconds per launch  */
+  MPSM_FLAG_UNFUSED = 4u          /* mpsm_join / mpsm_join_batch: run phase 3 and phase 4 as separate
+                                     kernels (sorted S written back, then searched and joined)
+                                     instead of joining each S segment while its sort still holds
+                                     it in shared memory; same results                            */
 };
 
 typedef struct {

@@ -46,13 +46,14 @@ enum Kid {
   K_SAMPLE, K_PLAN, K_INIT, K_HIST_RADIX, K_SCAN_RADIX, K_SCATTER_RADIX, K_SEG_SORT, K_RUN_BOUNDS, K_HIST_FINE,
   K_RUN_CDF, K_SPLITTERS, K_FOLD, K_SCAN_SPLIT, K_SCATTER_SPLIT, K_TILES, K_SEARCH, K_JOIN, K_PAIR_OFFSETS, K_CHECK,
   K_SAMPLE_S, K_RMI_DATA, K_RMI_GRAD, K_RMI_ADAM, K_RMI_TAB, K_RMI_LEAF, K_LEARN_BOUNDS, K_HIST_LEARN, K_SCAN_LEARN,
-  K_SCATTER_LEARN, K_NUM
+  K_SCATTER_LEARN, K_FENCES, K_SEG_SEARCH, K_SORT_JOIN, K_NUM
 };
 const char* const KNAME[K_NUM] = {"sample_bounds", "level_plan", "init_buckets", "hist_radix", "scan_radix",
                                   "scatter_radix", "seg_sort", "run_bounds", "hist_fine", "run_cdf", "splitters",
                                   "fold", "scan_split", "scatter_split", "tiles", "search", "join", "pair_offsets",
                                   "check_empty", "sample_s", "rmi_data", "rmi_grad", "rmi_adam", "rmi_tabulate",
-                                  "rmi_leaves", "learn_bounds", "hist_learn", "scan_learn", "scatter_learn"};
+                                  "rmi_leaves", "learn_bounds", "hist_learn", "scan_learn", "scatter_learn",
+                                  "fences", "seg_search", "sort_join"};
 // learned model: sample and training sizes
 constexpr u32 RMI_SAMPLE_MAX = 1u << 21;  // largest sample per model
 constexpr u32 RMI_STEPS = 200;            // full-batch Adam steps
@@ -123,6 +124,12 @@ struct mpsm_plan {
   cudaGraphExec_t gexec = nullptr;
   std::vector<u64> gsig;
   u32 graph_launches = 0;           // kernels in the captured graph
+  // fused phases 3 + 4
+  bool fused = false;               // the current call joins S segments inside their final sort
+  u32 maxT = 1;                     // largest T_R of the current call's jobs
+  u64* d_fence = nullptr;           // every 64th key of the sorted runs
+  u32* d_swin = nullptr;            // per (final S segment, run) windows
+  u64 swin_cap = 0;
   // learned CDF model (allocated on first use)
   bool learn = false;               // the current call uses a learned mode
   RmiModel* d_models = nullptr;     // 2 per job
@@ -243,7 +250,7 @@ void record(mpsm_plan* p, int i) {
 bool kernel_timing(const mpsm_plan* p) { return (p->opt.flags & MPSM_FLAG_KERNEL_TIMING) && p->kt_ev && !p->graph_mode; }
 
 void kt_begin(mpsm_plan* p, u32 id) {
-  p->launches += (id == K_SEG_SORT) ? 2u : 1u;  // the final sort is two kernels (size classes)
+  p->launches += (id == K_SEG_SORT || id == K_SORT_JOIN) ? 2u : 1u;  // the final sort is two kernels (size classes)
   if (kernel_timing(p) && p->kt_n < KT_POOL) {
     p->kt_id[p->kt_n] = id;
     cudaEventRecord(p->kt_ev[2 * p->kt_n], p->st);
@@ -364,6 +371,16 @@ int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
   }
   if (totR > p->max_nR || totS > p->max_nS) return MPSM_ERR_INVALID_ARG;
   if (totRuns > p->runs_cap) return MPSM_ERR_INVALID_ARG;
+  p->maxT = 1;
+  for (u32 i = 0; i < njobs; ++i) p->maxT = std::max(p->maxT, T[i]);
+  if (p->fused && (u64)p->fin_cap * p->maxT * 2 > p->swin_cap) {
+    dfree(p->d_swin);
+    p->swin_cap = (u64)p->fin_cap * p->maxT * 2;
+    if (dalloc(&p->d_swin, p->swin_cap)) {
+      p->swin_cap = 0;
+      return MPSM_ERR_OOM;
+    }
+  }
   // grow the window / tile arrays if this call needs more
   if (win_need * 2 > p->win_cap) {
     dfree(p->d_win);
@@ -447,7 +464,7 @@ int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
 }
 
 // radix passes over the big-segment list until every segment is final
-int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels) {
+int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels, bool keep_const = false) {
   u32 cur = 0, src = first_src;
   u32 done = 0;
   for (u32 lvl = 0; lvl < MAX_LEVELS; ++lvl) {
@@ -467,7 +484,7 @@ int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels) {
                 p->d_hist_a, p->d_bmin, p->d_bmax, nullptr, lctx(p, false), p->st, p->nsm));
     LAUNCH(K_SCAN_RADIX, launch_scan(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, p->d_hist_a, p->d_bmin, p->d_bmax,
                 nullptr, p->d_big[cur ^ 1], &p->d_cnt[C_BIG0 + (cur ^ 1)], p->big_cap, p->d_fin, &p->d_cnt[C_FIN],
-                p->fin_cap, dst, p->d_jobs, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm));
+                p->fin_cap, dst, p->d_jobs, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm, keep_const));
     LAUNCH(K_SCATTER_RADIX, launch_scatter(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs,
                    src, dst, p->d_hist_a, nullptr, &p->d_cnt[C_ERR], lctx(p, false), p->st, p->nsm));
     CK(cudaGetLastError());
@@ -563,7 +580,7 @@ int phase_splitters_learned(mpsm_plan* p) {
   LAUNCH(K_SCAN_LEARN, launch_scan(MODE_LEARN, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_hist_a, p->d_bmin,
                                    p->d_bmax, nullptr, p->d_big[0], &p->d_cnt[C_BIG0], p->big_cap, p->d_fin,
                                    &p->d_cnt[C_FIN], p->fin_cap, W_XS, p->d_jobs, p->d_part_off, &p->d_cnt[C_ERR],
-                                   p->st, p->nsm));
+                                   p->st, p->nsm, p->fused));
   CK(cudaGetLastError());
   record(p, EV_SPLIT);
   p->stage = ST_SPLIT;
@@ -593,7 +610,7 @@ int phase_splitters(mpsm_plan* p) {
   CK(cudaMemsetAsync(&p->d_cnt[C_FIN], 0, sizeof(u32), p->st));
   LAUNCH(K_SCAN_SPLIT, launch_scan(MODE_SPLIT, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_hist_a, p->d_fine_min, p->d_fine_max,
               p->d_fstart, p->d_big[0], &p->d_cnt[C_BIG0], p->big_cap, p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, W_XS,
-              p->d_jobs, p->d_part_off, &p->d_cnt[C_ERR], p->st, p->nsm));
+              p->d_jobs, p->d_part_off, &p->d_cnt[C_ERR], p->st, p->nsm, p->fused));
   CK(cudaGetLastError());
   record(p, EV_SPLIT);
   p->stage = ST_SPLIT;
@@ -619,6 +636,42 @@ int phase_sort_parts(mpsm_plan* p) {
   if (rc) return rc;
   record(p, EV_SORTS);
   p->stage = ST_SORTED;
+  return MPSM_OK;
+}
+
+int read_err(mpsm_plan* p);
+
+// Phases 3 and 4 fused: radix passes over the S partitions as in phase 3, then
+// per final segment the windows of every R run (fence search), then one kernel
+// that sorts each segment in shared memory and joins it there.  Sorted S is
+// never written back or read again.
+int phase_sort_join(mpsm_plan* p) {
+  int rc = run_levels(p, W_XS, W_XS, &p->levels_s, true);
+  if (rc) return rc;
+  record(p, EV_SORTS);
+  u64 totR = 0;
+  for (u32 i = 0; i < p->njobs; ++i) totR += p->h_jobs[i].nR;
+  LAUNCH(K_FENCES, launch_fences(p->xr, totR, p->d_fence, p->st, p->nsm));
+  LAUNCH(K_SEG_SEARCH, launch_seg_search(p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, p->d_jobs, p->d_runs, p->xr, p->d_fence,
+                                         p->d_swin, p->maxT, p->st, p->nsm));
+  record(p, EV_SEARCH);
+  FuseCtx fc{p->d_swin, p->maxT, p->d_runs, p->xr, p->d_jobs};
+  CK(cudaMemsetAsync(&p->d_cnt[C_WORK], 0, 2 * sizeof(u32), p->st));
+  LAUNCH(K_SORT_JOIN, launch_seg_sort_join(p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, &p->d_cnt[C_WORK], bufs(p), p->d_jobs,
+                                           &p->d_cnt[C_ERR], fc, p->st, p->nsm));
+  CK(cudaGetLastError());
+  record(p, EV_JOIN);
+  p->stage = ST_DONE;
+  return MPSM_OK;
+}
+
+// results of a fused call (job 0 to the caller)
+int fused_results(mpsm_plan* p, uint64_t* out_count, uint64_t* out_checksum) {
+  CK(cudaMemcpyAsync(p->h_jobs, p->d_jobs, p->njobs * sizeof(Job), cudaMemcpyDeviceToHost, p->st));
+  const int rc = read_err(p);
+  if (rc) return rc;
+  if (out_count) *out_count = p->h_jobs[0].count;
+  if (out_checksum) *out_checksum = p->h_jobs[0].checksum;
   return MPSM_OK;
 }
 
@@ -735,6 +788,8 @@ MPSM_API void mpsm_plan_destroy(mpsm_plan_t* p) {
   dfree(p->d_chunk_off);
   hfree(p->h_scalar);
   dfree(p->d_lstat);
+  dfree(p->d_fence);
+  dfree(p->d_swin);
   dfree(p->d_models);
   dfree(p->d_tasks);
   hfree(p->h_tasks);
@@ -858,6 +913,7 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   TRY(dalloc(&p->d_part_off, (u64)max_jobs * (P_MAX + 1)));
   TRY(halloc(&p->h_scalar, 16));
   TRY(dalloc(&p->d_lstat, 8));
+  TRY(dalloc(&p->d_fence, max_nR / 64 + 2));
   if (o.splitter_mode == MPSM_SPLIT_LEARNED || o.search_mode == MPSM_SEARCH_LEARNED) TRY(alloc_learn(p));
   {
     const u32 fl = o.flags;
@@ -873,6 +929,7 @@ MPSM_API int mpsm_sort_runs(mpsm_plan_t* p, const mpsm_tuple_t* R, uint64_t nR) 
   int rc = check_inputs(p, R, nR, nullptr, 0);
   if (rc) return rc;
   if (split_learned(p) || search_learned(p)) return MPSM_ERR_INVALID_ARG;
+  p->fused = false;
   Jobh j{reinterpret_cast<const Tuple*>(R), nullptr, nR, 0};
   rc = setup_jobs(p, &j, 1);
   if (rc) return rc;
@@ -946,12 +1003,17 @@ MPSM_API int mpsm_merge_join(mpsm_plan_t* p, uint64_t* out_count, uint64_t* out_
 static int join_device(mpsm_plan_t* p, const mpsm_tuple_t* R, uint64_t nR, const mpsm_tuple_t* S, uint64_t nS,
                        uint64_t* out_count, uint64_t* out_checksum, mpsm_pairs_t* pairs) {
   Jobh j{reinterpret_cast<const Tuple*>(R), reinterpret_cast<const Tuple*>(S), nR, nS};
+  p->fused = !pairs && !(p->opt.flags & MPSM_FLAG_UNFUSED);
   int rc = setup_jobs(p, &j, 1);
   if (rc) return rc;
   if ((rc = phase_runs(p))) return rc;
   if ((rc = phase_learn(p))) return rc;
   if ((rc = phase_splitters(p))) return rc;
   if ((rc = phase_scatter(p))) return rc;
+  if (p->fused) {
+    if ((rc = phase_sort_join(p))) return rc;
+    return fused_results(p, out_count, out_checksum);
+  }
   if ((rc = phase_sort_parts(p))) return rc;
   if ((rc = phase_search(p))) return rc;
   return phase_join(p, out_count, out_checksum, pairs);
@@ -991,11 +1053,13 @@ MPSM_API int mpsm_join_batch(mpsm_plan_t* p, const mpsm_job_t* jobs, uint32_t nj
     tS += jobs[i].nS;
   }
   if (tR > p->max_nR || tS > p->max_nS) return MPSM_ERR_INVALID_ARG;
+  p->fused = !(p->opt.flags & MPSM_FLAG_UNFUSED);
   int rc = setup_jobs(p, jh.data(), njobs);
   if (rc) return rc;
   // same job sizes and pointers as the captured graph -> replay it
   std::vector<u64> sig;
-  sig.reserve(4 * njobs);
+  sig.reserve(4 * njobs + 1);
+  sig.push_back(p->opt.flags);
   for (u32 i = 0; i < njobs; ++i) {
     sig.push_back((u64)(uintptr_t)jh[i].R);
     sig.push_back(jh[i].nR);
@@ -1017,8 +1081,9 @@ MPSM_API int mpsm_join_batch(mpsm_plan_t* p, const mpsm_job_t* jobs, uint32_t nj
     if (!prc) prc = phase_learn(p);
     if (!prc) prc = phase_splitters(p);
     if (!prc) prc = phase_scatter(p);
-    if (!prc) prc = phase_sort_parts(p);
-    if (!prc) {
+    if (!prc && p->fused) prc = phase_sort_join(p);
+    if (!prc && !p->fused) prc = phase_sort_parts(p);
+    if (!prc && !p->fused) {
       LAUNCH(K_TILES, launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, p->st));
       LAUNCH(K_SEARCH, launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win,
                                      lctx(p, search_learned(p)), p->st, p->nsm));
@@ -1078,7 +1143,8 @@ MPSM_API int mpsm_plan_stats(mpsm_plan_t* p, mpsm_stats_t* s) {
     s->part_max = mx;
     s->imbalance = po[J.parts] ? (double)mx * J.parts / (double)po[J.parts] : 0.0;
   }
-  if (J.ntiles && J.runs && p->stage >= ST_SEARCH) {
+  if (p->fused) s->tiles = 0;
+  if (!p->fused && J.ntiles && J.runs && p->stage >= ST_SEARCH) {
     const u64 nw = J.ntiles * J.runs;
     std::vector<u32> w(2 * nw);
     CK(cudaMemcpy(w.data(), p->d_win + 2 * J.win_base, 2 * nw * sizeof(u32), cudaMemcpyDeviceToHost));
@@ -1125,7 +1191,7 @@ MPSM_API int mpsm_plan_stats(mpsm_plan_t* p, mpsm_stats_t* s) {
 
 MPSM_API int mpsm_plan_set_flags(mpsm_plan_t* p, uint32_t flags) {
   if (!p) return MPSM_ERR_INVALID_ARG;
-  if (flags & ~(u32)(MPSM_FLAG_TIMING | MPSM_FLAG_KERNEL_TIMING)) return MPSM_ERR_INVALID_ARG;
+  if (flags & ~(u32)(MPSM_FLAG_TIMING | MPSM_FLAG_KERNEL_TIMING | MPSM_FLAG_UNFUSED)) return MPSM_ERR_INVALID_ARG;
   if ((flags & MPSM_FLAG_TIMING) && !p->ev[0])
     for (auto& e : p->ev)
       if (cudaEventCreate(&e) != cudaSuccess) return MPSM_ERR_CUDA;

@@ -524,9 +524,169 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
 // 4096 (two blocks per SM, so one block's copy overlaps the other's sort)
 // takes segments of at most 4096 tuples and all constant-key segments; CAP =
 // 8192 (one block per SM) takes the rest.
-template <u32 CAP, u32 MINB>
+// sum of one u64 per thread over the block (result valid in thread 0)
+__device__ __forceinline__ u64 block_sum_u64(u64 v, u64* s_red) {
+  v = warp_sum(v);
+  if (lane_id() == 0) s_red[warp_id()] = v;
+  __syncthreads();
+  u64 t = 0;
+  if (threadIdx.x == 0)
+    for (u32 w = 0; w < NW_SORT; ++w) t += s_red[w];
+  __syncthreads();
+  return t;
+}
+
+// Join of a segment whose keys all equal `key` (n tuples at s, global or shared):
+// every R tuple in its windows matches every S tuple of the segment.
+__device__ __forceinline__ void seg_join_const(const Tuple* s, u32 n, const Seg& sg, u32 item, const FuseCtx& fc,
+                                               u64* s_red) {
+  const u32 tid = threadIdx.x;
+  const Job& J = fc.jobs[sg.job];
+  u64 ssum = 0;
+  for (u32 i = tid; i < n; i += NT_SORT) ssum += s[i].pay;
+  u64 rcnt = 0, rsum = 0;
+  for (u32 j = tid; j < J.runs; j += NT_SORT) {
+    const u32* w = fc.swin + 2ull * ((u64)item * fc.maxT + j);
+    const Tuple* r = fc.xr + fc.runs[J.run_base + j].off;
+    for (u32 q = w[0]; q < w[1]; ++q) {
+      rsum += r[q].pay;
+      ++rcnt;
+    }
+  }
+  ssum = block_sum_u64(ssum, s_red);
+  rcnt = block_sum_u64(rcnt, s_red);
+  rsum = block_sum_u64(rsum, s_red);
+  if (tid == 0 && rcnt) {
+    atomicAdd(&fc.jobs[sg.job].count, rcnt * n);
+    atomicAdd(&fc.jobs[sg.job].checksum, rcnt * ssum + (u64)n * rsum);
+  }
+}
+
+// Join of a sorted segment (tup in the order ia, n tuples, keys in [mn, mx])
+// against its R windows.  dir (the free ping-pong index array, CAP entries)
+// becomes an order-preserving directory of at most CAP/2 key buckets; rtab (the
+// free digit-count array) stages up to RCH runs' windows at a time.
+constexpr u32 RCH = 128;
+
+template <u32 CAP>
+__device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* dir, u32* rtab, u32 n, u64 mn, u64 mx,
+                                         const Seg& sg, u32 item, const FuseCtx& fc, u64* s_red) {
+  constexpr u32 DB = (CAP >= 8192u) ? 12u : 11u;  // 2^DB = CAP / 2 buckets
+  const u32 tid = threadIdx.x;
+  const Job& J = fc.jobs[sg.job];
+  const u32 T = J.runs, run_base = J.run_base;
+  const u32 rbits = bitlen64(mx - mn);
+  const u32 dsh = rbits > DB ? rbits - DB : 0u;
+  const u32 nbk = (u32)((mx - mn) >> dsh) + 1u;
+  for (u32 i = tid; i < n; i += NT_SORT) {
+    const u32 b = (u32)((tup[ia[i]].key - mn) >> dsh);
+    const u32 x0 = i ? (u32)((tup[ia[i - 1]].key - mn) >> dsh) + 1u : 0u;
+    for (u32 x = x0; x <= b; ++x) dir[x] = (u16)i;
+    if (i == n - 1)
+      for (u32 x = b + 1u; x <= nbk; ++x) dir[x] = (u16)n;
+  }
+  u32* wl = rtab;                                            // RCH window starts
+  u32* wpre = rtab + RCH;                                    // RCH + 1 window prefix
+  u64* roff = reinterpret_cast<u64*>(rtab + 2 * RCH + 8);    // RCH run offsets
+  u64 cnt = 0, chk = 0;
+  for (u32 j0 = 0; j0 < T; j0 += RCH) {
+    const u32 nr = T - j0 < RCH ? T - j0 : RCH;
+    __syncthreads();  // directory built; the previous chunk's readers are done
+    if (tid < nr) {
+      const u32* w = fc.swin + 2ull * ((u64)item * fc.maxT + j0 + tid);
+      wl[tid] = w[0];
+      wpre[tid] = w[1] - w[0];
+      roff[tid] = fc.runs[run_base + j0 + tid].off;
+    }
+    __syncthreads();
+    if (tid < 32) {  // exclusive scan of the window lengths, 4 per lane
+      u32 v[4], sum = 0;
+#pragma unroll
+      for (u32 k = 0; k < 4; ++k) {
+        const u32 idx = tid * 4 + k;
+        v[k] = idx < nr ? wpre[idx] : 0u;
+        sum += v[k];
+      }
+      u32 inc = sum;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const u32 y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (tid >= (u32)d) inc += y;
+      }
+      u32 run = inc - sum;
+#pragma unroll
+      for (u32 k = 0; k < 4; ++k) {
+        const u32 idx = tid * 4 + k;
+        if (idx < nr) wpre[idx] = run;
+        run += v[k];
+      }
+      const u32 tot = __shfl_sync(0xffffffffu, inc, 31);
+      if (tid == 0) wpre[nr] = tot;
+    }
+    __syncthreads();
+    const u32 W = wpre[nr];
+    constexpr u32 U = 4;  // R loads in flight per thread
+    for (u32 q0 = 0; q0 < W; q0 += NT_SORT * U) {
+      Tuple r[U];
+#pragma unroll
+      for (u32 u = 0; u < U; ++u) {
+        const u32 q = q0 + u * NT_SORT + tid;
+        r[u].key = 0;
+        r[u].pay = 0;
+        if (q < W) {
+          u32 lo = 0, hi = nr;  // run: last with wpre[lo] <= q
+          while (hi - lo > 1) {
+            const u32 mid = (lo + hi) >> 1;
+            if (wpre[mid] <= q) lo = mid;
+            else hi = mid;
+          }
+          r[u] = ld_stream(fc.xr + roff[lo] + wl[lo] + (q - wpre[lo]));
+        }
+      }
+#pragma unroll
+      for (u32 u = 0; u < U; ++u) {
+        const u32 q = q0 + u * NT_SORT + tid;
+        if (q >= W) continue;
+        const u64 key = r[u].key;
+        if (key < mn || key > mx) continue;
+        const u32 bi = (u32)((key - mn) >> dsh);
+        u32 lb = dir[bi], ub = dir[bi + 1];
+        if (dsh) {  // a bucket spans several keys: narrow [lb, ub) to `key`
+          u32 a = lb, m = ub - lb;
+          while (m > 0) {
+            const u32 h = m >> 1;
+            if (tup[ia[a + h]].key < key) {
+              a += h + 1;
+              m -= h + 1;
+            } else {
+              m = h;
+            }
+          }
+          u32 e = a;
+          while (e < ub && tup[ia[e]].key == key) ++e;
+          lb = a;
+          ub = e;
+        }
+        if (lb >= ub) continue;
+        u64 ssum = 0;
+        for (u32 i = lb; i < ub; ++i) ssum += tup[ia[i]].pay;
+        cnt += ub - lb;
+        chk += (u64)(ub - lb) * r[u].pay + ssum;
+      }
+    }
+  }
+  cnt = block_sum_u64(cnt, s_red);
+  chk = block_sum_u64(chk, s_red);
+  if (tid == 0 && cnt) {
+    atomicAdd(&fc.jobs[sg.job].count, cnt);
+    atomicAdd(&fc.jobs[sg.job].checksum, chk);
+  }
+}
+
+template <u32 CAP, u32 MINB, bool FUSE>
 __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, const u32* nseg_ptr, u32 cap, u32* work,
-                                                            Bufs bufs, const Job* jobs, u32 dst_where, u32* err) {
+                                                            Bufs bufs, const Job* jobs, u32 dst_where, u32* err,
+                                                            FuseCtx fc) {
   constexpr u32 IT = CAP / NT_SORT;
   constexpr bool SMALL = CAP <= NMAX / 2;
   extern __shared__ __align__(128) unsigned char sm_raw[];
@@ -538,6 +698,7 @@ __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, con
   __shared__ u32 s_item;
   __shared__ u32 s_warp[NT_SORT / 32 + 1];
   __shared__ u64 s_mn[NW_SORT], s_mx[NW_SORT];
+  __shared__ u64 s_red[NW_SORT];
   const u32 tid = threadIdx.x, lane = lane_id(), wid = warp_id();
   if (tid == 0) mbar_init(&mbar, 1);
   __syncthreads();
@@ -561,8 +722,11 @@ __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, con
     const u32 n = (u32)sg.len;
     const bool inplace = (src == dst);
     if (constant) {
-      if (!inplace)
+      if (FUSE) {
+        seg_join_const(src, n, sg, item, fc, s_red);
+      } else if (!inplace) {
         for (u32 i = tid; i < n; i += NT_SORT) st_tuple(dst + i, src[i]);
+      }
       continue;
     }
     if (sg.len > CAP) {
@@ -603,8 +767,11 @@ __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, con
     }
     const u32 bits = bitlen64(mx - mn);
     if (bits == 0) {
-      if (!inplace)
+      if (FUSE) {
+        seg_join_const(tup, n, sg, item, fc, s_red);
+      } else if (!inplace) {
         for (u32 i = tid; i < n; i += NT_SORT) st_tuple(dst + i, tup[i]);
+      }
       __syncthreads();
       continue;
     }
@@ -698,8 +865,72 @@ __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, con
       ib = t;
       sh += w;
     }
-    for (u32 i = tid; i < n; i += NT_SORT) st_tuple(dst + i, tup[ia[i]]);
+    if (FUSE) {
+      seg_join<CAP>(tup, ia, ib, cnt, n, mn, mx, sg, item, fc, s_red);
+    } else {
+      for (u32 i = tid; i < n; i += NT_SORT) st_tuple(dst + i, tup[ia[i]]);
+    }
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- fused-path search
+// Fences: every 64th key of the sorted runs (one array over xr), small enough to
+// stay in L2, so a run bound costs a fence search plus one 64-tuple block.
+__global__ void k_fences(const Tuple* xr, u64 n, u64* fence) {
+  const u64 nf = (n + 63) / 64;
+  for (u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x; g < nf; g += (u64)gridDim.x * blockDim.x)
+    fence[g] = xr[g * 64].key;
+}
+
+// first position of run [off, off + len) whose key is >= key (upper: > key), minus off
+__device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 off, u64 len, u64 key, bool upper) {
+  const u64 end = off + len;
+  u64 lo = off, hi = end;
+  const u64 g0 = (off + 63) / 64, g1 = len ? (end - 1) / 64 + 1 : g0;
+  if (g0 < g1) {
+    u64 a = g0, m = g1 - g0;
+    while (m > 0) {
+      const u64 h = m >> 1;
+      const u64 f = fence[a + h];
+      if (!(upper ? f > key : f >= key)) {
+        a += h + 1;
+        m -= h + 1;
+      } else {
+        m = h;
+      }
+    }
+    if (a > g0) lo = (a - 1) * 64 + 1;
+    if (a < g1) hi = a * 64;
+  }
+  u64 m = hi - lo;
+  while (m > 0) {
+    const u64 h = m >> 1;
+    const u64 k = xr[lo + h].key;
+    if (!(upper ? k > key : k >= key)) {
+      lo += h + 1;
+      m -= h + 1;
+    } else {
+      m = h;
+    }
+  }
+  return lo - off;
+}
+
+// windows of every (final S segment, R run) pair from the segment's key bounds
+__global__ void k_seg_search(const Seg* segs, const u32* nseg_ptr, u32 cap, const Job* jobs, const Run* runs,
+                             const Tuple* xr, const u64* fence, u32* swin, u32 maxT) {
+  u32 nseg = *nseg_ptr;
+  if (nseg > cap) nseg = cap;
+  const u64 total = (u64)nseg * maxT;
+  for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (u64)gridDim.x * blockDim.x) {
+    const u32 item = (u32)(idx / maxT), j = (u32)(idx - (u64)item * maxT);
+    const Seg sg = segs[item];
+    const Job& J = jobs[sg.job];
+    if (j >= J.runs) continue;
+    const Run r = runs[J.run_base + j];
+    swin[2 * idx] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmin, false);
+    swin[2 * idx + 1] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmax, true);
   }
 }
 
@@ -733,8 +964,10 @@ void init_attrs_pass() {
   set_smem(k_scan<MODE_SPLIT>, SMEM_SCAN);
   set_smem(k_scatter<MODE_RADIX>, SMEM_SCATTER);
   set_smem(k_scatter<MODE_SPLIT>, SMEM_SCATTER);
-  set_smem(k_seg_sort<NMAX / 2, 2>, smem_sort(NMAX / 2));
-  set_smem(k_seg_sort<NMAX, 1>, smem_sort(NMAX));
+  set_smem(k_seg_sort<NMAX / 2, 2, false>, smem_sort(NMAX / 2));
+  set_smem(k_seg_sort<NMAX, 1, false>, smem_sort(NMAX));
+  set_smem(k_seg_sort<NMAX / 2, 2, true>, smem_sort(NMAX / 2));
+  set_smem(k_seg_sort<NMAX, 1, true>, smem_sort(NMAX));
 }
 
 namespace {
@@ -778,8 +1011,10 @@ void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, con
 void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32* hist, const u64* bmin,
                  const u64* bmax, const u32* part_fstart, Seg* big_out, u32* big_cnt, u32 big_cap, Seg* fin_out,
                  u32* fin_cnt, u32 fin_cap, u32 dst_where, Job* jobs, u64* part_off, u32* err, cudaStream_t st,
-                 int nsm) {
-  const u32 final_where = (dst_where == W_XR || dst_where == W_XS) ? dst_where : 0xFFu;
+                 int nsm, bool keep_const) {
+  // constant-key children already at their final place are skipped unless the
+  // fused sort-and-join must still see them
+  const u32 final_where = (!keep_const && (dst_where == W_XR || dst_where == W_XS)) ? dst_where : 0xFFu;
   if (mode == MODE_SPLIT) {
     k_scan<MODE_SPLIT><<<nsm * 2, NT_PASS, SMEM_SCAN, st>>>(segs, nseg, ls, hist, bmin, bmax, part_fstart, big_out,
                                                             big_cnt, big_cap, fin_out, fin_cnt, fin_cap, dst_where,
@@ -814,8 +1049,28 @@ void launch_seg_sort(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs 
                      u32 dst_where, u32* err, cudaStream_t st, int nsm) {
   // small segments first (two blocks per SM), then the large ones; each kernel
   // walks the whole list with its own work counter and skips the other class
-  k_seg_sort<NMAX / 2, 2><<<nsm * 2, NT_SORT, smem_sort(NMAX / 2), st>>>(segs, nseg, cap, work, bufs, jobs, dst_where, err);
-  k_seg_sort<NMAX, 1><<<nsm, NT_SORT, smem_sort(NMAX), st>>>(segs, nseg, cap, work + 1, bufs, jobs, dst_where, err);
+  const FuseCtx none{};
+  k_seg_sort<NMAX / 2, 2, false><<<nsm * 2, NT_SORT, smem_sort(NMAX / 2), st>>>(segs, nseg, cap, work, bufs, jobs,
+                                                                               dst_where, err, none);
+  k_seg_sort<NMAX, 1, false><<<nsm, NT_SORT, smem_sort(NMAX), st>>>(segs, nseg, cap, work + 1, bufs, jobs, dst_where,
+                                                                    err, none);
+}
+
+void launch_seg_sort_join(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs, u32* err,
+                          const FuseCtx& fc, cudaStream_t st, int nsm) {
+  k_seg_sort<NMAX / 2, 2, true><<<nsm * 2, NT_SORT, smem_sort(NMAX / 2), st>>>(segs, nseg, cap, work, bufs, jobs,
+                                                                              W_XS, err, fc);
+  k_seg_sort<NMAX, 1, true><<<nsm, NT_SORT, smem_sort(NMAX), st>>>(segs, nseg, cap, work + 1, bufs, jobs, W_XS, err,
+                                                                   fc);
+}
+
+void launch_fences(const Tuple* xr, u64 n, u64* fence, cudaStream_t st, int nsm) {
+  if (n) k_fences<<<nsm * 4, 256, 0, st>>>(xr, n, fence);
+}
+
+void launch_seg_search(const Seg* segs, const u32* nseg, u32 cap, const Job* jobs, const Run* runs, const Tuple* xr,
+                       const u64* fence, u32* swin, u32 maxT, cudaStream_t st, int nsm) {
+  k_seg_search<<<nsm * 8, 256, 0, st>>>(segs, nseg, cap, jobs, runs, xr, fence, swin, maxT);
 }
 
 void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st) {

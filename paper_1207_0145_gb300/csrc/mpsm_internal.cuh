@@ -97,6 +97,16 @@ struct LSeg {
   u32 nchunks, pad;
 };
 
+// Phases 3 and 4 fused: the final sort of each S segment joins it, still in
+// shared memory, against the window of every R run that can hold its keys.
+struct FuseCtx {
+  const u32* swin;          // per (segment, run): window [lo, hi) in the run; segment-major, stride maxT
+  u32 maxT;                 // largest T_R of the call's jobs
+  const Run* runs;
+  const Tuple* xr;          // the sorted runs
+  Job* jobs;                // count and checksum accumulate here
+};
+
 // pointer table of the buffers a segment may live in
 struct Bufs {
   Tuple* xr;

@@ -25,13 +25,19 @@ void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, con
 void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32* hist, const u64* bmin,
                  const u64* bmax, const u32* part_fstart, Seg* big_out, u32* big_cnt, u32 big_cap, Seg* fin_out,
                  u32* fin_cnt, u32 fin_cap, u32 dst_where, Job* jobs, u64* part_off, u32* err, cudaStream_t st,
-                 int nsm);
+                 int nsm, bool keep_const = false);
 void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                     Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
                     u32* err, const LearnCtx& lc, cudaStream_t st, int nsm);
 void launch_seg_sort(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs,
                      u32 dst_where, u32* err, cudaStream_t st, int nsm);
 void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st);
+// phases 3 + 4 fused (k_pass.cu): fences of the sorted runs, per (segment, run) windows, sort-and-join
+void launch_fences(const Tuple* xr, u64 n, u64* fence, cudaStream_t st, int nsm);
+void launch_seg_search(const Seg* segs, const u32* nseg, u32 cap, const Job* jobs, const Run* runs, const Tuple* xr,
+                       const u64* fence, u32* swin, u32 maxT, cudaStream_t st, int nsm);
+void launch_seg_sort_join(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs, u32* err,
+                          const FuseCtx& fc, cudaStream_t st, int nsm);
 
 // ---- splitters (k_split.cu)
 void launch_run_bounds(Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, cudaStream_t st);

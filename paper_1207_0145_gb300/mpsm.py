@@ -20,6 +20,7 @@ SPLIT_HIST, SPLIT_LEARNED = 0, 1
 SEARCH_BINARY, SEARCH_LEARNED = 0, 1
 FLAG_TIMING = 1
 FLAG_KERNEL_TIMING = 2
+FLAG_UNFUSED = 4
 
 _u64 = ctypes.c_uint64
 _u32 = ctypes.c_uint32
