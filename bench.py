@@ -44,9 +44,10 @@ ALG_BYTES = {
     "scatter_split": ("S tuples", 32),      # read S, write partitioned S (kept tuples)
     "seg_sort": ("tuples sorted", 32),      # read a segment, write it sorted
     "join": ("S' + R tuples", 16),          # read each kept S tuple and each R tuple once
+    "sort_join": ("S' + R tuples", 16),     # fused final sort + join: read each kept S and each R tuple once
     "scatter_radix": ("tuples", 32),        # one radix pass: read + write
-    "hist_fine": ("S tuples", 16),          # read S
-    "hist_radix": ("tuples", 16),
+    "hist_fine": ("S tuples", 8),           # read the S keys
+    "hist_radix": ("tuples", 8),            # read the keys
 }
 
 
@@ -336,8 +337,8 @@ def run_ours(args):
         unit_name, per_unit = ALG_BYTES.get(name, ("tuples", 16))
         if name == "scatter_split":
             units_launch = w.n_s
-        elif name == "join":
-            units_launch = st["s_kept"] + w.n_r
+        elif name in ("join", "sort_join"):
+            units_launch = (st["s_kept"] + w.n_r) * kt_steps / n
         elif name == "seg_sort":
             units_launch = (w.n_r + st["s_kept"]) * kt_steps / n  # the two final sorts share the family
         else:

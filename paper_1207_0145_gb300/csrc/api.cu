@@ -250,7 +250,7 @@ void record(mpsm_plan* p, int i) {
 bool kernel_timing(const mpsm_plan* p) { return (p->opt.flags & MPSM_FLAG_KERNEL_TIMING) && p->kt_ev && !p->graph_mode; }
 
 void kt_begin(mpsm_plan* p, u32 id) {
-  p->launches += (id == K_SEG_SORT || id == K_SORT_JOIN) ? 2u : 1u;  // the final sort is two kernels (size classes)
+  p->launches += (id == K_SEG_SORT) ? 2u : 1u;  // the unfused final sort is two kernels (size classes)
   if (kernel_timing(p) && p->kt_n < KT_POOL) {
     p->kt_id[p->kt_n] = id;
     cudaEventRecord(p->kt_ev[2 * p->kt_n], p->st);

@@ -525,37 +525,42 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
 // takes segments of at most 4096 tuples and all constant-key segments; CAP =
 // 8192 (one block per SM) takes the rest.
 // sum of one u64 per thread over the block (result valid in thread 0)
+template <u32 NT>
 __device__ __forceinline__ u64 block_sum_u64(u64 v, u64* s_red) {
   v = warp_sum(v);
   if (lane_id() == 0) s_red[warp_id()] = v;
   __syncthreads();
   u64 t = 0;
   if (threadIdx.x == 0)
-    for (u32 w = 0; w < NW_SORT; ++w) t += s_red[w];
+    for (u32 w = 0; w < NT / 32; ++w) t += s_red[w];
   __syncthreads();
   return t;
 }
 
-// Join of a segment whose keys all equal `key` (n tuples at s, global or shared):
-// every R tuple in its windows matches every S tuple of the segment.
-__device__ __forceinline__ void seg_join_const(const Tuple* s, u32 n, const Seg& sg, u32 item, const FuseCtx& fc,
-                                               u64* s_red) {
+// Join of a segment or piece whose keys all equal `key` (n tuples at s, global or
+// shared): every R tuple of its windows with that key matches every S tuple.
+template <u32 NT>
+__device__ __forceinline__ void seg_join_const(const Tuple* s, u32 n, u64 key, const Seg& sg, u32 item,
+                                               const FuseCtx& fc, u64* s_red) {
   const u32 tid = threadIdx.x;
   const Job& J = fc.jobs[sg.job];
   u64 ssum = 0;
-  for (u32 i = tid; i < n; i += NT_SORT) ssum += s[i].pay;
+  for (u32 i = tid; i < n; i += NT) ssum += s[i].pay;
   u64 rcnt = 0, rsum = 0;
-  for (u32 j = tid; j < J.runs; j += NT_SORT) {
+  for (u32 j = tid; j < J.runs; j += NT) {
     const u32* w = fc.swin + 2ull * ((u64)item * fc.maxT + j);
     const Tuple* r = fc.xr + fc.runs[J.run_base + j].off;
-    for (u32 q = w[0]; q < w[1]; ++q) {
-      rsum += r[q].pay;
-      ++rcnt;
+    for (u32 q = w[0]; q < w[1]; ++q) {  // the windows cover the segment's bounds, which may exceed `key`
+      const Tuple t = r[q];
+      if (t.key == key) {
+        rsum += t.pay;
+        ++rcnt;
+      }
     }
   }
-  ssum = block_sum_u64(ssum, s_red);
-  rcnt = block_sum_u64(rcnt, s_red);
-  rsum = block_sum_u64(rsum, s_red);
+  ssum = block_sum_u64<NT>(ssum, s_red);
+  rcnt = block_sum_u64<NT>(rcnt, s_red);
+  rsum = block_sum_u64<NT>(rsum, s_red);
   if (tid == 0 && rcnt) {
     atomicAdd(&fc.jobs[sg.job].count, rcnt * n);
     atomicAdd(&fc.jobs[sg.job].checksum, rcnt * ssum + (u64)n * rsum);
@@ -568,7 +573,7 @@ __device__ __forceinline__ void seg_join_const(const Tuple* s, u32 n, const Seg&
 // free digit-count array) stages up to RCH runs' windows at a time.
 constexpr u32 RCH = 128;
 
-template <u32 CAP>
+template <u32 CAP, u32 NT>
 __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* dir, u32* rtab, u32 n, u64 mn, u64 mx,
                                          const Seg& sg, u32 item, const FuseCtx& fc, u64* s_red) {
   constexpr u32 DB = (CAP >= 8192u) ? 12u : 11u;  // 2^DB = CAP / 2 buckets
@@ -578,7 +583,7 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
   const u32 rbits = bitlen64(mx - mn);
   const u32 dsh = rbits > DB ? rbits - DB : 0u;
   const u32 nbk = (u32)((mx - mn) >> dsh) + 1u;
-  for (u32 i = tid; i < n; i += NT_SORT) {
+  for (u32 i = tid; i < n; i += NT) {
     const u32 b = (u32)((tup[ia[i]].key - mn) >> dsh);
     const u32 x0 = i ? (u32)((tup[ia[i - 1]].key - mn) >> dsh) + 1u : 0u;
     for (u32 x = x0; x <= b; ++x) dir[x] = (u16)i;
@@ -626,11 +631,11 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
     __syncthreads();
     const u32 W = wpre[nr];
     constexpr u32 U = 4;  // R loads in flight per thread
-    for (u32 q0 = 0; q0 < W; q0 += NT_SORT * U) {
+    for (u32 q0 = 0; q0 < W; q0 += NT * U) {
       Tuple r[U];
 #pragma unroll
       for (u32 u = 0; u < U; ++u) {
-        const u32 q = q0 + u * NT_SORT + tid;
+        const u32 q = q0 + u * NT + tid;
         r[u].key = 0;
         r[u].pay = 0;
         if (q < W) {
@@ -645,7 +650,7 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
       }
 #pragma unroll
       for (u32 u = 0; u < U; ++u) {
-        const u32 q = q0 + u * NT_SORT + tid;
+        const u32 q = q0 + u * NT + tid;
         if (q >= W) continue;
         const u64 key = r[u].key;
         if (key < mn || key > mx) continue;
@@ -675,30 +680,31 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
       }
     }
   }
-  cnt = block_sum_u64(cnt, s_red);
-  chk = block_sum_u64(chk, s_red);
+  cnt = block_sum_u64<NT>(cnt, s_red);
+  chk = block_sum_u64<NT>(chk, s_red);
   if (tid == 0 && cnt) {
     atomicAdd(&fc.jobs[sg.job].count, cnt);
     atomicAdd(&fc.jobs[sg.job].checksum, chk);
   }
 }
 
-template <u32 CAP, u32 MINB, bool FUSE>
-__global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, const u32* nseg_ptr, u32 cap, u32* work,
+template <u32 CAP, u32 MINB, bool FUSE, u32 NT>
+__global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u32* nseg_ptr, u32 cap, u32* work,
                                                             Bufs bufs, const Job* jobs, u32 dst_where, u32* err,
                                                             FuseCtx fc) {
-  constexpr u32 IT = CAP / NT_SORT;
+  constexpr u32 IT = CAP / NT;
+  constexpr u32 NW = NT / 32;
   constexpr bool SMALL = CAP <= NMAX / 2;
   extern __shared__ __align__(128) unsigned char sm_raw[];
   Tuple* tup = reinterpret_cast<Tuple*>(sm_raw);        // CAP
   u16* ia = reinterpret_cast<u16*>(tup + CAP);          // CAP
   u16* ib = ia + CAP;                                   // CAP
-  u32* cnt = reinterpret_cast<u32*>(ib + CAP);          // NW_SORT * 256 (>= 2048)
+  u32* cnt = reinterpret_cast<u32*>(ib + CAP);          // NW * 256 (>= 2048)
   __shared__ __align__(8) u64 mbar;
   __shared__ u32 s_item;
-  __shared__ u32 s_warp[NT_SORT / 32 + 1];
-  __shared__ u64 s_mn[NW_SORT], s_mx[NW_SORT];
-  __shared__ u64 s_red[NW_SORT];
+  __shared__ u32 s_warp[NT / 32 + 1];
+  __shared__ u64 s_mn[NW], s_mx[NW];
+  __shared__ u64 s_red[NW];
   const u32 tid = threadIdx.x, lane = lane_id(), wid = warp_id();
   if (tid == 0) mbar_init(&mbar, 1);
   __syncthreads();
@@ -716,33 +722,40 @@ __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, con
     if (item >= n_items) break;
     const Seg sg = segs[item];
     const bool constant = (sg.flags & SEG_EXACT) && sg.kmin == sg.kmax;
-    if (SMALL ? (!constant && sg.len > CAP) : (constant || sg.len <= NMAX / 2)) continue;  // the other class
+    // the other class (the fused small class takes every segment, big ones in pieces)
+    if (SMALL ? (!FUSE && !constant && sg.len > CAP) : (constant || sg.len <= NMAX / 2)) continue;
     const Tuple* src = seg_src(bufs, jobs, sg.flags & 7u, sg.job, sg.off);
     Tuple* dst = dstb + sg.off;
     const u32 n = (u32)sg.len;
     const bool inplace = (src == dst);
     if (constant) {
       if (FUSE) {
-        seg_join_const(src, n, sg, item, fc, s_red);
+        seg_join_const<NT>(src, n, sg.kmin, sg, item, fc, s_red);
       } else if (!inplace) {
-        for (u32 i = tid; i < n; i += NT_SORT) st_tuple(dst + i, src[i]);
+        for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, src[i]);
       }
       continue;
     }
-    if (sg.len > CAP) {
+    if (!FUSE && sg.len > CAP) {
       if (tid == 0) atomicOr(err, (u32)DERR_SEG_TOO_BIG);
       continue;
     }
-    if (tid == 0) tma_load_1d(tup, src, n * (u32)sizeof(Tuple), &mbar);
+    // The fused join is exact for any split of S into pieces joined against windows
+    // that cover their keys, so a segment above CAP is sorted and joined in pieces.
+    bool failed = false;
+    for (u32 p0 = 0; p0 < n; p0 += CAP) {
+    const u32 n = (sg.len - p0 < CAP) ? (u32)(sg.len - p0) : CAP;  // this piece
+    if (tid == 0) tma_load_1d(tup, src + p0, n * (u32)sizeof(Tuple), &mbar);
     const bool ok = mbar_wait(&mbar, phase, SPIN_LIMIT);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) {
       if (tid == 0) atomicOr(err, (u32)DERR_TMA_TIMEOUT);
+      failed = true;
       break;
     }
     // exact key range of the segment
     u64 mn = ~0ull, mx = 0;
-    for (u32 i = tid; i < n; i += NT_SORT) {
+    for (u32 i = tid; i < n; i += NT) {
       const u64 k = tup[i].key;
       mn = k < mn ? k : mn;
       mx = k > mx ? k : mx;
@@ -761,16 +774,16 @@ __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, con
     mn = s_mn[0];
     mx = s_mx[0];
 #pragma unroll
-    for (u32 w = 1; w < NW_SORT; ++w) {
+    for (u32 w = 1; w < NW; ++w) {
       mn = s_mn[w] < mn ? s_mn[w] : mn;
       mx = s_mx[w] > mx ? s_mx[w] : mx;
     }
     const u32 bits = bitlen64(mx - mn);
     if (bits == 0) {
       if (FUSE) {
-        seg_join_const(tup, n, sg, item, fc, s_red);
+        seg_join_const<NT>(tup, n, mn, sg, item, fc, s_red);
       } else if (!inplace) {
-        for (u32 i = tid; i < n; i += NT_SORT) st_tuple(dst + i, tup[i]);
+        for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, tup[i]);
       }
       __syncthreads();
       continue;
@@ -778,12 +791,12 @@ __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, con
     // pass 1: counting sort on the low digit (order within a digit is free here)
     const u32 w1 = bits < 11u ? bits : 11u;
     const u32 F1 = 1u << w1;
-    for (u32 b = tid; b < F1; b += NT_SORT) cnt[b] = 0;
+    for (u32 b = tid; b < F1; b += NT) cnt[b] = 0;
     __syncthreads();
     u32 dr[IT];
 #pragma unroll
     for (u32 i = 0; i < IT; ++i) {
-      const u32 e = tid + i * NT_SORT;
+      const u32 e = tid + i * NT;
       if (e < n) {
         const u32 d = (u32)((tup[e].key - mn) & (u64)(F1 - 1u));
         const u32 r = atomicAdd(&cnt[d], 1u);
@@ -791,16 +804,16 @@ __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, con
       }
     }
     __syncthreads();
-    smem_exclusive_scan<u32, NT_SORT, 2048 / NT_SORT>(cnt, F1, s_warp);
+    smem_exclusive_scan<u32, NT, 2048 / NT>(cnt, F1, s_warp);
 #pragma unroll
     for (u32 i = 0; i < IT; ++i) {
-      const u32 e = tid + i * NT_SORT;
+      const u32 e = tid + i * NT;
       if (e < n) ia[cnt[dr[i] >> 16] + (dr[i] & 0xFFFFu)] = (u16)e;
     }
     __syncthreads();
     // further digits: stable ranking, 8 bits per pass
     u32 sh = w1;
-    const u32 per = (((n + NW_SORT - 1) / NW_SORT) + 31u) & ~31u;
+    const u32 per = (((n + NW - 1) / NW) + 31u) & ~31u;
     const u32 wb = wid * per;
     const u32 we = (wb + per < n) ? wb + per : n;
     const u32 nb = per / 32u;
@@ -808,7 +821,7 @@ __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, con
     while (sh < bits) {
       const u32 w = (bits - sh) < 8u ? (bits - sh) : 8u;
       const u32 FB = 1u << w;
-      for (u32 i = tid; i < NW_SORT * 256u; i += NT_SORT) cnt[i] = 0;
+      for (u32 i = tid; i < NW * 256u; i += NT) cnt[i] = 0;
       __syncthreads();
       u32 rec[IT];
       u16 ee[IT];
@@ -839,12 +852,12 @@ __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, con
       {
         u32 tot_d = 0;
         if (tid < FB)
-          for (u32 ww = 0; ww < NW_SORT; ++ww) tot_d += cnt[ww * 256u + tid];
+          for (u32 ww = 0; ww < NW; ++ww) tot_d += cnt[ww * 256u + tid];
         u32 total;
-        const u32 dbase = block_exclusive_scan<u32, NT_SORT>(tid < FB ? tot_d : 0u, &total, s_warp);
+        const u32 dbase = block_exclusive_scan<u32, NT>(tid < FB ? tot_d : 0u, &total, s_warp);
         if (tid < FB) {
           u32 run = dbase;
-          for (u32 ww = 0; ww < NW_SORT; ++ww) {
+          for (u32 ww = 0; ww < NW; ++ww) {
             const u32 c = cnt[ww * 256u + tid];
             cnt[ww * 256u + tid] = run;
             run += c;
@@ -866,11 +879,14 @@ __global__ void __launch_bounds__(NT_SORT, MINB) k_seg_sort(const Seg* segs, con
       sh += w;
     }
     if (FUSE) {
-      seg_join<CAP>(tup, ia, ib, cnt, n, mn, mx, sg, item, fc, s_red);
+      seg_join<CAP, NT>(tup, ia, ib, cnt, n, mn, mx, sg, item, fc, s_red);
     } else {
-      for (u32 i = tid; i < n; i += NT_SORT) st_tuple(dst + i, tup[ia[i]]);
+      for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, tup[ia[i]]);
     }
     __syncthreads();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // before the next piece's bulk copy
+    }
+    if (failed) break;
   }
 }
 
@@ -940,7 +956,8 @@ __global__ void k_check_empty(const u32* cnt, u32* err, u32 flag) {
 
 constexpr size_t SMEM_SCATTER = SC_TILE * sizeof(Tuple) + 3 * F_MAX * sizeof(u32) + 2 * SC_TILE * sizeof(u16) +
                                 FINE_MAX * sizeof(u16);
-constexpr size_t smem_sort(u32 cap) { return cap * sizeof(Tuple) + 2 * cap * sizeof(u16) + NW_SORT * 256 * sizeof(u32); }
+constexpr size_t smem_sort(u32 cap, u32 nt) { return cap * sizeof(Tuple) + 2 * cap * sizeof(u16) + (nt / 32) * 256 * sizeof(u32); }
+constexpr u32 NT_BIG = 512;  // threads of the 8192-tuple class (one block per SM; 1024 measured slower)
 constexpr size_t SMEM_SCAN = (3 * F_MAX + 1) * sizeof(u64);
 
 
@@ -964,10 +981,9 @@ void init_attrs_pass() {
   set_smem(k_scan<MODE_SPLIT>, SMEM_SCAN);
   set_smem(k_scatter<MODE_RADIX>, SMEM_SCATTER);
   set_smem(k_scatter<MODE_SPLIT>, SMEM_SCATTER);
-  set_smem(k_seg_sort<NMAX / 2, 2, false>, smem_sort(NMAX / 2));
-  set_smem(k_seg_sort<NMAX, 1, false>, smem_sort(NMAX));
-  set_smem(k_seg_sort<NMAX / 2, 2, true>, smem_sort(NMAX / 2));
-  set_smem(k_seg_sort<NMAX, 1, true>, smem_sort(NMAX));
+  set_smem(k_seg_sort<NMAX / 2, 2, false, NT_SORT>, smem_sort(NMAX / 2, NT_SORT));
+  set_smem(k_seg_sort<NMAX, 1, false, NT_BIG>, smem_sort(NMAX, NT_BIG));
+  set_smem(k_seg_sort<NMAX / 2, 2, true, NT_SORT>, smem_sort(NMAX / 2, NT_SORT));
 }
 
 namespace {
@@ -1050,18 +1066,17 @@ void launch_seg_sort(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs 
   // small segments first (two blocks per SM), then the large ones; each kernel
   // walks the whole list with its own work counter and skips the other class
   const FuseCtx none{};
-  k_seg_sort<NMAX / 2, 2, false><<<nsm * 2, NT_SORT, smem_sort(NMAX / 2), st>>>(segs, nseg, cap, work, bufs, jobs,
-                                                                               dst_where, err, none);
-  k_seg_sort<NMAX, 1, false><<<nsm, NT_SORT, smem_sort(NMAX), st>>>(segs, nseg, cap, work + 1, bufs, jobs, dst_where,
-                                                                    err, none);
+  k_seg_sort<NMAX / 2, 2, false, NT_SORT><<<nsm * 2, NT_SORT, smem_sort(NMAX / 2, NT_SORT), st>>>(
+      segs, nseg, cap, work, bufs, jobs, dst_where, err, none);
+  k_seg_sort<NMAX, 1, false, NT_BIG><<<nsm, NT_BIG, smem_sort(NMAX, NT_BIG), st>>>(segs, nseg, cap, work + 1, bufs, jobs,
+                                                                                 dst_where, err, none);
 }
 
 void launch_seg_sort_join(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs, u32* err,
                           const FuseCtx& fc, cudaStream_t st, int nsm) {
-  k_seg_sort<NMAX / 2, 2, true><<<nsm * 2, NT_SORT, smem_sort(NMAX / 2), st>>>(segs, nseg, cap, work, bufs, jobs,
-                                                                              W_XS, err, fc);
-  k_seg_sort<NMAX, 1, true><<<nsm, NT_SORT, smem_sort(NMAX), st>>>(segs, nseg, cap, work + 1, bufs, jobs, W_XS, err,
-                                                                   fc);
+  // one size class: segments above 4096 tuples are sorted and joined in pieces
+  k_seg_sort<NMAX / 2, 2, true, NT_SORT><<<nsm * 2, NT_SORT, smem_sort(NMAX / 2, NT_SORT), st>>>(
+      segs, nseg, cap, work, bufs, jobs, W_XS, err, fc);
 }
 
 void launch_fences(const Tuple* xr, u64 n, u64* fence, cudaStream_t st, int nsm) {

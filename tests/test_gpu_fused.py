@@ -64,3 +64,17 @@ def test_pairs_still_use_the_unfused_path():
     with Plan(w.n_r, w.n_s) as p:
         cnt, chk = p.join(to_dev(R), to_dev(S))
         assert (cnt, chk) == oracle.join(R, S)
+
+
+def test_fused_piece_of_equal_keys_inside_a_mixed_segment():
+    """One partition of 6000 S tuples, the first 5000 with key 2: the fused kernel
+    joins it in pieces of 4096, the first of which holds a single key while the
+    segment's R windows also hold key 3."""
+    R = np.array([[1, 11], [2, 22], [3, 33], [4, 44]], dtype=np.uint64)
+    S = np.zeros((6000, 2), dtype=np.uint64)
+    S[:5000, 0] = 2
+    S[5000:, 0] = 3
+    S[:, 1] = np.arange(6000, dtype=np.uint64) * 7919
+    want = oracle.join(R, S)
+    with Plan(16, 8192, partitions_s=1, runs_r=1) as p:
+        assert p.join(to_dev(R), to_dev(S)) == want
