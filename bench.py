@@ -44,7 +44,9 @@ ALG_BYTES = {
     "scatter_split": ("S tuples", 32),      # read S, write partitioned S (kept tuples)
     "seg_sort": ("tuples sorted", 32),      # read a segment, write it sorted
     "join": ("S' + R tuples", 16),          # read each kept S tuple and each R tuple once
-    "sort_join": ("S' + R tuples", 16),     # fused final sort + join: read each kept S and each R tuple once
+    # fused final sort + join: the work of the S sort pass (32) and of the join's reads (16 per S' and per R
+    # tuple); it moves only the reads (16 + 16), so its DRAM traffic sits below these algorithmic bytes
+    "sort_join": ("48 B per S' tuple + 16 B per R tuple", None),
     "scatter_radix": ("tuples", 32),        # one radix pass: read + write
     "hist_fine": ("S tuples", 8),           # read the S keys
     "hist_radix": ("tuples", 8),            # read the keys
@@ -66,6 +68,7 @@ def parse():
     ap.add_argument("--splitter", default="hist", choices=["hist", "learned"])
     ap.add_argument("--search", default="binary", choices=["binary", "learned"])
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
+    ap.add_argument("--pairs", action="store_true", help="materialise the matching pairs (|S| x 16 B buffer)")
     return ap.parse_args()
 
 
@@ -281,8 +284,11 @@ def run_ours(args):
     plan = Plan(w.n_r, w.n_s, stream=stream.cuda_stream, runs_r=args.runs,
                 splitter_mode=int(args.splitter == "learned"), search_mode=int(args.search == "learned"))
 
+    pairs = None
+    if args.pairs:  # foreign keys: exactly one pair per S tuple
+        pairs = torch.empty((w.n_s, 2), dtype=torch.int64, device=dev)
     for _ in range(args.warmup):
-        got = plan.join(R, S)
+        got = plan.join(R, S, pairs)
     st = plan.stats()
     launches_per_step = st["launches"]
 
@@ -298,7 +304,7 @@ def run_ours(args):
         e0.record(stream)
         results = []
         for _ in range(args.steps):
-            results.append(plan.join(R, S))
+            results.append(plan.join(R, S, pairs))
         e1.record(stream)
         e1.synchronize()
     barrier()
@@ -315,13 +321,13 @@ def run_ours(args):
     kt_steps = min(3, args.steps)
     ktimes = {}
     for _ in range(kt_steps):
-        plan.join(R, S)
+        plan.join(R, S, pairs)
         for name, (n, t) in plan.kernel_times().items():
             a = ktimes.setdefault(name, [0, 0.0])
             a[0] += n
             a[1] += t
     plan.set_flags(timing=True)
-    plan.join(R, S)
+    plan.join(R, S, pairs)
     st = plan.stats()
     plan.set_flags()
     th.join()
@@ -335,9 +341,12 @@ def run_ours(args):
         name, (n, t_ms) = dom
         per_launch_ms = t_ms / n
         unit_name, per_unit = ALG_BYTES.get(name, ("tuples", 16))
-        if name == "scatter_split":
+        if name == "sort_join":
+            units_launch = 1
+            per_unit = (48 * st["s_kept"] + 16 * w.n_r) * kt_steps / n
+        elif name == "scatter_split":
             units_launch = w.n_s
-        elif name in ("join", "sort_join"):
+        elif name == "join":
             units_launch = (st["s_kept"] + w.n_r) * kt_steps / n
         elif name == "seg_sort":
             units_launch = (w.n_r + st["s_kept"]) * kt_steps / n  # the two final sorts share the family
@@ -348,7 +357,8 @@ def run_ours(args):
         traffic = recorded_traffic(name, args.config)
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                "alg_bytes_per_launch": alg_bytes, "alg_unit": f"{per_unit} B per {unit_name}",
+                "alg_bytes_per_launch": alg_bytes,
+                "alg_unit": unit_name if name == "sort_join" else f"{per_unit} B per {unit_name}",
                 "ms_per_launch": per_launch_ms}
     alg_step = 80 * st["s_kept"] + 48 * w.n_r
     roof_step = {"alg_bytes_per_step": alg_step, "achieved": alg_step / (ms / 1e3) / 1e9,
@@ -356,7 +366,7 @@ def run_ours(args):
 
     # ---- end to end through the host-buffer entry point (pinned memory)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.pairs:
         Rh = torch.empty((w.n_r, 2), dtype=torch.int64, pin_memory=True)
         Sh = torch.empty((w.n_s, 2), dtype=torch.int64, pin_memory=True)
         Rh.copy_(R)
@@ -403,7 +413,7 @@ def run_ours(args):
             "kernels_ms": {k: [v[0], round(v[1] / kt_steps, 3)] for k, v in sorted(ktimes.items(),
                                                                                   key=lambda kv: -kv[1][1])},
             "levels": [st["levels_r"], st["levels_s"]], "imbalance": st["imbalance"],
-            "modes": {"splitter": args.splitter, "search": args.search},
+            "modes": {"splitter": args.splitter, "search": args.search, "pairs": bool(args.pairs)},
             "learned": {k: st[k] for k in ("ms_learn", "loss_s0", "loss_s", "loss_r0", "loss_r", "part_probes",
                                            "search_probes", "search_err", "part_max")},
         }

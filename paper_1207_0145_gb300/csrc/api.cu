@@ -653,7 +653,7 @@ int phase_sort_join(mpsm_plan* p) {
   for (u32 i = 0; i < p->njobs; ++i) totR += p->h_jobs[i].nR;
   LAUNCH(K_FENCES, launch_fences(p->xr, totR, p->d_fence, p->st, p->nsm));
   LAUNCH(K_SEG_SEARCH, launch_seg_search(p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, p->d_jobs, p->d_runs, p->xr, p->d_fence,
-                                         p->d_swin, p->maxT, p->st, p->nsm));
+                                         p->d_swin, p->maxT, lctx(p, search_learned(p)), p->st, p->nsm));
   record(p, EV_SEARCH);
   FuseCtx fc{p->d_swin, p->maxT, p->d_runs, p->xr, p->d_jobs};
   CK(cudaMemsetAsync(&p->d_cnt[C_WORK], 0, 2 * sizeof(u32), p->st));
@@ -895,11 +895,12 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   TRY(dalloc(&p->d_ls2, max_jobs));
   TRY(dalloc(&p->d_tot, T_NUM));
   const u64 s_chunks = 4ull * p->nsm + 2ull * max_jobs + 16;
-  p->hist_a_cap = std::max<u64>(nside / 32 + nside / 400 + (1u << 20), s_chunks * P_MAX);
+  // radix passes: chunks x F <= n / 32 at the regular fan-out, plus n / 64 for the one-bucket-per-key passes
+  p->hist_a_cap = std::max<u64>(nside / 32 + nside / 64 + (1u << 20), s_chunks * P_MAX);
   p->hist_b_cap = s_chunks * FINE_MAX;
   TRY(dalloc(&p->d_hist_a, p->hist_a_cap));
   TRY(dalloc(&p->d_hist_b, p->hist_b_cap));
-  p->bucket_cap = nside / 400 + 65536 + (u64)max_jobs * 64;
+  p->bucket_cap = nside / 64 + 65536 + (u64)max_jobs * 64;
   TRY(dalloc(&p->d_bmin, p->bucket_cap));
   TRY(dalloc(&p->d_bmax, p->bucket_cap));
   const u64 nf = (u64)max_jobs * FINE_MAX;

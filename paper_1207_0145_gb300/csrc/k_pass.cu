@@ -119,6 +119,13 @@ __global__ void __launch_bounds__(1024) k_level_plan(const Seg* segs, u32* nseg_
         const u32 bits = bitlen64(range);
         shift = bits > d ? bits - d : 0u;
         F = (u32)(range >> shift) + 1u;
+        // few distinct key values in many tuples (a hot key among few others): one
+        // bucket per value, so every child is constant or small after this pass; at
+        // most one bucket per 64 tuples keeps the histogram and bucket arrays in bounds
+        if (range < (u64)fmax && F < range + 1u && range + 1u <= s.len / 64u) {
+          shift = 0;
+          F = (u32)range + 1u;
+        }
         lo = s.kmin;
       } else {
         const Job& J = jobs[s.job];
@@ -900,7 +907,8 @@ __global__ void k_fences(const Tuple* xr, u64 n, u64* fence) {
 }
 
 // first position of run [off, off + len) whose key is >= key (upper: > key), minus off
-__device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 off, u64 len, u64 key, bool upper) {
+__device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 off, u64 len, u64 key, bool upper,
+                                         u32& probes) {
   const u64 end = off + len;
   u64 lo = off, hi = end;
   const u64 g0 = (off + 63) / 64, g1 = len ? (end - 1) / 64 + 1 : g0;
@@ -908,6 +916,7 @@ __device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 
     u64 a = g0, m = g1 - g0;
     while (m > 0) {
       const u64 h = m >> 1;
+      ++probes;
       const u64 f = fence[a + h];
       if (!(upper ? f > key : f >= key)) {
         a += h + 1;
@@ -922,6 +931,7 @@ __device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 
   u64 m = hi - lo;
   while (m > 0) {
     const u64 h = m >> 1;
+    ++probes;
     const u64 k = xr[lo + h].key;
     if (!(upper ? k > key : k >= key)) {
       lo += h + 1;
@@ -933,20 +943,52 @@ __device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 
   return lo - off;
 }
 
-// windows of every (final S segment, R run) pair from the segment's key bounds
+// windows of every (final S segment, R run) pair from the segment's key bounds:
+// fence search, or with the learned R-side model its predicted position times
+// the run length followed by an exact exponential + binary search
 __global__ void k_seg_search(const Seg* segs, const u32* nseg_ptr, u32 cap, const Job* jobs, const Run* runs,
-                             const Tuple* xr, const u64* fence, u32* swin, u32 maxT) {
+                             const Tuple* xr, const u64* fence, u32* swin, u32 maxT, LearnCtx lc) {
   u32 nseg = *nseg_ptr;
   if (nseg > cap) nseg = cap;
   const u64 total = (u64)nseg * maxT;
+  u32 probes = 0, nsearch = 0;
+  u64 err_sum = 0;
   for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (u64)gridDim.x * blockDim.x) {
     const u32 item = (u32)(idx / maxT), j = (u32)(idx - (u64)item * maxT);
     const Seg sg = segs[item];
     const Job& J = jobs[sg.job];
     if (j >= J.runs) continue;
     const Run r = runs[J.run_base + j];
-    swin[2 * idx] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmin, false);
-    swin[2 * idx + 1] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmax, true);
+    if (lc.models) {
+      const RmiModel* M = &lc.models[2 * sg.job + 1];
+      const Tuple* a = xr + r.off;
+      auto at = [&](u64 i) { return a[i].key; };
+      u64 g = (u64)(rmi_predict(M, sg.kmin) * (float)r.len);
+      g = g > r.len ? r.len : g;
+      const u64 lo = gallop_from(at, r.len, g, sg.kmin, probes);
+      err_sum += g > lo ? g - lo : lo - g;
+      u64 hi = r.len;
+      if (sg.kmax != ~0ull) {
+        u64 h = (u64)(rmi_predict(M, sg.kmax) * (float)r.len);
+        h = h < lo ? lo : (h > r.len ? r.len : h);
+        hi = gallop_from(at, r.len, h, sg.kmax + 1ull, probes);
+      }
+      swin[2 * idx] = (u32)lo;
+      swin[2 * idx + 1] = (u32)hi;
+    } else {
+      swin[2 * idx] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmin, false, probes);
+      swin[2 * idx + 1] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmax, true, probes);
+    }
+    nsearch += 2;
+  }
+  if (lc.stat) {
+    const u32 wp = warp_sum(probes), wn = warp_sum(nsearch);
+    const u64 we = warp_sum(err_sum);
+    if (lane_id() == 0 && wn) {
+      atomicAdd(&lc.stat[2], (u64)wp);
+      atomicAdd(&lc.stat[3], (u64)wn);
+      atomicAdd(&lc.stat[4], we);
+    }
   }
 }
 
@@ -1084,8 +1126,8 @@ void launch_fences(const Tuple* xr, u64 n, u64* fence, cudaStream_t st, int nsm)
 }
 
 void launch_seg_search(const Seg* segs, const u32* nseg, u32 cap, const Job* jobs, const Run* runs, const Tuple* xr,
-                       const u64* fence, u32* swin, u32 maxT, cudaStream_t st, int nsm) {
-  k_seg_search<<<nsm * 8, 256, 0, st>>>(segs, nseg, cap, jobs, runs, xr, fence, swin, maxT);
+                       const u64* fence, u32* swin, u32 maxT, const LearnCtx& lc, cudaStream_t st, int nsm) {
+  k_seg_search<<<nsm * 8, 256, 0, st>>>(segs, nseg, cap, jobs, runs, xr, fence, swin, maxT, lc);
 }
 
 void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st) {

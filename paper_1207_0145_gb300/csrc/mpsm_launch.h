@@ -35,7 +35,7 @@ void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st);
 // phases 3 + 4 fused (k_pass.cu): fences of the sorted runs, per (segment, run) windows, sort-and-join
 void launch_fences(const Tuple* xr, u64 n, u64* fence, cudaStream_t st, int nsm);
 void launch_seg_search(const Seg* segs, const u32* nseg, u32 cap, const Job* jobs, const Run* runs, const Tuple* xr,
-                       const u64* fence, u32* swin, u32 maxT, cudaStream_t st, int nsm);
+                       const u64* fence, u32* swin, u32 maxT, const LearnCtx& lc, cudaStream_t st, int nsm);
 void launch_seg_sort_join(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs, u32* err,
                           const FuseCtx& fc, cudaStream_t st, int nsm);
 
