@@ -581,8 +581,8 @@ __device__ __forceinline__ void seg_join_const(const Tuple* s, u32 n, u64 key, c
 constexpr u32 RCH = 128;
 
 template <u32 CAP, u32 NT>
-__device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* dir, u32* rtab, u32 n, u64 mn, u64 mx,
-                                         const Seg& sg, u32 item, const FuseCtx& fc, u64* s_red) {
+__device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* dir, u32* rtab, const u32* cdir, u32 n,
+                                         u64 mn, u64 mx, const Seg& sg, u32 item, const FuseCtx& fc, u64* s_red) {
   constexpr u32 DB = (CAP >= 8192u) ? 12u : 11u;  // 2^DB = CAP / 2 buckets
   const u32 tid = threadIdx.x;
   const Job& J = fc.jobs[sg.job];
@@ -590,12 +590,14 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
   const u32 rbits = bitlen64(mx - mn);
   const u32 dsh = rbits > DB ? rbits - DB : 0u;
   const u32 nbk = (u32)((mx - mn) >> dsh) + 1u;
-  for (u32 i = tid; i < n; i += NT) {
-    const u32 b = (u32)((tup[ia[i]].key - mn) >> dsh);
-    const u32 x0 = i ? (u32)((tup[ia[i - 1]].key - mn) >> dsh) + 1u : 0u;
-    for (u32 x = x0; x <= b; ++x) dir[x] = (u16)i;
-    if (i == n - 1)
-      for (u32 x = b + 1u; x <= nbk; ++x) dir[x] = (u16)n;
+  if (!cdir) {
+    for (u32 i = tid; i < n; i += NT) {
+      const u32 b = (u32)((tup[ia[i]].key - mn) >> dsh);
+      const u32 x0 = i ? (u32)((tup[ia[i - 1]].key - mn) >> dsh) + 1u : 0u;
+      for (u32 x = x0; x <= b; ++x) dir[x] = (u16)i;
+      if (i == n - 1)
+        for (u32 x = b + 1u; x <= nbk; ++x) dir[x] = (u16)n;
+    }
   }
   u32* wl = rtab;                                            // RCH window starts
   u32* wpre = rtab + RCH;                                    // RCH + 1 window prefix
@@ -661,9 +663,17 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
         if (q >= W) continue;
         const u64 key = r[u].key;
         if (key < mn || key > mx) continue;
-        const u32 bi = (u32)((key - mn) >> dsh);
-        u32 lb = dir[bi], ub = dir[bi + 1];
-        if (dsh) {  // a bucket spans several keys: narrow [lb, ub) to `key`
+        u32 lb, ub;
+        if (cdir) {  // exact per-key starts
+          const u32 d = (u32)(key - mn);
+          lb = cdir[d];
+          ub = cdir[d + 1];
+        } else {
+          const u32 bi = (u32)((key - mn) >> dsh);
+          lb = dir[bi];
+          ub = dir[bi + 1];
+        }
+        if (!cdir && dsh) {  // a bucket spans several keys: narrow [lb, ub) to `key`
           u32 a = lb, m = ub - lb;
           while (m > 0) {
             const u32 h = m >> 1;
@@ -760,30 +770,35 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
       failed = true;
       break;
     }
-    // exact key range of the segment
+    // key range: the segment's exact bounds from the pass that made it, else a reduction
     u64 mn = ~0ull, mx = 0;
-    for (u32 i = tid; i < n; i += NT) {
-      const u64 k = tup[i].key;
-      mn = k < mn ? k : mn;
-      mx = k > mx ? k : mx;
-    }
+    if (sg.flags & SEG_EXACT) {
+      mn = sg.kmin;
+      mx = sg.kmax;
+    } else {
+      for (u32 i = tid; i < n; i += NT) {
+        const u64 k = tup[i].key;
+        mn = k < mn ? k : mn;
+        mx = k > mx ? k : mx;
+      }
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      const u64 a = __shfl_xor_sync(0xffffffffu, mn, d), b = __shfl_xor_sync(0xffffffffu, mx, d);
-      mn = a < mn ? a : mn;
-      mx = b > mx ? b : mx;
-    }
-    if (lane == 0) {
-      s_mn[wid] = mn;
-      s_mx[wid] = mx;
-    }
-    __syncthreads();
-    mn = s_mn[0];
-    mx = s_mx[0];
+      for (int d = 16; d > 0; d >>= 1) {
+        const u64 a = __shfl_xor_sync(0xffffffffu, mn, d), b = __shfl_xor_sync(0xffffffffu, mx, d);
+        mn = a < mn ? a : mn;
+        mx = b > mx ? b : mx;
+      }
+      if (lane == 0) {
+        s_mn[wid] = mn;
+        s_mx[wid] = mx;
+      }
+      __syncthreads();
+      mn = s_mn[0];
+      mx = s_mx[0];
 #pragma unroll
-    for (u32 w = 1; w < NW; ++w) {
-      mn = s_mn[w] < mn ? s_mn[w] : mn;
-      mx = s_mx[w] > mx ? s_mx[w] : mx;
+      for (u32 w = 1; w < NW; ++w) {
+        mn = s_mn[w] < mn ? s_mn[w] : mn;
+        mx = s_mx[w] > mx ? s_mx[w] : mx;
+      }
     }
     const u32 bits = bitlen64(mx - mn);
     if (bits == 0) {
@@ -812,6 +827,7 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     }
     __syncthreads();
     smem_exclusive_scan<u32, NT, 2048 / NT>(cnt, F1, s_warp);
+    if (tid == 0) cnt[F1] = n;  // with bits <= 11, cnt is then the start of every key value
 #pragma unroll
     for (u32 i = 0; i < IT; ++i) {
       const u32 e = tid + i * NT;
@@ -886,7 +902,10 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
       sh += w;
     }
     if (FUSE) {
-      seg_join<CAP, NT>(tup, ia, ib, cnt, n, mn, mx, sg, item, fc, s_red);
+      if (bits <= 11u)  // one counting pass: its digit starts are an exact per-key directory
+        seg_join<CAP, NT>(tup, ia, nullptr, reinterpret_cast<u32*>(ib), cnt, n, mn, mx, sg, item, fc, s_red);
+      else
+        seg_join<CAP, NT>(tup, ia, ib, cnt, nullptr, n, mn, mx, sg, item, fc, s_red);
     } else {
       for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, tup[ia[i]]);
     }
