@@ -486,7 +486,7 @@ int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels, bool k
                 nullptr, p->d_big[cur ^ 1], &p->d_cnt[C_BIG0 + (cur ^ 1)], p->big_cap, p->d_fin, &p->d_cnt[C_FIN],
                 p->fin_cap, dst, p->d_jobs, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm, keep_const));
     LAUNCH(K_SCATTER_RADIX, launch_scatter(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs,
-                   src, dst, p->d_hist_a, nullptr, &p->d_cnt[C_ERR], lctx(p, false), p->st, p->nsm));
+                   src, dst, p->d_hist_a, nullptr, &p->d_cnt[C_ERR], lctx(p, false), p->st, p->nsm, lvl == 0));
     CK(cudaGetLastError());
     src = dst;
     cur ^= 1;

@@ -32,7 +32,12 @@ namespace mpsm {
 namespace {
 
 constexpr u32 NT_PASS = 512;
-constexpr u32 SC_TILE = 4096;  // tuples per scatter tile
+// scatter geometry (measured): the first radix pass over runs or partitions, fanning
+// out up to 2048 ways, writes longer runs per bucket from 8192-tuple tiles (one
+// 1024-thread block per SM); the range-partition scatter and the later radix passes
+// over smaller segments are fastest with 4096-tuple tiles and two 512-thread blocks
+constexpr u32 RX_TILE = 8192, RX_NT = 1024, RX_MINB = 1;
+constexpr u32 SP_TILE = 4096, SP_NT = 512, SP_MINB = 2;
 constexpr u32 NT_SORT = 512;
 constexpr u32 NW_SORT = NT_SORT / 32;
 
@@ -382,17 +387,17 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
 
 // ---------------------------------------------------------------- scatter
 // Per chunk (worker): tiles of SC_TILE tuples arrive by bulk async copy into
-// shared memory (two blocks per SM, so one block's copy overlaps the other's
+// shared memory (with two blocks per SM one block's copy overlaps the other's
 // work).  Each tuple gets
 // (bucket, rank) from a shared-memory counter; an exclusive scan gives the
 // tile's bucket starts; a permutation index orders the tile by bucket so the
 // write-out stores runs of consecutive destinations (coalesced 16-byte stores).
-template <u32 MODE>
-__global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u32* nseg_ptr, const LSeg* ls,
+template <u32 MODE, u32 SC_TILE, u32 NT_SC, u32 SC_MINB>
+__global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, const u32* nseg_ptr, const LSeg* ls,
                                                         const u64* totals, u64 chunk, Bufs bufs, const Job* jobs,
                                                         u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
                                                         u32* err, LearnCtx lc) {
-  constexpr u32 IT = SC_TILE / NT_PASS;
+  constexpr u32 IT = SC_TILE / NT_SC;
   constexpr u32 DROP = 0xFFFFFFFFu;
   extern __shared__ __align__(128) unsigned char sm_raw[];
   Tuple* stage = reinterpret_cast<Tuple*>(sm_raw);                 // SC_TILE
@@ -404,7 +409,7 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
   u16* spl = sb + SC_TILE;                                         // FINE_MAX (MODE_SPLIT)
   __shared__ __align__(8) u64 mbar;
   __shared__ u32 s_seg;
-  __shared__ u32 s_warp[NT_PASS / 32 + 1];
+  __shared__ u32 s_warp[NT_SC / 32 + 1];
   const u32 tid = threadIdx.x;
   if (tid == 0) mbar_init(&mbar, 1);
   __syncthreads();
@@ -420,7 +425,7 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
     const u32 F = L.F;
     const u64 ci = c - L.chunk_base;
     const u32* orow = hist + L.hist_base + ci * F;
-    for (u32 b = tid; b < F; b += NT_PASS) {
+    for (u32 b = tid; b < F; b += NT_SC) {
       cur[b] = orow[b];
       hcnt[b] = 0;
     }
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
       const Job& J = jobs[S.job];
       kmin = J.kmin;
       kmax = J.kmax;
-      for (u32 f = tid; f < J.nfine; f += NT_PASS) spl[f] = (u16)(MODE == MODE_SPLIT ? sp : lc.cell)[J.fine_base + f];
+      for (u32 f = tid; f < J.nfine; f += NT_SC) spl[f] = (u16)(MODE == MODE_SPLIT ? sp : lc.cell)[J.fine_base + f];
     }
     const u64 row0 = S.off - jobs[S.job].s_base;  // MODE_LEARN: row of the segment's first tuple in the job's S
     u32 probes = 0;
@@ -454,7 +459,7 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
       u32 br[IT];
 #pragma unroll
       for (u32 i = 0; i < IT; ++i) {
-        const u32 x = i * NT_PASS + tid;
+        const u32 x = i * NT_SC + tid;
         br[i] = DROP;
         if (x >= n) continue;
         const u64 key = T[x].key;
@@ -478,7 +483,7 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
       __syncthreads();
       // hb = exclusive scan of hcnt
       {
-        constexpr u32 PER = F_MAX / NT_PASS;
+        constexpr u32 PER = F_MAX / NT_SC;
         u32 loc[PER], sum = 0;
 #pragma unroll
         for (u32 i = 0; i < PER; ++i) {
@@ -487,7 +492,7 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
           sum += loc[i];
         }
         u32 tot;
-        u32 pre = block_exclusive_scan<u32, NT_PASS>(sum, &tot, s_warp);
+        u32 pre = block_exclusive_scan<u32, NT_SC>(sum, &tot, s_warp);
 #pragma unroll
         for (u32 i = 0; i < PER; ++i) {
           const u32 b = tid * PER + i;
@@ -501,18 +506,18 @@ __global__ void __launch_bounds__(NT_PASS, 2) k_scatter(const Seg* segs, const u
         if (br[i] == DROP) continue;
         const u32 b = br[i] >> 16;
         const u32 p = hb[b] + (br[i] & 0xFFFFu);
-        sidx[p] = (u16)(i * NT_PASS + tid);
+        sidx[p] = (u16)(i * NT_SC + tid);
         sb[p] = (u16)b;
       }
       __syncthreads();
       const u32 kept = hb[F - 1] + hcnt[F - 1];
-      for (u32 p = tid; p < kept; p += NT_PASS) {
+      for (u32 p = tid; p < kept; p += NT_SC) {
         const u32 b = sb[p];
         st_tuple(dst + cur[b] + (p - hb[b]), T[sidx[p]]);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
-      for (u32 b = tid; b < F; b += NT_PASS) {
+      for (u32 b = tid; b < F; b += NT_SC) {
         cur[b] += hcnt[b];
         hcnt[b] = 0;
       }
@@ -1015,8 +1020,9 @@ __global__ void k_check_empty(const u32* cnt, u32* err, u32 flag) {
   if (threadIdx.x == 0 && *cnt != 0) atomicOr(err, flag);
 }
 
-constexpr size_t SMEM_SCATTER = SC_TILE * sizeof(Tuple) + 3 * F_MAX * sizeof(u32) + 2 * SC_TILE * sizeof(u16) +
-                                FINE_MAX * sizeof(u16);
+constexpr size_t smem_scatter(u32 tile) {
+  return tile * sizeof(Tuple) + 3 * F_MAX * sizeof(u32) + 2 * tile * sizeof(u16) + FINE_MAX * sizeof(u16);
+}
 constexpr size_t smem_sort(u32 cap, u32 nt) { return cap * sizeof(Tuple) + 2 * cap * sizeof(u16) + (nt / 32) * 256 * sizeof(u32); }
 constexpr u32 NT_BIG = 512;  // threads of the 8192-tuple class (one block per SM; 1024 measured slower)
 constexpr size_t SMEM_SCAN = (3 * F_MAX + 1) * sizeof(u64);
@@ -1037,11 +1043,12 @@ void init_attrs_pass() {
   set_smem(k_hist<MODE_FINE, FINE_MAX>, FINE_MAX * 20);
   set_smem(k_hist<MODE_LEARN, F_MAX>, F_MAX * 20 + FINE_MAX * 2);
   set_smem(k_scan<MODE_LEARN>, SMEM_SCAN);
-  set_smem(k_scatter<MODE_LEARN>, SMEM_SCATTER);
+  set_smem(k_scatter<MODE_LEARN, SP_TILE, SP_NT, SP_MINB>, smem_scatter(SP_TILE));
   set_smem(k_scan<MODE_RADIX>, SMEM_SCAN);
   set_smem(k_scan<MODE_SPLIT>, SMEM_SCAN);
-  set_smem(k_scatter<MODE_RADIX>, SMEM_SCATTER);
-  set_smem(k_scatter<MODE_SPLIT>, SMEM_SCATTER);
+  set_smem(k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB>, smem_scatter(RX_TILE));
+  set_smem(k_scatter<MODE_RADIX, SP_TILE, SP_NT, SP_MINB>, smem_scatter(SP_TILE));
+  set_smem(k_scatter<MODE_SPLIT, SP_TILE, SP_NT, SP_MINB>, smem_scatter(SP_TILE));
   set_smem(k_seg_sort<NMAX / 2, 2, false, NT_SORT>, smem_sort(NMAX / 2, NT_SORT));
   set_smem(k_seg_sort<NMAX, 1, false, NT_BIG>, smem_sort(NMAX, NT_BIG));
   set_smem(k_seg_sort<NMAX / 2, 2, true, NT_SORT>, smem_sort(NMAX / 2, NT_SORT));
@@ -1109,16 +1116,19 @@ void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32
 
 void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                     Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
-                    u32* err, const LearnCtx& lc, cudaStream_t st, int nsm) {
+                    u32* err, const LearnCtx& lc, cudaStream_t st, int nsm, bool big_tiles) {
   if (mode == MODE_SPLIT) {
-    k_scatter<MODE_SPLIT><<<nsm * 2, NT_PASS, SMEM_SCATTER, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
-                                                                  src_where, dst_where, hist, sp, err, lc);
+    k_scatter<MODE_SPLIT, SP_TILE, SP_NT, SP_MINB><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
+        segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   } else if (mode == MODE_LEARN) {
-    k_scatter<MODE_LEARN><<<nsm * 2, NT_PASS, SMEM_SCATTER, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
-                                                                  src_where, dst_where, hist, sp, err, lc);
+    k_scatter<MODE_LEARN, SP_TILE, SP_NT, SP_MINB><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
+        segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
+  } else if (big_tiles) {
+    k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB><<<nsm * RX_MINB, RX_NT, smem_scatter(RX_TILE), st>>>(
+        segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   } else {
-    k_scatter<MODE_RADIX><<<nsm * 2, NT_PASS, SMEM_SCATTER, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
-                                                                  src_where, dst_where, hist, sp, err, lc);
+    k_scatter<MODE_RADIX, SP_TILE, SP_NT, SP_MINB><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
+        segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   }
 }
 

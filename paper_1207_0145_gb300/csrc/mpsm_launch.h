@@ -28,7 +28,7 @@ void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32
                  int nsm, bool keep_const = false);
 void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                     Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
-                    u32* err, const LearnCtx& lc, cudaStream_t st, int nsm);
+                    u32* err, const LearnCtx& lc, cudaStream_t st, int nsm, bool big_tiles = false);
 void launch_seg_sort(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs,
                      u32 dst_where, u32* err, cudaStream_t st, int nsm);
 void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st);
