@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=20120145)
     ap.add_argument("--runs", type=int, default=0, help="T_R (0 = automatic)")
+    ap.add_argument("--parts", type=int, default=0, help="P, partitions of S (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16, help="CPU baseline runs 1/this of the workload")
@@ -281,7 +282,7 @@ def run_ours(args):
         w.fill_r_device(R.data_ptr(), stream.cuda_stream)
         w.fill_s_device(S.data_ptr(), stream.cuda_stream)
     stream.synchronize()
-    plan = Plan(w.n_r, w.n_s, stream=stream.cuda_stream, runs_r=args.runs,
+    plan = Plan(w.n_r, w.n_s, stream=stream.cuda_stream, runs_r=args.runs, partitions_s=args.parts,
                 splitter_mode=int(args.splitter == "learned"), search_mode=int(args.search == "learned"))
 
     pairs = None
