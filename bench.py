@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--search", default="binary", choices=["binary", "learned"])
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
     ap.add_argument("--pairs", action="store_true", help="materialise the matching pairs (|S| x 16 B buffer)")
+    ap.add_argument("--side", default="s", choices=["s", "r", "smaller"], help="input that is range-partitioned")
     return ap.parse_args()
 
 
@@ -283,8 +284,12 @@ def run_ours(args):
         w.fill_s_device(S.data_ptr(), stream.cuda_stream)
     stream.synchronize()
     plan = Plan(w.n_r, w.n_s, stream=stream.cuda_stream, runs_r=args.runs, partitions_s=args.parts,
+                partition_side={"s": 0, "r": 1, "smaller": 2}[args.side],
                 splitter_mode=int(args.splitter == "learned"), search_mode=int(args.search == "learned"))
 
+    # the run side and the partitioned side (swapped under role reversal)
+    rev = args.side == "r" or (args.side == "smaller" and w.n_r < w.n_s)
+    n_run, n_part = (w.n_s, w.n_r) if rev else (w.n_r, w.n_s)
     pairs = None
     if args.pairs:  # foreign keys: exactly one pair per S tuple
         pairs = torch.empty((w.n_s, 2), dtype=torch.int64, device=dev)
@@ -344,13 +349,13 @@ def run_ours(args):
         unit_name, per_unit = ALG_BYTES.get(name, ("tuples", 16))
         if name == "sort_join":
             units_launch = 1
-            per_unit = (48 * st["s_kept"] + 16 * w.n_r) * kt_steps / n
+            per_unit = (48 * st["s_kept"] + 16 * n_run) * kt_steps / n
         elif name == "scatter_split":
-            units_launch = w.n_s
+            units_launch = n_part
         elif name == "join":
-            units_launch = (st["s_kept"] + w.n_r) * kt_steps / n
+            units_launch = (st["s_kept"] + n_run) * kt_steps / n
         elif name == "seg_sort":
-            units_launch = (w.n_r + st["s_kept"]) * kt_steps / n  # the two final sorts share the family
+            units_launch = (n_run + st["s_kept"]) * kt_steps / n  # the two final sorts share the family
         else:
             units_launch = (w.n_r + w.n_s) * kt_steps / n
         alg_bytes = per_unit * units_launch
@@ -361,7 +366,7 @@ def run_ours(args):
                 "alg_bytes_per_launch": alg_bytes,
                 "alg_unit": unit_name if name == "sort_join" else f"{per_unit} B per {unit_name}",
                 "ms_per_launch": per_launch_ms}
-    alg_step = 80 * st["s_kept"] + 48 * w.n_r
+    alg_step = 80 * st["s_kept"] + 48 * n_run
     roof_step = {"alg_bytes_per_step": alg_step, "achieved": alg_step / (ms / 1e3) / 1e9,
                  "frac": alg_step / (ms / 1e3) / 1e9 / peak}
 
@@ -414,7 +419,8 @@ def run_ours(args):
             "kernels_ms": {k: [v[0], round(v[1] / kt_steps, 3)] for k, v in sorted(ktimes.items(),
                                                                                   key=lambda kv: -kv[1][1])},
             "levels": [st["levels_r"], st["levels_s"]], "imbalance": st["imbalance"],
-            "modes": {"splitter": args.splitter, "search": args.search, "pairs": bool(args.pairs)},
+            "modes": {"splitter": args.splitter, "search": args.search, "pairs": bool(args.pairs),
+                      "partitioned": args.side},
             "learned": {k: st[k] for k in ("ms_learn", "loss_s0", "loss_s", "loss_r0", "loss_r", "part_probes",
                                            "search_probes", "search_err", "part_max")},
         }

@@ -315,6 +315,9 @@ CONFIGS = {
     "pairs-100M-400M": lambda seed=DEFAULT_SEED: plain(100 * M, 400 * M, seed),
     "plain-25M-100M": lambda seed=DEFAULT_SEED: plain(25 * M, 100 * M, seed),
     "plain-12M-48M": lambda seed=DEFAULT_SEED: plain(12 * M, 48 * M, seed),
+    # multiplicities 1 and 16 beside the headline's 4 (role reversal, Sec. 5.4)
+    "plain-800M-800M": lambda seed=DEFAULT_SEED: plain(800 * M, 800 * M, seed),
+    "plain-200M-3200M": lambda seed=DEFAULT_SEED: plain(200 * M, 3200 * M, seed),
     "zipf0.9-200M-800M": lambda seed=DEFAULT_SEED: zipf(200 * M, 800 * M, 0.9, seed),
     "sparse-1600M-1600M": lambda seed=DEFAULT_SEED: sparse(1600 * M, 1600 * M, 0.7, seed),
 }

@@ -57,6 +57,10 @@ enum {
 
 enum { MPSM_SPLIT_HIST = 0, MPSM_SPLIT_LEARNED = 1 };
 enum { MPSM_SEARCH_BINARY = 0, MPSM_SEARCH_LEARNED = 1 };
+/* Role of the inputs (Sec. 3.2, Sec. 5.4 "role reversal"): which input is
+ * range-partitioned; the other one is cut into sorted runs.  The result does not
+ * depend on it (pairs keep their (r_payload, s_payload) order either way). */
+enum { MPSM_PART_S = 0, MPSM_PART_R = 1, MPSM_PART_SMALLER = 2 };
 enum {
   MPSM_FLAG_TIMING = 1u,          /* record per-phase CUDA events (read by mpsm_plan_stats)        */
   MPSM_FLAG_KERNEL_TIMING = 2u,   /* record CUDA events around every kernel launch (read by
@@ -79,7 +83,10 @@ typedef struct {
   uint64_t seed;           /* seed of the hash that spreads hot keys over learned partitions */
   uint32_t learn_steps;    /* Adam steps of the learned model; 0 = 200                       */
   uint32_t run_len;        /* target R tuples per run when runs_r = 0; 0 = automatic          */
-  uint32_t reserved[4];    /* must be zero                                                   */
+  uint32_t partition_side; /* MPSM_PART_*: mpsm_join / mpsm_join_host partition S (default), R,
+                              or the smaller input; the plan is then sized for either role.
+                              The phase entry points and mpsm_join_batch use the default      */
+  uint32_t reserved[3];    /* must be zero                                                   */
 } mpsm_options_t;
 
 /* Fills *opt with the defaults (all automatic, histogram splitters, binary search). */

@@ -827,8 +827,9 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   mpsm_options_t o;
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
       if (o.reserved[i]) return MPSM_ERR_INVALID_ARG;
+    if (o.partition_side > MPSM_PART_SMALLER) return MPSM_ERR_INVALID_ARG;
   } else {
     mpsm_options_default(&o);
   }
@@ -841,6 +842,7 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   if (!p) return MPSM_ERR_OOM;
   p->opt = o;
   p->st = (cudaStream_t)stream;
+  if (o.partition_side != MPSM_PART_S) max_nR = max_nS = std::max(max_nR, max_nS);  // either input may take either role
   p->max_nR = max_nR;
   p->max_nS = max_nS;
   p->max_jobs = max_jobs;
@@ -1020,12 +1022,27 @@ static int join_device(mpsm_plan_t* p, const mpsm_tuple_t* R, uint64_t nR, const
   return phase_join(p, out_count, out_checksum, pairs);
 }
 
+// Role reversal (Sec. 5.4): partition R and cut S into runs by joining S with R;
+// count and checksum are symmetric, and the pairs get their columns swapped back.
+static bool reverse_roles(const mpsm_plan* p, u64 nR, u64 nS) {
+  return p->opt.partition_side == MPSM_PART_R || (p->opt.partition_side == MPSM_PART_SMALLER && nR < nS);
+}
+
 MPSM_API int mpsm_join(mpsm_plan_t* p, const mpsm_tuple_t* R, uint64_t nR, const mpsm_tuple_t* S, uint64_t nS,
                        uint64_t* out_count, uint64_t* out_checksum, mpsm_pairs_t* pairs) {
   int rc = check_inputs(p, R, nR, S, nS);
   if (rc) return rc;
   if (pairs && pairs->capacity && (!pairs->data || !aligned16(pairs->data))) return MPSM_ERR_INVALID_ARG;
-  return join_device(p, R, nR, S, nS, out_count, out_checksum, pairs);
+  if (!reverse_roles(p, nR, nS)) return join_device(p, R, nR, S, nS, out_count, out_checksum, pairs);
+  uint64_t cnt = 0;
+  rc = join_device(p, S, nS, R, nR, &cnt, out_checksum, pairs);
+  if (out_count) *out_count = cnt;
+  if (rc == MPSM_OK && pairs && pairs->data && cnt) {
+    launch_swap_pairs(reinterpret_cast<Tuple*>(pairs->data), std::min<u64>(cnt, pairs->capacity), p->st, p->nsm);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(p->st));
+  }
+  return rc;
 }
 
 MPSM_API int mpsm_join_host(mpsm_plan_t* p, const mpsm_tuple_t* R_host, uint64_t nR, const mpsm_tuple_t* S_host,
@@ -1036,8 +1053,10 @@ MPSM_API int mpsm_join_host(mpsm_plan_t* p, const mpsm_tuple_t* R_host, uint64_t
   if (!p->stage_s && dalloc(&p->stage_s, p->max_nS)) return MPSM_ERR_OOM;
   if (nR) CK(cudaMemcpyAsync(p->stage_r, R_host, nR * sizeof(Tuple), cudaMemcpyHostToDevice, p->st));
   if (nS) CK(cudaMemcpyAsync(p->stage_s, S_host, nS * sizeof(Tuple), cudaMemcpyHostToDevice, p->st));
-  return join_device(p, reinterpret_cast<const mpsm_tuple_t*>(p->stage_r), nR,
-                     reinterpret_cast<const mpsm_tuple_t*>(p->stage_s), nS, out_count, out_checksum, nullptr);
+  const mpsm_tuple_t* r = reinterpret_cast<const mpsm_tuple_t*>(p->stage_r);
+  const mpsm_tuple_t* sd = reinterpret_cast<const mpsm_tuple_t*>(p->stage_s);
+  if (reverse_roles(p, nR, nS)) return join_device(p, sd, nS, r, nR, out_count, out_checksum, nullptr);
+  return join_device(p, r, nR, sd, nS, out_count, out_checksum, nullptr);
 }
 
 MPSM_API int mpsm_join_batch(mpsm_plan_t* p, const mpsm_job_t* jobs, uint32_t njobs, uint64_t* out_counts,

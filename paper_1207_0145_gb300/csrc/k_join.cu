@@ -487,6 +487,18 @@ void launch_join(u32 mode, Job* jobs, u32 njobs, const Run* runs, const Tuple* x
   }
 }
 
+// (a, b) -> (b, a) for n pairs (role reversal: the run side wrote its payload first)
+__global__ void k_swap_pairs(Tuple* pairs, u64 n) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+    const Tuple t = pairs[i];
+    st_tuple(pairs + i, Tuple{t.pay, t.key});
+  }
+}
+
+void launch_swap_pairs(Tuple* pairs, u64 n, cudaStream_t st, int nsm) {
+  if (n) k_swap_pairs<<<nsm * 8, 256, 0, st>>>(pairs, n);
+}
+
 void launch_pair_offsets(Job* jobs, u32 njobs, const u64* totals, const u64* tile_cnt, u64* tile_out,
                          u64* pair_total, cudaStream_t st) {
   k_pair_offsets<<<1, 1024, 0, st>>>(jobs, njobs, totals, tile_cnt, tile_out, pair_total);

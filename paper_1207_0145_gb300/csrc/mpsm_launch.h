@@ -55,6 +55,7 @@ void launch_search(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr,
 void launch_join(u32 mode, Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,
                  const u64* totals, const u32* win, u64* tile_cnt, const u64* tile_out, Tuple* pairs,
                  u32* err, cudaStream_t st, int nsm);
+void launch_swap_pairs(Tuple* pairs, u64 n, cudaStream_t st, int nsm);
 void launch_pair_offsets(Job* jobs, u32 njobs, const u64* totals, const u64* tile_cnt, u64* tile_out,
                          u64* pair_total, cudaStream_t st);
 
