@@ -66,12 +66,50 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16, help="CPU baseline runs 1/this of the workload")
-    ap.add_argument("--splitter", default="hist", choices=["hist", "learned"])
+    ap.add_argument("--splitter", default="hist", choices=["hist", "learned", "equi-height"])
+    ap.add_argument("--fine-bits", type=int, default=0, help="B, fine histogram bits of S (0 = 12)")
     ap.add_argument("--search", default="binary", choices=["binary", "learned"])
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
     ap.add_argument("--pairs", action="store_true", help="materialise the matching pairs (|S| x 16 B buffer)")
     ap.add_argument("--side", default="s", choices=["s", "r", "smaller"], help="input that is range-partitioned")
     return ap.parse_args()
+
+
+SPLITTER_MODES = {"hist": 0, "learned": 1, "equi-height": 2}
+
+
+def _device_array(ptr: int, n: int, dtype):
+    """Copy n values of dtype from a device pointer of the plan's view."""
+    import numpy as np
+    import torch
+
+    nbytes = n * np.dtype(dtype).itemsize
+
+    class _CAI:
+        __cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3,
+                                    "strides": None}
+
+    return torch.as_tensor(_CAI(), device="cuda").cpu().numpy().view(dtype)
+
+
+def partition_balance(plan, st):
+    """Per partition of the partitioned side: its size n and the run-side tuples r in
+    its key range, from the fine histograms and the splitter vector of the last
+    join; the largest over the mean of n and of the split-relevant cost
+    n log2 n + T n + r (Sec. 4.3), the quantity Fig. 16 balances."""
+    import numpy as np
+
+    v = plan.view()
+    nb, P, T = int(v.nfine), int(v.partitions_s), int(st["runs_r"])
+    if nb == 0 or P == 0:
+        return None
+    sp = _device_array(v.splitters, nb, np.uint32).astype(np.int64)
+    n = np.bincount(sp, weights=_device_array(v.fine_s, nb, np.uint64).astype(np.float64), minlength=P)
+    r = np.bincount(sp, weights=_device_array(v.fine_r, nb, np.uint64).astype(np.float64), minlength=P)
+    cost = n * np.log2(np.maximum(n, 1.0)) + T * n + r
+    return {"parts": P, "fine_buckets": nb, "size_max_over_mean": float(n.max() / n.mean()),
+            "cost_max_over_mean": float(cost.max() / cost.mean()),
+            "run_side_max_over_mean": float(r.max() / max(r.mean(), 1.0))}
 
 
 def dist_env():
@@ -285,7 +323,8 @@ def run_ours(args):
     stream.synchronize()
     plan = Plan(w.n_r, w.n_s, stream=stream.cuda_stream, runs_r=args.runs, partitions_s=args.parts,
                 partition_side={"s": 0, "r": 1, "smaller": 2}[args.side],
-                splitter_mode=int(args.splitter == "learned"), search_mode=int(args.search == "learned"))
+                splitter_mode=SPLITTER_MODES[args.splitter], search_mode=int(args.search == "learned"),
+                fine_bits=args.fine_bits)
 
     # the run side and the partitioned side (swapped under role reversal)
     rev = args.side == "r" or (args.side == "smaller" and w.n_r < w.n_s)
@@ -397,6 +436,7 @@ def run_ours(args):
         e2e = {"value": total_units / (ems / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": units * 16,
                "d2h_bytes_per_step": 16, "ms_per_step": ems}
 
+    balance = partition_balance(plan, st) if args.splitter != "learned" else None
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, args.cpu_sample)
@@ -419,6 +459,7 @@ def run_ours(args):
             "kernels_ms": {k: [v[0], round(v[1] / kt_steps, 3)] for k, v in sorted(ktimes.items(),
                                                                                   key=lambda kv: -kv[1][1])},
             "levels": [st["levels_r"], st["levels_s"]], "imbalance": st["imbalance"],
+            "balance": balance,
             "modes": {"splitter": args.splitter, "search": args.search, "pairs": bool(args.pairs),
                       "partitioned": args.side},
             "learned": {k: st[k] for k in ("ms_learn", "loss_s0", "loss_s", "loss_r0", "loss_r", "part_probes",

@@ -11,7 +11,9 @@
  * Workload shapes follow the paper's experiments (Sec. 5.1): tuples of a 64-bit
  * join key and a 64-bit payload; R with unique keys; S drawn from R's keys with
  * a multiplicity (foreign keys), optionally Zipf-skewed, or from a sparse,
- * clustered 64-bit domain with a share of keys that match nothing.
+ * clustered 64-bit domain with a share of keys that match nothing, or with the
+ * negatively correlated 80:20 skew of Sec. 5.6 (R's keys crowd the low fifth of
+ * the key domain, S's foreign keys the high fifth).
  *
  * Building blocks (all published, restated here):
  *  - splitmix64 finaliser (Steele, Lea, Flood 2014; Vigna's constants) as the
@@ -36,7 +38,7 @@
 
 typedef struct { uint64_t key, payload; } gen_tuple_t;
 
-enum { GEN_KIND_UNIFORM = 0, GEN_KIND_ZIPF = 1, GEN_KIND_SPARSE = 2 };
+enum { GEN_KIND_UNIFORM = 0, GEN_KIND_ZIPF = 1, GEN_KIND_SPARSE = 2, GEN_KIND_NEGCORR = 3 };
 
 /* Streams: each independent draw has its own stream id. */
 enum {
@@ -166,10 +168,31 @@ GEN_HD uint64_t gen_sparse_key(const gen_spec_t* s, uint64_t g) {
   return c.lo + 2ull * j + d0 + add;
 }
 
+/* --- negatively correlated 80:20 domain --------------------------------- */
+/* g-th smallest R key: the first 4/5 of R's keys are 1, 2, ... (dense), the rest
+ * follow 16 apart, so 80 % of R's keys sit in the low fifth of [1, max key]. */
+GEN_HD uint64_t gen_negcorr_key(uint64_t nR, uint64_t g) {
+  const uint64_t lo = nR / 5 * 4 + nR % 5 * 4 / 5;  /* floor(4 nR / 5) */
+  return g < lo ? 1ull + g : 1ull + lo + 16ull * (g - lo);
+}
+
+/* first g whose key lies in the top fifth of the domain (above 4/5 of the max key) */
+GEN_HD uint64_t gen_negcorr_hi(uint64_t nR) {
+  if (nR <= 1) return 0;
+  const uint64_t lo = nR / 5 * 4 + nR % 5 * 4 / 5;
+  const uint64_t top = gen_negcorr_key(nR, nR - 1);
+  const uint64_t cut = top / 5 * 4 + top % 5 * 4 / 5;
+  /* below lo, key 1 + cut is the first above the cut; from lo on, the smallest g
+   * with 1 + lo + 16 (g - lo) > cut, i.e. 16 (g - lo) >= cut - lo */
+  const uint64_t g = cut < lo ? cut : lo + (cut - lo) / 16 + ((cut - lo) % 16 ? 1u : 0u);
+  return g < nR ? g : nR - 1;
+}
+
 /* --- R ------------------------------------------------------------------- */
 GEN_HD uint64_t gen_r_key(const gen_spec_t* s, uint64_t row) {
   uint64_t p = gen_perm(row, s->nR, s->hR, gen_perm_key(s->seed, GEN_ST_RPERM));
   if (s->kind == GEN_KIND_SPARSE) return gen_sparse_key(s, p);
+  if (s->kind == GEN_KIND_NEGCORR) return gen_negcorr_key(s->nR, p);
   return 1ull + p;
 }
 
@@ -198,6 +221,16 @@ GEN_HD uint64_t gen_s_row(const gen_spec_t* s, uint64_t j) {
   if (s->kind == GEN_KIND_SPARSE) {
     uint64_t q = gen_perm(j, s->nS, s->hS, gen_perm_key(s->seed, GEN_ST_FK));
     if (q >= s->n_fk) return GEN_NONE;
+  }
+  if (s->kind == GEN_KIND_NEGCORR) {
+    /* 4 in 5 tuples take one of R's keys in the top fifth of the domain, the rest
+     * one of the keys below it; g is the key's rank among R's keys */
+    const uint64_t gh = gen_negcorr_hi(s->nR);
+    const uint64_t v = gen_rand(s->seed, GEN_ST_SROW2, j);
+    const uint64_t g = (gen_below(gen_rand(s->seed, GEN_ST_SROW, j), 5) != 0 || gh == 0)
+                           ? gh + gen_below(v, s->nR - gh)
+                           : gen_below(v, gh);
+    return gen_perm_inv(g, s->nR, s->hR, gen_perm_key(s->seed, GEN_ST_RPERM));
   }
   return gen_below(gen_rand(s->seed, GEN_ST_SROW, j), s->nR);
 }

@@ -55,7 +55,11 @@ enum {
   MPSM_ERR_STATE = 6          /* a phase entry point called before the phase it needs      */
 };
 
-enum { MPSM_SPLIT_HIST = 0, MPSM_SPLIT_LEARNED = 1 };
+/* Splitters of S (Sec. 4.3): HIST minimises the largest split-relevant cost
+ * |S_i| log|S_i| + T |S_i| + |R in range| over contiguous groups of the fine
+ * buckets; EQUI_HEIGHT groups the same buckets by |S_i| alone, the equi-height
+ * baseline of Sec. 5.6 (Fig. 16b); LEARNED takes sample quantiles (below). */
+enum { MPSM_SPLIT_HIST = 0, MPSM_SPLIT_LEARNED = 1, MPSM_SPLIT_EQUI_HEIGHT = 2 };
 enum { MPSM_SEARCH_BINARY = 0, MPSM_SEARCH_LEARNED = 1 };
 /* Role of the inputs (Sec. 3.2, Sec. 5.4 "role reversal"): which input is
  * range-partitioned; the other one is cut into sorted runs.  The result does not

@@ -38,6 +38,8 @@ def lib():
             "oracle_log2_q16": ([_u64], _u64),
             "oracle_splitters": ([_p, _p, _u32, _u32, _u32, _p, _p], _u32),
             "oracle_splitters_dp": ([_p, _p, _u32, _u32, _u32], _u64),
+            "oracle_splitters_kind": ([_p, _p, _u32, _u32, _u32, _u32, _p, _p], _u32),
+            "oracle_splitters_dp_kind": ([_p, _p, _u32, _u32, _u32, _u32], _u64),
             "oracle_prefix_sums": ([_p, _u32, _u32, _p, _p], ctypes.c_int),
             "oracle_scatter": ([_p, _p, _u32, _u64, _u64, _u32, _p, _u32, _p, _p], ctypes.c_int),
             "oracle_windows": ([_p, _p, _u64, _p, _p, _u32, _p], ctypes.c_int),
@@ -130,21 +132,23 @@ def log2_q16(n: int) -> int:
     return lib().oracle_log2_q16(n)
 
 
-def splitters(H, G, P: int, T: int):
-    """(sp, n_partitions, best_cost) of the cost-balanced contiguous grouping."""
+def splitters(H, G, P: int, T: int, kind: int = 0):
+    """(sp, n_partitions, best_cost) of the contiguous grouping minimising the largest
+    partition cost: kind 0 the split-relevant cost (Sec. 4.3), kind 1 equi-height
+    (the partitioned side's count alone, Sec. 5.6)."""
     H = np.ascontiguousarray(H, dtype=np.uint64)
     G = np.ascontiguousarray(G, dtype=np.uint64)
     sp = np.empty(len(H), dtype=np.uint32)
     best = _u64()
-    np_ = lib().oracle_splitters(H.ctypes.data, G.ctypes.data, len(H), P, T, sp.ctypes.data,
-                                 ctypes.byref(best))
+    np_ = lib().oracle_splitters_kind(H.ctypes.data, G.ctypes.data, len(H), P, T, kind, sp.ctypes.data,
+                                      ctypes.byref(best))
     return sp, np_, best.value
 
 
-def splitters_dp(H, G, P: int, T: int) -> int:
+def splitters_dp(H, G, P: int, T: int, kind: int = 0) -> int:
     H = np.ascontiguousarray(H, dtype=np.uint64)
     G = np.ascontiguousarray(G, dtype=np.uint64)
-    return lib().oracle_splitters_dp(H.ctypes.data, G.ctypes.data, len(H), P, T)
+    return lib().oracle_splitters_dp_kind(H.ctypes.data, G.ctypes.data, len(H), P, T, kind)
 
 
 def prefix_sums(h):

@@ -237,21 +237,22 @@ OEXPORT uint64_t oracle_log2_q16(uint64_t n) {
  * + T |S_i|           (process it once per run of the other side)
  * + |R in range|      (relevant data of the run side, the CDF difference)
  * with S the partitioned side and R the run side. */
-static uint64_t split_cost(uint64_t n, uint64_t r, uint32_t T) {
+static uint64_t split_cost(uint64_t n, uint64_t r, uint32_t T, uint32_t kind) {
+  if (kind == 1) return n << 16;  /* equi-height: the partition's share of the partitioned side only */
   return n * oracle_log2_q16(n) + (((uint64_t)T * n + r) << 16);
 }
 
 /* Greedy from the left: each partition takes buckets while its cost stays <= C.
  * Returns the number of partitions (UINT32_MAX if one bucket alone exceeds C);
  * fills sp[bucket] = partition when sp != NULL. */
-static uint32_t greedy(const uint64_t* H, const uint64_t* G, uint32_t nb, uint32_t T, uint64_t C,
+static uint32_t greedy(const uint64_t* H, const uint64_t* G, uint32_t nb, uint32_t T, uint32_t kind, uint64_t C,
                        uint32_t* sp) {
   uint32_t parts = 0, a = 0;
   while (a < nb) {
     uint64_t n = H[a], r = G[a];
-    if (split_cost(n, r, T) > C) return UINT32_MAX;
+    if (split_cost(n, r, T, kind) > C) return UINT32_MAX;
     uint32_t b = a + 1;
-    while (b < nb && split_cost(n + H[b], r + G[b], T) <= C) {
+    while (b < nb && split_cost(n + H[b], r + G[b], T, kind) <= C) {
       n += H[b];
       r += G[b];
       ++b;
@@ -270,28 +271,36 @@ static uint32_t greedy(const uint64_t* H, const uint64_t* G, uint32_t nb, uint32
  * optimum C* by bisection over integer costs (greedy feasibility is exact for
  * costs that grow with the range) and returns the leftmost greedy grouping at
  * C*.  sp[f] = partition of bucket f; returns the number of partitions used. */
-OEXPORT uint32_t oracle_splitters(const uint64_t* H, const uint64_t* G, uint32_t nb, uint32_t P,
-                                  uint32_t T, uint32_t* sp, uint64_t* best) {
+OEXPORT uint32_t oracle_splitters_kind(const uint64_t* H, const uint64_t* G, uint32_t nb, uint32_t P,
+                                       uint32_t T, uint32_t kind, uint32_t* sp, uint64_t* best) {
   uint64_t n = 0, r = 0, lo = 0;
   for (uint32_t f = 0; f < nb; ++f) {
     n += H[f];
     r += G[f];
-    lo = std::max(lo, split_cost(H[f], G[f], T));
+    lo = std::max(lo, split_cost(H[f], G[f], T, kind));
   }
-  uint64_t hi = split_cost(n, r, T);
+  uint64_t hi = split_cost(n, r, T, kind);
   /* smallest C in [lo, hi] with greedy(C) <= P; greedy(hi) == 1 <= P */
   while (lo < hi) {
     const uint64_t mid = lo + (hi - lo) / 2;
-    if (greedy(H, G, nb, T, mid, nullptr) <= P) hi = mid; else lo = mid + 1;
+    if (greedy(H, G, nb, T, kind, mid, nullptr) <= P) hi = mid; else lo = mid + 1;
   }
   *best = lo;
-  return greedy(H, G, nb, T, lo, sp);
+  return greedy(H, G, nb, T, kind, lo, sp);
+}
+
+/* kind 0: the split-relevant cost above; kind 1: equi-height partitions, i.e. the
+ * same contiguous grouping minimising the largest partition of the partitioned
+ * side alone (the baseline of Sec. 5.6, Fig. 16b). */
+OEXPORT uint32_t oracle_splitters(const uint64_t* H, const uint64_t* G, uint32_t nb, uint32_t P,
+                                  uint32_t T, uint32_t* sp, uint64_t* best) {
+  return oracle_splitters_kind(H, G, nb, P, T, 0, sp, best);
 }
 
 /* Exhaustive check of the same objective for small nb (DP over prefixes):
  * the smallest achievable largest cost with at most P contiguous groups. */
-OEXPORT uint64_t oracle_splitters_dp(const uint64_t* H, const uint64_t* G, uint32_t nb, uint32_t P,
-                                     uint32_t T) {
+OEXPORT uint64_t oracle_splitters_dp_kind(const uint64_t* H, const uint64_t* G, uint32_t nb, uint32_t P,
+                                          uint32_t T, uint32_t kind) {
   const uint64_t INF = ~0ull;
   std::vector<uint64_t> prev(nb + 1, INF), cur(nb + 1, INF);
   prev[0] = 0;
@@ -304,7 +313,7 @@ OEXPORT uint64_t oracle_splitters_dp(const uint64_t* H, const uint64_t* G, uint3
         n += H[a];
         r += G[a];
         if (prev[a] == INF) continue;
-        const uint64_t v = std::max(prev[a], split_cost(n, r, T));
+        const uint64_t v = std::max(prev[a], split_cost(n, r, T, kind));
         cur[b] = std::min(cur[b], v);
       }
     }
@@ -312,6 +321,11 @@ OEXPORT uint64_t oracle_splitters_dp(const uint64_t* H, const uint64_t* G, uint3
     prev.swap(cur);
   }
   return bestv;
+}
+
+OEXPORT uint64_t oracle_splitters_dp(const uint64_t* H, const uint64_t* G, uint32_t nb, uint32_t P,
+                                     uint32_t T) {
+  return oracle_splitters_dp_kind(H, G, nb, P, T, 0);
 }
 
 /* Prefix sums (Sec. 3.2.1, the ps equation under Fig. 6): ps_i[j] = sum of

@@ -464,6 +464,8 @@ int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
 }
 
 // radix passes over the big-segment list until every segment is final
+// keep_const: constant-key children stay where they are (the fused join reads them
+// in place) and the buckets aim at the fused kernel's tile
 int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels, bool keep_const = false) {
   u32 cur = 0, src = first_src;
   u32 done = 0;
@@ -478,7 +480,8 @@ int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels, bool k
     u64* tot = p->d_tot + T_LEVEL;
     const u32 rb = p->opt.radix_bits ? p->opt.radix_bits : 11u;
     LAUNCH(K_PLAN, launch_level_plan(p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->big_cap, p->d_ls, tot, MODE_RADIX, CH_RADIX, rb,
-                      p->d_jobs, p->hist_a_cap, p->bucket_cap, &p->d_cnt[C_ERR], p->st));
+                      p->d_jobs, p->hist_a_cap, p->bucket_cap, &p->d_cnt[C_ERR], p->st,
+                      keep_const ? FILL_FUSED : 0));
     LAUNCH(K_INIT, launch_init_buckets(p->d_bmin, p->d_bmax, nullptr, tot, p->st, p->nsm));
     LAUNCH(K_HIST_RADIX, launch_hist(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs, src,
                 p->d_hist_a, p->d_bmin, p->d_bmax, nullptr, lctx(p, false), p->st, p->nsm));
@@ -601,7 +604,8 @@ int phase_splitters(mpsm_plan* p) {
   LAUNCH(K_HIST_FINE, launch_hist(MODE_FINE, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls, tf, p->ch_s, bufs(p), p->d_jobs, W_SIN,
               p->d_hist_b, p->d_fine_min, p->d_fine_max, p->d_fine_s, lctx(p, false), p->st, p->nsm));
   LAUNCH(K_RUN_CDF, launch_run_cdf(p->d_jobs, nj, p->d_runs, p->xr, p->d_rc, p->st));
-  LAUNCH(K_SPLITTERS, launch_splitters(p->d_jobs, nj, p->d_fine_s, p->d_rc, p->d_fine_r, p->d_sp, p->d_fstart, &p->d_cnt[C_ERR], p->st));
+  LAUNCH(K_SPLITTERS, launch_splitters(p->d_jobs, nj, p->d_fine_s, p->d_rc, p->d_fine_r, p->d_sp, p->d_fstart, &p->d_cnt[C_ERR], p->st,
+                                       p->opt.splitter_mode == MPSM_SPLIT_EQUI_HEIGHT));
   LAUNCH(K_PLAN, launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls2, ts, MODE_SPLIT, p->ch_s, 11, p->d_jobs,
                     p->hist_a_cap, ~0ull, &p->d_cnt[C_ERR], p->st));
   LAUNCH(K_FOLD, launch_fold(p->d_split, &p->d_cnt[C_SPLIT], p->d_ls, p->d_ls2, tf, p->d_jobs, p->d_hist_b, p->d_fstart,
@@ -836,7 +840,9 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   if (o.fine_bits > 12 || (o.radix_bits && (o.radix_bits < 4 || o.radix_bits > 11))) return MPSM_ERR_INVALID_ARG;
   if (o.partitions_s > P_MAX || o.runs_r > RUNS_MAX || o.learn_steps > 100000) return MPSM_ERR_INVALID_ARG;
   if (o.join_tile && (o.join_tile < 256 || o.join_tile > TILE_MAX || o.join_tile % 256)) return MPSM_ERR_INVALID_ARG;
-  if (o.splitter_mode != MPSM_SPLIT_HIST && o.splitter_mode != MPSM_SPLIT_LEARNED) return MPSM_ERR_INVALID_ARG;
+  if (o.splitter_mode != MPSM_SPLIT_HIST && o.splitter_mode != MPSM_SPLIT_LEARNED &&
+      o.splitter_mode != MPSM_SPLIT_EQUI_HEIGHT)
+    return MPSM_ERR_INVALID_ARG;
   if (o.search_mode != MPSM_SEARCH_BINARY && o.search_mode != MPSM_SEARCH_LEARNED) return MPSM_ERR_INVALID_ARG;
   mpsm_plan* p = new (std::nothrow) mpsm_plan();
   if (!p) return MPSM_ERR_OOM;

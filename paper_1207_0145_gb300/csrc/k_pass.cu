@@ -12,8 +12,9 @@
 //                  and the children segments for the next pass
 //   k_scatter    : per chunk, every tuple copied to ps_i[bucket]++ (Sec. 4.3) --
 //                  synchronisation-free, since each chunk owns its ranges
-// The same kernels run three bucket functions: MODE_RADIX (top bits of
-// key - segment min, the sort passes of phases 1 and 3), MODE_FINE (the fine
+// The same kernels run three bucket functions: MODE_RADIX (top bits of key -
+// segment min, or F equal-width key ranges before the fused sort-and-join; the sort
+// passes of phases 1 and 3), MODE_FINE (the fine
 // B-bit histogram of S over R's key range, Sec. 4.2) and MODE_SPLIT (fine bucket
 // -> partition through the splitter vector sp, Sec. 4.3).
 // Segments that fit NMAX tuples are finished by k_seg_sort: one block loads the
@@ -40,6 +41,27 @@ constexpr u32 RX_TILE = 8192, RX_NT = 1024, RX_MINB = 1;
 constexpr u32 SP_TILE = 4096, SP_NT = 512, SP_MINB = 2;
 constexpr u32 NT_SORT = 512;
 constexpr u32 NW_SORT = NT_SORT / 32;
+
+// floor(a * 2^64 / d) for a < d, by binary long division (the remainder stays below d)
+__device__ __forceinline__ u64 frac64(u64 a, u64 d) {
+  u64 rem = a, q = 0;
+  for (int i = 0; i < 64; ++i) {
+    const bool carry = (rem >> 63) != 0;  // 2 rem >= 2^64 > d
+    rem <<= 1;
+    q <<= 1;
+    if (carry || rem >= d) {
+      rem -= d;
+      q |= 1ull;
+    }
+  }
+  return q;
+}
+
+// MODE_RADIX bucket of a key before the clamp to F - 1 (see k_level_plan)
+__device__ __forceinline__ u64 radix_bucket(const LSeg& L, u64 key) {
+  const u64 d = key < L.lo ? 0ull : key - L.lo;
+  return L.mul ? __umul64hi(d, L.mul) : d >> L.shift;
+}
 
 __device__ __forceinline__ u64 ld_key_stream(const Tuple* p) {
   return (u64)__ldcs(reinterpret_cast<const long long*>(&p->key));
@@ -81,8 +103,10 @@ __global__ void k_sample_bounds(Seg* segs, const u32* nseg_ptr, Bufs bufs, const
       mn = a < mn ? a : mn;
       mx = b > mx ? b : mx;
     }
-    // a sample misses the extremes by about range/1024: widen so the edge buckets stay small
-    const u64 pad = (mx - mn) >> 8;
+    // 1024 evenly spaced samples of uniform keys miss an extreme by more than range/64
+    // with probability about e^-16; widen by that much so the edge buckets, which take
+    // every key beyond the bounds, stay as small as the others
+    const u64 pad = (mx - mn) >> 6;
     mn = mn > pad ? mn - pad : 0ull;
     mx = (~0ull - mx) > pad ? mx + pad : ~0ull;
     if (lane == 0) {
@@ -94,7 +118,7 @@ __global__ void k_sample_bounds(Seg* segs, const u32* nseg_ptr, Bufs bufs, const
 
 // ---------------------------------------------------------------- level plan
 __global__ void __launch_bounds__(1024) k_level_plan(const Seg* segs, u32* nseg_ptr, u32 seg_cap, LSeg* ls,
-                                                     u64* totals, u32 mode, u64 chunk, u32 radix_bits,
+                                                     u64* totals, u32 mode, u64 chunk, u32 radix_bits, u64 fill,
                                                      const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err) {
   __shared__ u64 s_warp[33];
   __shared__ u64 carry[3];
@@ -116,19 +140,34 @@ __global__ void __launch_bounds__(1024) k_level_plan(const Seg* segs, u32* nseg_
       u32 F, shift;
       u64 lo;
       if (mode == MODE_RADIX) {
-        const u64 want = (s.len + N_LEAF - 1) / N_LEAF;
-        u32 f = F_MIN;
-        while (f < want && f < fmax) f <<= 1;
-        const u32 d = 31u - (u32)__clz(f);
         const u64 range = s.kmax - s.kmin;
-        const u32 bits = bitlen64(range);
-        shift = bits > d ? bits - d : 0u;
-        F = (u32)(range >> shift) + 1u;
+        shift = 0;
+        if (fill) {
+          // F buckets of equal key width over [kmin, kmax], F chosen so that a bucket of
+          // uniform keys holds `fill` tuples and its child fits the fused kernel's tile
+          // in one piece.  bucket = floor((key - kmin) * F / (range + 1)), computed as the
+          // high word of (key - kmin) * mul, mul = floor(2^64 F / (range + 1)), which stays
+          // below F and is monotone in the key.
+          const u64 want = (s.len + fill - 1) / fill;
+          F = want < F_MIN ? F_MIN : (want > fmax ? fmax : (u32)want);
+          if (range >= (u64)F) L.mul = range == ~0ull ? (u64)F : frac64(F, range + 1u);
+        } else {
+          // top bits of key - kmin: the smallest power of two >= len / N_LEAF buckets
+          // (at most fmax), of which the key range may fill only a part
+          const u64 want = (s.len + N_LEAF - 1) / N_LEAF;
+          u32 f = F_MIN;
+          while (f < want && f < fmax) f <<= 1;
+          const u32 d = 31u - (u32)__clz(f);
+          const u32 bits = bitlen64(range);
+          shift = bits > d ? bits - d : 0u;
+          F = (u32)(range >> shift) + 1u;
+        }
         // few distinct key values in many tuples (a hot key among few others): one
         // bucket per value, so every child is constant or small after this pass; at
         // most one bucket per 64 tuples keeps the histogram and bucket arrays in bounds
-        if (range < (u64)fmax && F < range + 1u && range + 1u <= s.len / 64u) {
+        if (range < (u64)F || (range < (u64)fmax && range + 1u <= s.len / 64u)) {
           shift = 0;
+          L.mul = 0;
           F = (u32)range + 1u;
         }
         lo = s.kmin;
@@ -242,7 +281,7 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
         if (t >= e) continue;
         u32 b;
         if (MODE == MODE_RADIX) {
-          const u64 d = k[i] < L.lo ? 0ull : (k[i] - L.lo) >> L.shift;
+          const u64 d = radix_bucket(L, k[i]);
           b = d >= F ? F - 1u : (u32)d;
         } else if (MODE == MODE_LEARN) {
           if (k[i] < kmin || k[i] > kmax) continue;
@@ -465,7 +504,7 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
         const u64 key = T[x].key;
         u32 b;
         if (MODE == MODE_RADIX) {
-          const u64 d = key < L.lo ? 0ull : (key - L.lo) >> L.shift;
+          const u64 d = radix_bucket(L, key);
           b = d >= F ? F - 1u : (u32)d;
         } else if (MODE == MODE_LEARN) {
           if (key < kmin || key > kmax) continue;
@@ -1065,8 +1104,9 @@ void launch_sample_bounds(Seg* segs, const u32* nseg, u32 max_segs, Bufs bufs, c
 }
 
 void launch_level_plan(const Seg* segs, u32* nseg, u32 seg_cap, LSeg* ls, u64* totals, u32 mode, u64 chunk,
-                       u32 radix_bits, const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err, cudaStream_t st) {
-  k_level_plan<<<1, 1024, 0, st>>>(segs, nseg, seg_cap, ls, totals, mode, chunk, radix_bits, jobs, hist_cap,
+                       u32 radix_bits, const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err, cudaStream_t st,
+                       u64 fill) {
+  k_level_plan<<<1, 1024, 0, st>>>(segs, nseg, seg_cap, ls, totals, mode, chunk, radix_bits, fill, jobs, hist_cap,
                                    bucket_cap, err);
 }
 

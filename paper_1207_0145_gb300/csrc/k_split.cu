@@ -12,6 +12,7 @@
 // The cost of a partition holding n tuples of S and r tuples of R, in units of
 // 2^-16 tuples, is n*log2(n) + T*n + r with log2 in Q16 fixed point (integer
 // arithmetic only, so the choice of splitters is reproducible bit for bit).
+// The equi-height baseline of Sec. 5.6 (Fig. 16b) uses the cost n alone.
 // The paper leaves the optimiser open; this one bisects the integer bound C and
 // tests feasibility with the left-to-right greedy grouping, whose group count
 // after P greedy jumps is found by repeated squaring of the jump function.
@@ -60,9 +61,16 @@ __device__ __forceinline__ u64 log2_q16(u64 n, const u32* frac) {
   return ((u64)k << 16) + frac[m - 1024u];
 }
 
-__device__ __forceinline__ u64 part_cost(const u64* PH, const u64* PG, u32 a, u32 b, u32 T, const u32* frac) {
-  const u64 n = PH[b] - PH[a], r = PG[b] - PG[a];
+// split-relevant cost of n partitioned-side and r run-side tuples; with `height`
+// set, the partitioned side's count alone (equi-height partitions, Sec. 5.6)
+__device__ __forceinline__ u64 split_cost(u64 n, u64 r, u32 T, const u32* frac, bool height) {
+  if (height) return n << 16;
   return n * log2_q16(n, frac) + (((u64)T * n + r) << 16);
+}
+
+__device__ __forceinline__ u64 part_cost(const u64* PH, const u64* PG, u32 a, u32 b, u32 T, const u32* frac,
+                                         bool height) {
+  return split_cost(PH[b] - PH[a], PG[b] - PG[a], T, frac, height);
 }
 
 __global__ void k_run_bounds(Job* jobs, u32 njobs, const Run* runs, const Tuple* xr) {
@@ -133,7 +141,7 @@ __global__ void k_run_cdf(const Job* jobs, u32 njobs, const Run* runs, const Tup
 }
 
 __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s, const u64* rc, u64* fine_r, u32* sp,
-                                                    u32* part_fstart, u32* err) {
+                                                    u32* part_fstart, u32* err, bool height) {
   constexpr u32 NT = 1024;
   // dynamic shared memory: PH, PG (u64, FINE_MAX + 1 each), frac (u32, 1024), A, B (u16, FINE_MAX + 8 each)
   extern __shared__ __align__(128) unsigned char sm_raw[];
@@ -179,8 +187,7 @@ __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s
   // costs spread over P partitions (merging buckets never lowers the cost)
   u64 mx = 0, sm = 0;
   for (u32 f = tid; f < nb; f += NT) {
-    const u64 n = PH[f], r = PG[f];
-    const u64 c = n * log2_q16(n, frac) + (((u64)T * n + r) << 16);
+    const u64 c = split_cost(PH[f], PG[f], T, frac, height);
     mx = c > mx ? c : mx;
     sm += c;
   }
@@ -210,7 +217,7 @@ __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s
   if (tid == 0) {
     PH[nb] = totH;
     PG[nb] = totG;
-    const u64 h = totH * log2_q16(totH, frac) + (((u64)T * totH + totG) << 16);
+    const u64 h = split_cost(totH, totG, T, frac, height);
     s_hi = h > s_lo ? h : s_lo;
   }
   __syncthreads();
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s
       u32 l = a + 1, h = nb;
       while (l < h) {
         const u32 m = (l + h + 1) >> 1;
-        if (part_cost(PH, PG, a, m, T, frac) <= C) l = m; else h = m - 1;
+        if (part_cost(PH, PG, a, m, T, frac, height) <= C) l = m; else h = m - 1;
       }
       A[a] = (u16)l;
     }
@@ -325,8 +332,8 @@ void launch_run_cdf(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr
 }
 
 void launch_splitters(Job* jobs, u32 njobs, const u64* fine_s, const u64* rc, u64* fine_r, u32* sp,
-                      u32* part_fstart, u32* err, cudaStream_t st) {
-  k_splitters<<<njobs, 1024, SMEM_SPLITTERS, st>>>(jobs, fine_s, rc, fine_r, sp, part_fstart, err);
+                      u32* part_fstart, u32* err, cudaStream_t st, bool equi_height) {
+  k_splitters<<<njobs, 1024, SMEM_SPLITTERS, st>>>(jobs, fine_s, rc, fine_r, sp, part_fstart, err, equi_height);
 }
 
 void launch_fold(const Seg* segs, const u32* nseg, const LSeg* ls_fine, const LSeg* ls_split, const u64* totals,

@@ -26,6 +26,10 @@ struct __align__(16) Tuple {
 // ---------------------------------------------------------------- constants
 constexpr u32 NMAX = 8192;        // tuples one block sorts in shared memory (128 KB)
 constexpr u32 N_LEAF = 4096;      // target segment size after a radix pass
+// tuples per bucket that the radix passes before the fused sort-and-join aim for:
+// 7/8 of its N_LEAF-tuple tile, so the spread of uniform keys (about sqrt(3584) =
+// 60) stays far below the tile and a segment is joined in one piece
+constexpr u64 FILL_FUSED = N_LEAF - N_LEAF / 16;
 constexpr u32 F_MIN = 16;         // smallest radix fan-out (guarantees 4 bits/pass progress)
 constexpr u32 F_MAX = 2048;       // largest radix fan-out (radix_bits <= 11)
 constexpr u32 FINE_MAX = 4096;    // largest fine histogram (fine_bits <= 12)
@@ -93,8 +97,9 @@ struct LSeg {
   u64 chunk_base;           // first global chunk of the segment
   u64 hist_base;            // first histogram entry (chunks x F, chunk-major)
   u64 bucket_base;          // first bucket-bound entry (F)
-  u32 shift, F;             // bucket = min(F-1, (key - lo) >> shift)
+  u32 shift, F;             // bucket = min(F-1, (key - lo) >> shift), or with mul set:
   u32 nchunks, pad;
+  u64 mul;                  // bucket = min(F-1, mulhi(key - lo, mul)) (MODE_RADIX)
 };
 
 // Phases 3 and 4 fused: the final sort of each S segment joins it, still in

@@ -17,7 +17,8 @@ void init_attrs_learn();
 // ---- partitioning passes (k_pass.cu)
 void launch_sample_bounds(Seg* segs, const u32* nseg, u32 max_segs, Bufs bufs, const Job* jobs, cudaStream_t st);
 void launch_level_plan(const Seg* segs, u32* nseg, u32 seg_cap, LSeg* ls, u64* totals, u32 mode, u64 chunk,
-                       u32 radix_bits, const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err, cudaStream_t st);
+                       u32 radix_bits, const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err, cudaStream_t st,
+                       u64 fill = 0);  // MODE_RADIX: target tuples per bucket, 0 = power-of-two buckets
 void launch_init_buckets(u64* bmin, u64* bmax, u64* btot, const u64* totals, cudaStream_t st, int nsm);
 void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                  Bufs bufs, const Job* jobs, u32 src_where, u32* hist, u64* bmin, u64* bmax, u64* btot,
@@ -43,7 +44,7 @@ void launch_seg_sort_join(const Seg* segs, const u32* nseg, u32 cap, u32* work, 
 void launch_run_bounds(Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, cudaStream_t st);
 void launch_run_cdf(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, u64* rc, cudaStream_t st);
 void launch_splitters(Job* jobs, u32 njobs, const u64* fine_s, const u64* rc, u64* fine_r, u32* sp,
-                      u32* part_fstart, u32* err, cudaStream_t st);
+                      u32* part_fstart, u32* err, cudaStream_t st, bool equi_height = false);
 void launch_fold(const Seg* segs, const u32* nseg, const LSeg* ls_fine, const LSeg* ls_split, const u64* totals,
                  const Job* jobs, const u32* hist_fine, const u32* part_fstart, u32* hist_split, cudaStream_t st,
                  int nsm);

@@ -63,6 +63,27 @@ def test_sparse_workload_structure():
     assert len(np.unique(keys >> np.uint64(58))) >= 32
 
 
+def test_negcorr_workload_skew():
+    # Sec. 5.6: 80 % of R's keys in the low fifth of the domain, 80 % of S's in the high fifth
+    w = gen.negcorr(100_000, 400_000, seed=5)
+    R, S = w.r_host(), w.s_host()
+    keys = np.sort(R[:, 0])
+    lo = 4 * 100_000 // 5
+    assert keys[:lo].tolist() == list(range(1, lo + 1))
+    assert (np.diff(keys[lo:]) == 16).all()
+    top = int(keys[-1])
+    assert abs(np.mean(R[:, 0] <= top // 5) - 0.8) < 1e-3
+    assert abs(np.mean(S[:, 0] > top * 4 // 5) - 0.8) < 0.01
+    rows = w.s_rows_host().astype(np.int64)
+    assert (S[:, 0] == R[rows, 0]).all()  # foreign keys
+    # R's keys in random order (not sorted by row)
+    assert (np.diff(R[:, 0].astype(np.int64)) < 0).any()
+    for n in (1, 2, 3, 7):
+        t = gen.negcorr(n, 50, seed=9)
+        r, s2 = t.r_host(), t.s_host()
+        assert np.isin(s2[:, 0], r[:, 0]).all()
+
+
 def test_batch_jobs_shape():
     jobs = gen.batch_jobs(256)
     nr = np.array([j.n_r for j in jobs])

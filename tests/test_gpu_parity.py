@@ -152,12 +152,15 @@ def phase2_oracle(R, S, v, T):
     return Rs, run_off, kmin, kmax
 
 
-@pytest.mark.parametrize("fine_bits,parts", [(12, 0), (6, 9), (2, 2)])
-def test_phase2_histograms_splitters_prefix_sums(fine_bits, parts):
-    w = gen.zipf(60_000, 500_000, 0.9, seed=13)
+@pytest.mark.parametrize("fine_bits,parts,kind", [(12, 0, 0), (6, 9, 0), (2, 2, 0), (10, 0, 1), (12, 0, 1),
+                                                  (10, 0, 0)])
+def test_phase2_histograms_splitters_prefix_sums(fine_bits, parts, kind):
+    # kind 1: equi-height splitters (Sec. 5.6) on the negatively correlated workload
+    w = gen.zipf(60_000, 500_000, 0.9, seed=13) if (kind == 0 and fine_bits != 10) else gen.negcorr(60_000, 240_000, seed=17)
     R, S = w.r_host(), w.s_host()
     T = 8
-    p, dR, dS = run_phases(R, S, runs_r=T, fine_bits=fine_bits, partitions_s=parts)
+    mode = M.SPLIT_EQUI_HEIGHT if kind else M.SPLIT_HIST
+    p, dR, dS = run_phases(R, S, runs_r=T, fine_bits=fine_bits, partitions_s=parts, splitter_mode=mode)
     p.sort_runs(dR)
     p.splitters(dS)
     v = p.view()
@@ -173,7 +176,7 @@ def test_phase2_histograms_splitters_prefix_sums(fine_bits, parts):
     G = oracle.run_counts(Rs, run_off, kmin, kmax, shift, nb)
     assert (from_dev_ptr(v.fine_r, nb, width=1) == G).all()
     P_req = parts or 32
-    sp, nparts, _ = oracle.splitters(H, G, min(P_req, nb), T)
+    sp, nparts, _ = oracle.splitters(H, G, min(P_req, nb), T, kind=kind)
     assert v.partitions_s == nparts
     assert (from_dev_ptr(v.splitters, nb, width=1, dtype=np.uint32) == sp).all()
     # per-worker partition histograms and prefix sums (the ps equation under Fig. 6)
@@ -227,6 +230,20 @@ def test_phase3_sorted_partitions_and_phase4(w):
     assert (got_win.astype(np.uint64) == want_win).all()
     assert p.merge_join() == oracle.join(R, S)
     p.close()
+
+
+@pytest.mark.parametrize("mode", [M.SPLIT_HIST, M.SPLIT_EQUI_HEIGHT, M.SPLIT_LEARNED])
+def test_negatively_correlated_join_every_splitter_mode(mode):
+    # Sec. 5.6 workload: the splitters change the partitions, never the result
+    w = gen.negcorr(150_000, 600_000, seed=23)
+    R, S = w.r_host(), w.s_host()
+    want = oracle.join(R, S)
+    assert want == oracle.closed_form(w)
+    for side in (M.PART_S, M.PART_R):
+        with Plan(w.n_r, w.n_s, splitter_mode=mode, fine_bits=10, partition_side=side) as p:
+            assert p.join(to_dev(R), to_dev(S)) == want
+            if mode == M.SPLIT_EQUI_HEIGHT and side == M.PART_S:
+                assert p.stats()["imbalance"] < 1.5  # equal sizes up to the fine-bucket granularity
 
 
 # ------------------------------------------------------------------ pairs

@@ -242,6 +242,49 @@ def test_splitters_optimal_against_exhaustive_dp():
         assert int(sp[-1]) == nparts - 1
 
 
+def test_equi_height_splitters_against_exhaustive_dp_and_closed_forms():
+    # kind 1 groups the buckets by the partitioned side's count alone (Sec. 5.6)
+    rng = np.random.default_rng(22)
+    for _ in range(300):
+        nb = int(rng.integers(1, 11))
+        P = int(rng.integers(1, 5))
+        H = rng.integers(0, 2000, nb, dtype=np.uint64)
+        G = rng.integers(0, 500, nb, dtype=np.uint64)
+        sp, nparts, best = oracle.splitters(H, G, P, 7, kind=1)
+        assert best == oracle.splitters_dp(H, G, P, 7, kind=1)
+        sizes = np.bincount(sp, weights=H.astype(np.float64), minlength=nparts)
+        assert int(sizes.max()) << 16 == best
+        # the run side does not change the grouping
+        assert (oracle.splitters(H, G[::-1].copy(), P, 7, kind=1)[0] == sp).all()
+    # equal buckets split evenly: 12 buckets of 5 into 4 partitions of 3 buckets (15 tuples)
+    sp, nparts, best = oracle.splitters(np.full(12, 5, dtype=np.uint64), np.zeros(12, dtype=np.uint64), 4, 3, kind=1)
+    assert sp.tolist() == [0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3] and best == 15 << 16
+    # ten unit buckets into three partitions: the largest holds ceil(10 / 3) = 4, leftmost greedy 4 + 4 + 2
+    sp, nparts, best = oracle.splitters(np.ones(10, dtype=np.uint64), np.zeros(10, dtype=np.uint64), 3, 1, kind=1)
+    assert best == 4 << 16 and sp.tolist() == [0, 0, 0, 0, 1, 1, 1, 1, 2, 2]
+
+
+def test_equi_cost_differs_from_equi_height_under_negative_correlation():
+    # Fig. 16a: the partitioned side dense at the high end, the run side dense at
+    # the low end.  Equi-height gives the low partitions the wide key ranges (and so
+    # most of the run side); equi-cost weighs the run side in, so its largest cost
+    # is lower.
+    nb, P, T = 64, 8, 32
+    H = np.array([1] * 48 + [16] * 16, dtype=np.uint64) * 1000
+    G = np.array([16] * 16 + [1] * 48, dtype=np.uint64) * 1000
+    sp_h, _, _ = oracle.splitters(H, G, P, T, kind=1)
+    sp_c, _, best_c = oracle.splitters(H, G, P, T, kind=0)
+    def largest_cost(sp):
+        worst = 0
+        for g in range(int(sp.max()) + 1):
+            n, r = int(H[sp == g].sum()), int(G[sp == g].sum())
+            worst = max(worst, n * oracle.log2_q16(n) + ((T * n + r) << 16))
+        return worst
+    assert largest_cost(sp_c) == best_c
+    assert largest_cost(sp_h) > best_c
+    assert (sp_c != sp_h).any()
+
+
 # ------------------------------------------------------------------ phase 4: windows
 
 
