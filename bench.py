@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=16, help="CPU baseline runs 1/this of the workload")
     ap.add_argument("--splitter", default="hist", choices=["hist", "learned", "equi-height"])
     ap.add_argument("--fine-bits", type=int, default=0, help="B, fine histogram bits of S (0 = 12)")
-    ap.add_argument("--search", default="binary", choices=["binary", "learned"])
+    ap.add_argument("--search", default="binary", choices=["binary", "learned", "interp"])
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
     ap.add_argument("--pairs", action="store_true", help="materialise the matching pairs (|S| x 16 B buffer)")
     ap.add_argument("--side", default="s", choices=["s", "r", "smaller"], help="input that is range-partitioned")
@@ -76,6 +76,7 @@ def parse():
 
 
 SPLITTER_MODES = {"hist": 0, "learned": 1, "equi-height": 2}
+SEARCH_MODES = {"binary": 0, "learned": 1, "interp": 2}
 
 
 def _device_array(ptr: int, n: int, dtype):
@@ -323,7 +324,7 @@ def run_ours(args):
     stream.synchronize()
     plan = Plan(w.n_r, w.n_s, stream=stream.cuda_stream, runs_r=args.runs, partitions_s=args.parts,
                 partition_side={"s": 0, "r": 1, "smaller": 2}[args.side],
-                splitter_mode=SPLITTER_MODES[args.splitter], search_mode=int(args.search == "learned"),
+                splitter_mode=SPLITTER_MODES[args.splitter], search_mode=SEARCH_MODES[args.search],
                 fine_bits=args.fine_bits)
 
     # the run side and the partitioned side (swapped under role reversal)

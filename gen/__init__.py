@@ -25,7 +25,7 @@ import numpy as np
 M = 1 << 20
 DEFAULT_SEED = 20120145
 
-KIND_UNIFORM, KIND_ZIPF, KIND_SPARSE, KIND_NEGCORR = 0, 1, 2, 3
+KIND_UNIFORM, KIND_ZIPF, KIND_SPARSE, KIND_NEGCORR, KIND_LOCSKEW = 0, 1, 2, 3, 4
 GEN_NONE = (1 << 64) - 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -185,7 +185,8 @@ class Workload:
     kind = KIND_UNIFORM: R keys are a random permutation of 1..nR; S keys are
     uniform foreign keys into R.  KIND_NEGCORR: R's keys are 1..4nR/5 and then every
     16th key (80 % in the low fifth of the domain), in random order; 80 % of S's
-    foreign keys fall in the high fifth.  KIND_ZIPF: S rows follow Zipf(theta) over R's
+    foreign keys fall in the high fifth.  KIND_LOCSKEW: R's keys are 1..nR stored in
+    64 row clusters of ascending key ranges, shuffled inside each cluster.  KIND_ZIPF: S rows follow Zipf(theta) over R's
     rows, hot rows at random positions.  KIND_SPARSE: R keys from the clustered
     64-bit domain; round(fk_share * nS) S tuples are foreign keys, the rest fall
     strictly inside gaps between R keys and match nothing.
@@ -292,6 +293,12 @@ def sparse(n_r: int, n_s: int, fk_share: float = 0.7, seed: int = DEFAULT_SEED) 
     return Workload(KIND_SPARSE, n_r, n_s, seed, fk_share=fk_share)
 
 
+def locskew(n_r: int, n_s: int, seed: int = DEFAULT_SEED) -> Workload:
+    """Location skew (Sec. 5.5): R stored in 64 row clusters of ascending key ranges,
+    each cluster's keys in random order; S uniform foreign keys."""
+    return Workload(KIND_LOCSKEW, n_r, n_s, seed)
+
+
 def negcorr(n_r: int, n_s: int, seed: int = DEFAULT_SEED) -> Workload:
     """Negatively correlated 80:20 skew (Sec. 5.6): 80 % of R's unique keys in the low
     fifth of the key domain, 80 % of S's foreign keys in the high fifth."""
@@ -330,4 +337,6 @@ CONFIGS = {
     "sparse-1600M-1600M": lambda seed=DEFAULT_SEED: sparse(1600 * M, 1600 * M, 0.7, seed),
     # Sec. 5.6 (multiplicity 4, at a quarter of the paper's 1600M x 6400M)
     "negcorr-400M-1600M": lambda seed=DEFAULT_SEED: negcorr(400 * M, 1600 * M, seed),
+    # Sec. 5.5, location skew of the run side (multiplicity 4)
+    "locskew-400M-1600M": lambda seed=DEFAULT_SEED: locskew(400 * M, 1600 * M, seed),
 }

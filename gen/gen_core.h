@@ -13,7 +13,8 @@
  * a multiplicity (foreign keys), optionally Zipf-skewed, or from a sparse,
  * clustered 64-bit domain with a share of keys that match nothing, or with the
  * negatively correlated 80:20 skew of Sec. 5.6 (R's keys crowd the low fifth of
- * the key domain, S's foreign keys the high fifth).
+ * the key domain, S's foreign keys the high fifth), or with the location skew of
+ * Sec. 5.5 (R stored in small-to-large key order by clusters, each shuffled).
  *
  * Building blocks (all published, restated here):
  *  - splitmix64 finaliser (Steele, Lea, Flood 2014; Vigna's constants) as the
@@ -38,7 +39,7 @@
 
 typedef struct { uint64_t key, payload; } gen_tuple_t;
 
-enum { GEN_KIND_UNIFORM = 0, GEN_KIND_ZIPF = 1, GEN_KIND_SPARSE = 2, GEN_KIND_NEGCORR = 3 };
+enum { GEN_KIND_UNIFORM = 0, GEN_KIND_ZIPF = 1, GEN_KIND_SPARSE = 2, GEN_KIND_NEGCORR = 3, GEN_KIND_LOCSKEW = 4 };
 
 /* Streams: each independent draw has its own stream id. */
 enum {
@@ -188,8 +189,28 @@ GEN_HD uint64_t gen_negcorr_hi(uint64_t nR) {
   return g < nR ? g : nR - 1;
 }
 
+/* --- location skew: R in GEN_LOC_CLUSTERS clusters of rows ----------------- */
+/* Cluster c holds rows [b_c, b_{c+1}), b_c = floor(nR c / C), and exactly the keys
+ * 1 + b_c .. b_{c+1} in a random order of its own: small to large key order across
+ * clusters, no order inside one. */
+#define GEN_LOC_CLUSTERS 64ull
+
+GEN_HD uint64_t gen_loc_bound(uint64_t nR, uint64_t c) {
+  return (uint64_t)(((unsigned __int128)nR * c) / GEN_LOC_CLUSTERS);
+}
+
+GEN_HD uint64_t gen_loc_key(const gen_spec_t* s, uint64_t row) {
+  uint64_t c = (uint64_t)(((unsigned __int128)row * GEN_LOC_CLUSTERS) / s->nR);
+  while (c + 1 < GEN_LOC_CLUSTERS && gen_loc_bound(s->nR, c + 1) <= row) ++c;
+  while (c > 0 && gen_loc_bound(s->nR, c) > row) --c;
+  const uint64_t b0 = gen_loc_bound(s->nR, c), nc = gen_loc_bound(s->nR, c + 1) - b0;
+  const uint64_t key = gen_perm_key(s->seed ^ ((c + 1ull) * 0xC2B2AE3D27D4EB4Full), GEN_ST_RPERM);
+  return 1ull + b0 + gen_perm(row - b0, nc, gen_half_bits(nc), key);
+}
+
 /* --- R ------------------------------------------------------------------- */
 GEN_HD uint64_t gen_r_key(const gen_spec_t* s, uint64_t row) {
+  if (s->kind == GEN_KIND_LOCSKEW) return gen_loc_key(s, row);
   uint64_t p = gen_perm(row, s->nR, s->hR, gen_perm_key(s->seed, GEN_ST_RPERM));
   if (s->kind == GEN_KIND_SPARSE) return gen_sparse_key(s, p);
   if (s->kind == GEN_KIND_NEGCORR) return gen_negcorr_key(s->nR, p);

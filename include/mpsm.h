@@ -60,7 +60,12 @@ enum {
  * buckets; EQUI_HEIGHT groups the same buckets by |S_i| alone, the equi-height
  * baseline of Sec. 5.6 (Fig. 16b); LEARNED takes sample quantiles (below). */
 enum { MPSM_SPLIT_HIST = 0, MPSM_SPLIT_LEARNED = 1, MPSM_SPLIT_EQUI_HEIGHT = 2 };
-enum { MPSM_SEARCH_BINARY = 0, MPSM_SEARCH_LEARNED = 1 };
+/* Merge-start search in the sorted runs (Sec. 3.2.2): BINARY (with a fence index
+ * of every 64th run key on the fused path), LEARNED (the R-side model's guess, then
+ * exponential + binary search), INTERP (the paper's interpolation search: up to 16
+ * rule-of-proportion probes between the known end keys, then binary search).  All
+ * three find the exact bounds; they differ in probes and time only. */
+enum { MPSM_SEARCH_BINARY = 0, MPSM_SEARCH_LEARNED = 1, MPSM_SEARCH_INTERP = 2 };
 /* Role of the inputs (Sec. 3.2, Sec. 5.4 "role reversal"): which input is
  * range-partitioned; the other one is cut into sorted runs.  The result does not
  * depend on it (pairs keep their (r_payload, s_payload) order either way). */

@@ -240,6 +240,7 @@ LearnCtx lctx(const mpsm_plan* p, bool models) {
   c.cell = p->d_sp;  // the fine bucket -> partition array doubles as the learned cell table
   c.seed = p->opt.seed;
   c.stat = p->d_lstat;
+  c.interp = p->opt.search_mode == MPSM_SEARCH_INTERP;
   return c;
 }
 
@@ -843,7 +844,9 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   if (o.splitter_mode != MPSM_SPLIT_HIST && o.splitter_mode != MPSM_SPLIT_LEARNED &&
       o.splitter_mode != MPSM_SPLIT_EQUI_HEIGHT)
     return MPSM_ERR_INVALID_ARG;
-  if (o.search_mode != MPSM_SEARCH_BINARY && o.search_mode != MPSM_SEARCH_LEARNED) return MPSM_ERR_INVALID_ARG;
+  if (o.search_mode != MPSM_SEARCH_BINARY && o.search_mode != MPSM_SEARCH_LEARNED &&
+      o.search_mode != MPSM_SEARCH_INTERP)
+    return MPSM_ERR_INVALID_ARG;
   mpsm_plan* p = new (std::nothrow) mpsm_plan();
   if (!p) return MPSM_ERR_OOM;
   p->opt = o;

@@ -160,6 +160,10 @@ __global__ void k_search(const Job* jobs, u32 njobs, const Run* runs, const Tupl
         lb = gallop_from(at, r.len, g, klo, probes);
         err_sum += g > lb ? g - lb : lb - g;
         ++nsearch;
+      } else if (lc.interp) {
+        auto at = [&](u64 i) { return a[i].key; };
+        lb = interp_lower_bound(at, r.len, klo, probes);
+        ++nsearch;
       } else {
         lb = lower_bound_g(a, r.len, klo);
         probes += bitlen64(r.len);

@@ -969,14 +969,24 @@ __global__ void k_fences(const Tuple* xr, u64 n, u64* fence) {
     fence[g] = xr[g * 64].key;
 }
 
-// first position of run [off, off + len) whose key is >= key (upper: > key), minus off
+// first position of run [off, off + len) whose key is >= key (upper: > key), minus off;
+// the fences are searched by bisection or (interp) by interpolation search
 __device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 off, u64 len, u64 key, bool upper,
-                                         u32& probes) {
+                                         u32& probes, bool interp = false) {
   const u64 end = off + len;
   u64 lo = off, hi = end;
   const u64 g0 = (off + 63) / 64, g1 = len ? (end - 1) / 64 + 1 : g0;
   if (g0 < g1) {
     u64 a = g0, m = g1 - g0;
+    if (interp) {
+      if (upper && key == ~0ull) {
+        a = g1;
+      } else {
+        auto at = [&](u64 i) { return fence[g0 + i]; };
+        a = g0 + interp_lower_bound(at, g1 - g0, upper ? key + 1ull : key, probes);
+      }
+      m = 0;
+    }
     while (m > 0) {
       const u64 h = m >> 1;
       ++probes;
@@ -1038,9 +1048,9 @@ __global__ void k_seg_search(const Seg* segs, const u32* nseg_ptr, u32 cap, cons
       }
       swin[2 * idx] = (u32)lo;
       swin[2 * idx + 1] = (u32)hi;
-    } else {
-      swin[2 * idx] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmin, false, probes);
-      swin[2 * idx + 1] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmax, true, probes);
+    } else {  // fences by bisection, or by interpolation search (Sec. 3.2.2)
+      swin[2 * idx] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmin, false, probes, lc.interp);
+      swin[2 * idx + 1] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmax, true, probes, lc.interp);
     }
     nsearch += 2;
   }

@@ -163,6 +163,7 @@ struct LearnCtx {
   u64 seed;                 // seed of the hot-key spreading hash
   u64* stat;                // [0] partition probes, [1] keys partitioned, [2] search probes,
                             // [3] searches, [4] sum of |prediction - exact| start positions
+  u32 interp;               // without models: merge starts by interpolation search, not binary
 };
 
 }  // namespace mpsm

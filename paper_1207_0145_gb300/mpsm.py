@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libmpsm.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_DEVICE, ERR_STATE = range(7)
 SPLIT_HIST, SPLIT_LEARNED, SPLIT_EQUI_HEIGHT = 0, 1, 2
-SEARCH_BINARY, SEARCH_LEARNED = 0, 1
+SEARCH_BINARY, SEARCH_LEARNED, SEARCH_INTERP = 0, 1, 2
 PART_S, PART_R, PART_SMALLER = 0, 1, 2
 FLAG_TIMING = 1
 FLAG_KERNEL_TIMING = 2

@@ -84,6 +84,24 @@ def test_negcorr_workload_skew():
         assert np.isin(s2[:, 0], r[:, 0]).all()
 
 
+def test_locskew_workload_structure():
+    # Sec. 5.5: small to large key order by clusters, no order inside a cluster
+    n = 100_003
+    w = gen.locskew(n, 300_000, seed=6)
+    R, S = w.r_host(), w.s_host()
+    assert sorted(R[:, 0].tolist()) == list(range(1, n + 1))
+    for c in range(64):
+        a, b = n * c // 64, n * (c + 1) // 64
+        blk = R[a:b, 0]
+        assert sorted(blk.tolist()) == list(range(a + 1, b + 1))
+        assert (np.diff(blk.astype(np.int64)) < 0).any()
+    rows = w.s_rows_host().astype(np.int64)
+    assert (S[:, 0] == R[rows, 0]).all()
+    for m in (1, 2, 63, 64, 65, 130):
+        t = gen.locskew(m, 40, seed=2)
+        assert sorted(t.r_host()[:, 0].tolist()) == list(range(1, m + 1))
+
+
 def test_batch_jobs_shape():
     jobs = gen.batch_jobs(256)
     nr = np.array([j.n_r for j in jobs])

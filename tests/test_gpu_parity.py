@@ -201,12 +201,15 @@ def test_phase2_histograms_splitters_prefix_sums(fine_bits, parts, kind):
     p.close()
 
 
-@pytest.mark.parametrize("w", [gen.plain(200_000, 900_000, seed=14), gen.sparse(100_000, 300_000, seed=15),
-                               gen.zipf(100_000, 700_000, 1.1, seed=16)])
-def test_phase3_sorted_partitions_and_phase4(w):
+@pytest.mark.parametrize("w,search", [(gen.plain(200_000, 900_000, seed=14), 0), (gen.sparse(100_000, 300_000, seed=15), 0),
+                                      (gen.zipf(100_000, 700_000, 1.1, seed=16), 0),
+                                      (gen.plain(200_000, 900_000, seed=14), 2), (gen.sparse(100_000, 300_000, seed=15), 2),
+                                      (gen.zipf(100_000, 700_000, 1.1, seed=16), 2), (gen.locskew(150_000, 500_000, seed=18), 2)])
+def test_phase3_sorted_partitions_and_phase4(w, search):
+    # search 2: merge starts by interpolation search (Sec. 3.2.2); the windows are exact either way
     R, S = w.r_host(), w.s_host()
     T = 16
-    p, dR, dS = run_phases(R, S, runs_r=T, join_tile=1024)
+    p, dR, dS = run_phases(R, S, runs_r=T, join_tile=1024, search_mode=search)
     p.sort_runs(dR)
     p.splitters(dS)
     p.scatter()
@@ -244,6 +247,32 @@ def test_negatively_correlated_join_every_splitter_mode(mode):
             assert p.join(to_dev(R), to_dev(S)) == want
             if mode == M.SPLIT_EQUI_HEIGHT and side == M.PART_S:
                 assert p.stats()["imbalance"] < 1.5  # equal sizes up to the fine-bucket granularity
+
+
+@pytest.mark.parametrize("w", [gen.plain(300_000, 1_200_000, seed=31), gen.zipf(100_000, 400_000, 0.9, seed=32),
+                               gen.sparse(100_000, 200_000, seed=33), gen.locskew(200_000, 800_000, seed=34),
+                               gen.negcorr(100_000, 400_000, seed=35)])
+def test_interpolation_search_join(w):
+    # the fused path's windows (every segment x run) and the step path's tile starts
+    R, S = w.r_host(), w.s_host()
+    want = oracle.join(R, S)
+    for flags in (0, M.FLAG_UNFUSED):
+        with Plan(w.n_r, w.n_s, search_mode=M.SEARCH_INTERP, flags=flags) as p:
+            assert p.join(to_dev(R), to_dev(S)) == want
+
+
+def test_interpolation_search_probes_on_uniform_runs():
+    # on uniform keys the rule of proportion lands next to the answer: far fewer
+    # probes than the binary search's log2 of the run length
+    w = gen.plain(1 << 22, 1 << 22, seed=36)
+    R, S = w.r_host(), w.s_host()
+    probes = {}
+    for mode in (M.SEARCH_BINARY, M.SEARCH_INTERP):
+        with Plan(w.n_r, w.n_s, search_mode=mode, runs_r=4, flags=M.FLAG_UNFUSED) as p:
+            assert p.join(to_dev(R), to_dev(S)) == oracle.closed_form(w)
+            probes[mode] = p.stats()["search_probes"]
+    assert probes[M.SEARCH_BINARY] >= 20  # log2 of a 2^20-tuple run
+    assert probes[M.SEARCH_INTERP] < 10
 
 
 # ------------------------------------------------------------------ pairs
