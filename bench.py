@@ -254,6 +254,23 @@ def cpu_baseline(w, div: int):
             "seconds": round(dt, 2), "result": [c, k]}
 
 
+def cpu_pmpsm(w, div: int):
+    """The paper's own algorithm, P-MPSM, multithreaded on all host cores (pmpsm_cpu/),
+    on the same bounded sample as the oracle baseline: a stronger CPU comparison."""
+    import pmpsm_cpu
+
+    sw = sample_workload(w, div)
+    R, S = sw.r_host(), sw.s_host()
+    cores = os.cpu_count() or 1
+    pmpsm_cpu.join(R, S, threads=cores)  # warm-up (page faults of the buffers)
+    t = time.perf_counter()
+    c, k, ms = pmpsm_cpu.join(R, S, threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": (sw.n_r + sw.n_s) / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "p-mpsm threads",
+            "sample": f"same workload shape at 1/{div}: |R|={sw.n_r}, |S|={sw.n_s}, B = 10, T = {cores}",
+            "seconds": round(dt, 3), "phases_ms": [round(x, 1) for x in ms], "result": [c, k]}
+
+
 # ------------------------------------------------------------------ reference arm
 
 
@@ -438,9 +455,10 @@ def run_ours(args):
                "d2h_bytes_per_step": 16, "ms_per_step": ems}
 
     balance = partition_balance(plan, st) if args.splitter != "learned" else None
-    cpu = None
+    cpu = cpu_mt = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, args.cpu_sample)
+        cpu_mt = cpu_pmpsm(w, args.cpu_sample)
 
     if rank == 0:
         line = {
@@ -453,7 +471,7 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single"},
             "parity": parity, "result": list(results[-1]),
             "roofline": roof, "roofline_step": roof_step,
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "cpu_baseline": cpu, "cpu_pmpsm": cpu_mt, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches_per_step * args.steps,
             "phases_ms": {k: round(st[k], 3) for k in ("ms_sort_runs", "ms_splitters", "ms_scatter",
                                                        "ms_sort_partitions", "ms_search", "ms_join", "ms_total")},
