@@ -34,10 +34,12 @@ namespace {
 
 constexpr u32 NT_PASS = 512;
 // scatter geometry (measured): the first radix pass over runs or partitions, fanning
-// out up to 2048 ways, writes longer runs per bucket from 8192-tuple tiles (one
-// 1024-thread block per SM); the range-partition scatter and the later radix passes
-// over smaller segments are fastest with 4096-tuple tiles and two 512-thread blocks
-constexpr u32 RX_TILE = 8192, RX_NT = 1024, RX_MINB = 1;
+// out up to 2048 ways, runs one 1024-thread block per SM on two 5120-tuple buffers,
+// so the next tile loads while the current one is ranked and written (long write
+// runs per bucket and no idle SM while a lone block waits for its tile); the
+// range-partition scatter and the later radix passes over smaller segments are
+// fastest with 4096-tuple tiles and two 512-thread blocks
+constexpr u32 RX_TILE = 5120, RX_NT = 1024, RX_MINB = 1, RX_STAGES = 2;
 constexpr u32 SP_TILE = 4096, SP_NT = 512, SP_MINB = 2;
 constexpr u32 NT_SORT = 512;
 constexpr u32 NW_SORT = NT_SORT / 32;
@@ -431,28 +433,30 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
 // (bucket, rank) from a shared-memory counter; an exclusive scan gives the
 // tile's bucket starts; a permutation index orders the tile by bucket so the
 // write-out stores runs of consecutive destinations (coalesced 16-byte stores).
-template <u32 MODE, u32 SC_TILE, u32 NT_SC, u32 SC_MINB>
+template <u32 MODE, u32 SC_TILE, u32 NT_SC, u32 SC_MINB, u32 STAGES>
 __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, const u32* nseg_ptr, const LSeg* ls,
                                                         const u64* totals, u64 chunk, Bufs bufs, const Job* jobs,
                                                         u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
                                                         u32* err, LearnCtx lc) {
+  static_assert(STAGES == 1 || STAGES == 2, "one or two tile buffers");
   constexpr u32 IT = SC_TILE / NT_SC;
   constexpr u32 DROP = 0xFFFFFFFFu;
   extern __shared__ __align__(128) unsigned char sm_raw[];
-  Tuple* stage = reinterpret_cast<Tuple*>(sm_raw);                 // SC_TILE
-  u32* hcnt = reinterpret_cast<u32*>(stage + SC_TILE);             // F_MAX
+  Tuple* stages = reinterpret_cast<Tuple*>(sm_raw);                // STAGES x SC_TILE
+  u32* hcnt = reinterpret_cast<u32*>(stages + STAGES * SC_TILE);   // F_MAX
   u32* hb = hcnt + F_MAX;                                          // F_MAX
   u32* cur = hb + F_MAX;                                           // F_MAX
   u16* sidx = reinterpret_cast<u16*>(cur + F_MAX);                 // SC_TILE
   u16* sb = sidx + SC_TILE;                                        // SC_TILE
   u16* spl = sb + SC_TILE;                                         // FINE_MAX (MODE_SPLIT)
-  __shared__ __align__(8) u64 mbar;
+  __shared__ __align__(8) u64 mbar[STAGES];
   __shared__ u32 s_seg;
   __shared__ u32 s_warp[NT_SC / 32 + 1];
   const u32 tid = threadIdx.x;
-  if (tid == 0) mbar_init(&mbar, 1);
+  if (tid == 0)
+    for (u32 q = 0; q < STAGES; ++q) mbar_init(&mbar[q], 1);
   __syncthreads();
-  u32 phase = 0;
+  u32 phases = 0;  // bit q: the parity buffer q's barrier completes next
   const u64 nch = totals[0];
   const u32 nseg = *nseg_ptr;
   Tuple* dbase = dst_where == W_XR ? bufs.xr : (dst_where == W_XS ? bufs.xs : bufs.y);
@@ -482,19 +486,30 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
     const Tuple* src = seg_src(bufs, jobs, src_where, S.job, S.off);
     Tuple* dst = dbase + S.off;
     const u32 ntile = (u32)((e - a + SC_TILE - 1) / SC_TILE);
+    auto tile_len = [&](u32 k) {
+      const u64 t0 = a + (u64)k * SC_TILE;
+      return (u32)((e - t0) < SC_TILE ? (e - t0) : SC_TILE);
+    };
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    // with two buffers, tile k + 1 of the chunk loads while tile k is ranked and written
+    if (STAGES == 2 && tid == 0 && ntile)
+      tma_load_1d(stages, src + a, tile_len(0) * (u32)sizeof(Tuple), &mbar[0]);
     for (u32 k = 0; k < ntile; ++k) {
       const u64 t0 = a + (u64)k * SC_TILE;
-      const u32 n = (u32)((e - t0) < SC_TILE ? (e - t0) : SC_TILE);
-      if (tid == 0) tma_load_1d(stage, src + t0, n * (u32)sizeof(Tuple), &mbar);
-      const bool ok = mbar_wait(&mbar, phase, SPIN_LIMIT);
-      phase ^= 1u;
+      const u32 n = tile_len(k);
+      const u32 q = STAGES == 2 ? (k & 1u) : 0u;
+      if (STAGES == 1 && tid == 0) tma_load_1d(stages, src + t0, n * (u32)sizeof(Tuple), &mbar[0]);
+      const bool ok = mbar_wait(&mbar[q], (phases >> q) & 1u, SPIN_LIMIT);
+      phases ^= 1u << q;
       if (!__syncthreads_and(ok)) {
         if (tid == 0) atomicOr(err, (u32)DERR_TMA_TIMEOUT);
         return;
       }
-      const Tuple* T = stage;
+      // the other buffer's last readers (tile k - 1) passed the fence and barrier that ended it
+      if (STAGES == 2 && tid == 0 && k + 1 < ntile)
+        tma_load_1d(stages + (q ^ 1u) * SC_TILE, src + t0 + SC_TILE, tile_len(k + 1) * (u32)sizeof(Tuple), &mbar[q ^ 1u]);
+      const Tuple* T = stages + q * SC_TILE;
       u32 br[IT];
 #pragma unroll
       for (u32 i = 0; i < IT; ++i) {
@@ -1069,8 +1084,8 @@ __global__ void k_check_empty(const u32* cnt, u32* err, u32 flag) {
   if (threadIdx.x == 0 && *cnt != 0) atomicOr(err, flag);
 }
 
-constexpr size_t smem_scatter(u32 tile) {
-  return tile * sizeof(Tuple) + 3 * F_MAX * sizeof(u32) + 2 * tile * sizeof(u16) + FINE_MAX * sizeof(u16);
+constexpr size_t smem_scatter(u32 tile, u32 stages = 1) {
+  return stages * tile * sizeof(Tuple) + 3 * F_MAX * sizeof(u32) + 2 * tile * sizeof(u16) + FINE_MAX * sizeof(u16);
 }
 constexpr size_t smem_sort(u32 cap, u32 nt) { return cap * sizeof(Tuple) + 2 * cap * sizeof(u16) + (nt / 32) * 256 * sizeof(u32); }
 constexpr u32 NT_BIG = 512;  // threads of the 8192-tuple class (one block per SM; 1024 measured slower)
@@ -1092,12 +1107,12 @@ void init_attrs_pass() {
   set_smem(k_hist<MODE_FINE, FINE_MAX>, FINE_MAX * 20);
   set_smem(k_hist<MODE_LEARN, F_MAX>, F_MAX * 20 + FINE_MAX * 2);
   set_smem(k_scan<MODE_LEARN>, SMEM_SCAN);
-  set_smem(k_scatter<MODE_LEARN, SP_TILE, SP_NT, SP_MINB>, smem_scatter(SP_TILE));
+  set_smem(k_scatter<MODE_LEARN, SP_TILE, SP_NT, SP_MINB, 1>, smem_scatter(SP_TILE));
   set_smem(k_scan<MODE_RADIX>, SMEM_SCAN);
   set_smem(k_scan<MODE_SPLIT>, SMEM_SCAN);
-  set_smem(k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB>, smem_scatter(RX_TILE));
-  set_smem(k_scatter<MODE_RADIX, SP_TILE, SP_NT, SP_MINB>, smem_scatter(SP_TILE));
-  set_smem(k_scatter<MODE_SPLIT, SP_TILE, SP_NT, SP_MINB>, smem_scatter(SP_TILE));
+  set_smem(k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB, RX_STAGES>, smem_scatter(RX_TILE, RX_STAGES));
+  set_smem(k_scatter<MODE_RADIX, SP_TILE, SP_NT, SP_MINB, 1>, smem_scatter(SP_TILE));
+  set_smem(k_scatter<MODE_SPLIT, SP_TILE, SP_NT, SP_MINB, 1>, smem_scatter(SP_TILE));
   set_smem(k_seg_sort<NMAX / 2, 2, false, NT_SORT>, smem_sort(NMAX / 2, NT_SORT));
   set_smem(k_seg_sort<NMAX, 1, false, NT_BIG>, smem_sort(NMAX, NT_BIG));
   set_smem(k_seg_sort<NMAX / 2, 2, true, NT_SORT>, smem_sort(NMAX / 2, NT_SORT));
@@ -1168,16 +1183,16 @@ void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, 
                     Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
                     u32* err, const LearnCtx& lc, cudaStream_t st, int nsm, bool big_tiles) {
   if (mode == MODE_SPLIT) {
-    k_scatter<MODE_SPLIT, SP_TILE, SP_NT, SP_MINB><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
+    k_scatter<MODE_SPLIT, SP_TILE, SP_NT, SP_MINB, 1><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   } else if (mode == MODE_LEARN) {
-    k_scatter<MODE_LEARN, SP_TILE, SP_NT, SP_MINB><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
+    k_scatter<MODE_LEARN, SP_TILE, SP_NT, SP_MINB, 1><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   } else if (big_tiles) {
-    k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB><<<nsm * RX_MINB, RX_NT, smem_scatter(RX_TILE), st>>>(
+    k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB, RX_STAGES><<<nsm * RX_MINB, RX_NT, smem_scatter(RX_TILE, RX_STAGES), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   } else {
-    k_scatter<MODE_RADIX, SP_TILE, SP_NT, SP_MINB><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
+    k_scatter<MODE_RADIX, SP_TILE, SP_NT, SP_MINB, 1><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   }
 }
