@@ -605,43 +605,57 @@ __device__ __forceinline__ u64 block_sum_u64(u64 v, u64* s_red) {
 
 // Join of a segment or piece whose keys all equal `key` (n tuples at s, global or
 // shared): every R tuple of its windows with that key matches every S tuple.
+// Each matching R tuple r adds n pairs and n r.pay + (sum of the S payloads) to
+// the calling thread's running count and checksum.
 template <u32 NT>
 __device__ __forceinline__ void seg_join_const(const Tuple* s, u32 n, u64 key, const Seg& sg, u32 item,
-                                               const FuseCtx& fc, u64* s_red) {
+                                               const FuseCtx& fc, u64* s_red, u64& acc_cnt, u64& acc_chk) {
   const u32 tid = threadIdx.x;
   const Job& J = fc.jobs[sg.job];
   u64 ssum = 0;
   for (u32 i = tid; i < n; i += NT) ssum += s[i].pay;
-  u64 rcnt = 0, rsum = 0;
+  ssum = block_sum_u64<NT>(ssum, s_red);
+  if (tid == 0) s_red[0] = ssum;
+  __syncthreads();
+  ssum = s_red[0];
+  __syncthreads();
   for (u32 j = tid; j < J.runs; j += NT) {
     const u32* w = fc.swin + 2ull * ((u64)item * fc.maxT + j);
     const Tuple* r = fc.xr + fc.runs[J.run_base + j].off;
     for (u32 q = w[0]; q < w[1]; ++q) {  // the windows cover the segment's bounds, which may exceed `key`
       const Tuple t = r[q];
       if (t.key == key) {
-        rsum += t.pay;
-        ++rcnt;
+        acc_cnt += n;
+        acc_chk += ssum + (u64)n * t.pay;
       }
     }
   }
-  ssum = block_sum_u64<NT>(ssum, s_red);
-  rcnt = block_sum_u64<NT>(rcnt, s_red);
-  rsum = block_sum_u64<NT>(rsum, s_red);
-  if (tid == 0 && rcnt) {
-    atomicAdd(&fc.jobs[sg.job].count, rcnt * n);
-    atomicAdd(&fc.jobs[sg.job].checksum, rcnt * ssum + (u64)n * rsum);
+}
+
+// Adds the block's running count and checksum to job `job`'s totals (every thread calls it).
+template <u32 NT>
+__device__ __forceinline__ void flush_job_result(u64& acc_cnt, u64& acc_chk, u32 job, const FuseCtx& fc, u64* s_red) {
+  const u64 c = block_sum_u64<NT>(acc_cnt, s_red);
+  const u64 k = block_sum_u64<NT>(acc_chk, s_red);
+  if (threadIdx.x == 0 && job != 0xFFFFFFFFu && c) {
+    atomicAdd(&fc.jobs[job].count, c);
+    atomicAdd(&fc.jobs[job].checksum, k);
   }
+  acc_cnt = 0;
+  acc_chk = 0;
 }
 
 // Join of a sorted segment (tup in the order ia, n tuples, keys in [mn, mx])
-// against its R windows.  dir (the free ping-pong index array, CAP entries)
+// against its R windows, added to the calling thread's running count and
+// checksum.  dir (the free ping-pong index array, CAP entries)
 // becomes an order-preserving directory of at most CAP/2 key buckets; rtab (the
 // free digit-count array) stages up to RCH runs' windows at a time.
 constexpr u32 RCH = 128;
 
 template <u32 CAP, u32 NT>
 __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* dir, u32* rtab, const u32* cdir, u32 n,
-                                         u64 mn, u64 mx, const Seg& sg, u32 item, const FuseCtx& fc, u64* s_red) {
+                                         u64 mn, u64 mx, const Seg& sg, u32 item, const FuseCtx& fc, u64& cnt,
+                                         u64& chk) {
   constexpr u32 DB = (CAP >= 8192u) ? 12u : 11u;  // 2^DB = CAP / 2 buckets
   const u32 tid = threadIdx.x;
   const Job& J = fc.jobs[sg.job];
@@ -661,7 +675,6 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
   u32* wl = rtab;                                            // RCH window starts
   u32* wpre = rtab + RCH;                                    // RCH + 1 window prefix
   u64* roff = reinterpret_cast<u64*>(rtab + 2 * RCH + 8);    // RCH run offsets
-  u64 cnt = 0, chk = 0;
   for (u32 j0 = 0; j0 < T; j0 += RCH) {
     const u32 nr = T - j0 < RCH ? T - j0 : RCH;
     __syncthreads();  // directory built; the previous chunk's readers are done
@@ -756,12 +769,6 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
       }
     }
   }
-  cnt = block_sum_u64<NT>(cnt, s_red);
-  chk = block_sum_u64<NT>(chk, s_red);
-  if (tid == 0 && cnt) {
-    atomicAdd(&fc.jobs[sg.job].count, cnt);
-    atomicAdd(&fc.jobs[sg.job].checksum, chk);
-  }
 }
 
 template <u32 CAP, u32 MINB, bool FUSE, u32 NT>
@@ -788,6 +795,10 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
   u32 n_items = *nseg_ptr;
   if (n_items > cap) n_items = cap;
   Tuple* dstb = dst_where == W_XR ? bufs.xr : bufs.xs;
+  // fused: each thread's count and checksum run on across the segments of one job;
+  // the block adds them to the job's totals when the job changes and at the end
+  u64 acc_cnt = 0, acc_chk = 0;
+  u32 acc_job = 0xFFFFFFFFu;
   for (;;) {
     // order this block's earlier generic-proxy use of the buffers before the next bulk copy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -800,13 +811,17 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     const bool constant = (sg.flags & SEG_EXACT) && sg.kmin == sg.kmax;
     // the other class (the fused small class takes every segment, big ones in pieces)
     if (SMALL ? (!FUSE && !constant && sg.len > CAP) : (constant || sg.len <= NMAX / 2)) continue;
+    if (FUSE && sg.job != acc_job) {  // block-uniform: sg is the block's segment
+      flush_job_result<NT>(acc_cnt, acc_chk, acc_job, fc, s_red);
+      acc_job = sg.job;
+    }
     const Tuple* src = seg_src(bufs, jobs, sg.flags & 7u, sg.job, sg.off);
     Tuple* dst = dstb + sg.off;
     const u32 n = (u32)sg.len;
     const bool inplace = (src == dst);
     if (constant) {
       if (FUSE) {
-        seg_join_const<NT>(src, n, sg.kmin, sg, item, fc, s_red);
+        seg_join_const<NT>(src, n, sg.kmin, sg, item, fc, s_red, acc_cnt, acc_chk);
       } else if (!inplace) {
         for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, src[i]);
       }
@@ -862,7 +877,7 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     const u32 bits = bitlen64(mx - mn);
     if (bits == 0) {
       if (FUSE) {
-        seg_join_const<NT>(tup, n, mn, sg, item, fc, s_red);
+        seg_join_const<NT>(tup, n, mn, sg, item, fc, s_red, acc_cnt, acc_chk);
       } else if (!inplace) {
         for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, tup[i]);
       }
@@ -962,9 +977,10 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     }
     if (FUSE) {
       if (bits <= 11u)  // one counting pass: its digit starts are an exact per-key directory
-        seg_join<CAP, NT>(tup, ia, nullptr, reinterpret_cast<u32*>(ib), cnt, n, mn, mx, sg, item, fc, s_red);
+        seg_join<CAP, NT>(tup, ia, nullptr, reinterpret_cast<u32*>(ib), cnt, n, mn, mx, sg, item, fc, acc_cnt,
+                          acc_chk);
       else
-        seg_join<CAP, NT>(tup, ia, ib, cnt, nullptr, n, mn, mx, sg, item, fc, s_red);
+        seg_join<CAP, NT>(tup, ia, ib, cnt, nullptr, n, mn, mx, sg, item, fc, acc_cnt, acc_chk);
     } else {
       for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, tup[ia[i]]);
     }
@@ -973,6 +989,7 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     }
     if (failed) break;
   }
+  if (FUSE) flush_job_result<NT>(acc_cnt, acc_chk, acc_job, fc, s_red);
 }
 
 // ---------------------------------------------------------------- fused-path search
