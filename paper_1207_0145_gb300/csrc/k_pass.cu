@@ -33,12 +33,12 @@ namespace mpsm {
 namespace {
 
 constexpr u32 NT_PASS = 512;
-// scatter geometry (measured): the first radix pass over runs or partitions, fanning
-// out up to 2048 ways, runs one 1024-thread block per SM on two 5120-tuple buffers,
-// so the next tile loads while the current one is ranked and written (long write
-// runs per bucket and no idle SM while a lone block waits for its tile); the
-// range-partition scatter and the later radix passes over smaller segments are
-// fastest with 4096-tuple tiles and two 512-thread blocks
+// scatter geometry (measured): the first radix pass over runs or partitions (fan-out
+// up to 2048) and the range-partition scatter run one 1024-thread block per SM on
+// two 5120-tuple buffers, so the next tile loads while the current one is ranked and
+// written (long write runs per bucket and no idle SM while a lone block waits for its
+// tile); the later radix passes over smaller segments and the learned partitioning
+// are fastest with 4096-tuple tiles and two 512-thread blocks
 constexpr u32 RX_TILE = 5120, RX_NT = 1024, RX_MINB = 1, RX_STAGES = 2;
 constexpr u32 SP_TILE = 4096, SP_NT = 512, SP_MINB = 2;
 constexpr u32 NT_SORT = 512;
@@ -784,13 +784,16 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
   u16* ib = ia + CAP;                                   // CAP
   u32* cnt = reinterpret_cast<u32*>(ib + CAP);          // NW * 256 (>= 2048)
   __shared__ __align__(8) u64 mbar;
-  __shared__ u32 s_item;
+  __shared__ u32 s_item[2];
   __shared__ u32 s_warp[NT / 32 + 1];
   __shared__ u64 s_mn[NW], s_mx[NW];
   __shared__ u64 s_red[NW];
   const u32 tid = threadIdx.x, lane = lane_id(), wid = warp_id();
-  if (tid == 0) mbar_init(&mbar, 1);
-  __syncthreads();
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    if (!FUSE) s_item[0] = atomicAdd(work, 1u);
+  }
+  u32 slot = 0;
   u32 phase = 0;
   u32 n_items = *nseg_ptr;
   if (n_items > cap) n_items = cap;
@@ -802,11 +805,19 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
   for (;;) {
     // order this block's earlier generic-proxy use of the buffers before the next bulk copy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (tid == 0) s_item = atomicAdd(work, 1u);
-    __syncthreads();
-    const u32 item = s_item;
-    __syncthreads();
+    if (FUSE) {  // fetch the item now (measured faster here than fetching one ahead)
+      if (tid == 0) s_item[slot] = atomicAdd(work, 1u);
+      __syncthreads();
+    } else {  // publish the item thread 0 fetched during the previous one
+      __syncthreads();
+    }
+    const u32 item = s_item[slot];
+    if (FUSE) __syncthreads();
     if (item >= n_items) break;
+    if (!FUSE) {  // the next item, read after the next pass through the barrier above
+      if (tid == 0) s_item[slot ^ 1u] = atomicAdd(work, 1u);
+      slot ^= 1u;
+    }
     const Seg sg = segs[item];
     const bool constant = (sg.flags & SEG_EXACT) && sg.kmin == sg.kmax;
     // the other class (the fused small class takes every segment, big ones in pieces)
@@ -1129,7 +1140,7 @@ void init_attrs_pass() {
   set_smem(k_scan<MODE_SPLIT>, SMEM_SCAN);
   set_smem(k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB, RX_STAGES>, smem_scatter(RX_TILE, RX_STAGES));
   set_smem(k_scatter<MODE_RADIX, SP_TILE, SP_NT, SP_MINB, 1>, smem_scatter(SP_TILE));
-  set_smem(k_scatter<MODE_SPLIT, SP_TILE, SP_NT, SP_MINB, 1>, smem_scatter(SP_TILE));
+  set_smem(k_scatter<MODE_SPLIT, RX_TILE, RX_NT, RX_MINB, RX_STAGES>, smem_scatter(RX_TILE, RX_STAGES));
   set_smem(k_seg_sort<NMAX / 2, 2, false, NT_SORT>, smem_sort(NMAX / 2, NT_SORT));
   set_smem(k_seg_sort<NMAX, 1, false, NT_BIG>, smem_sort(NMAX, NT_BIG));
   set_smem(k_seg_sort<NMAX / 2, 2, true, NT_SORT>, smem_sort(NMAX / 2, NT_SORT));
@@ -1200,7 +1211,7 @@ void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, 
                     Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
                     u32* err, const LearnCtx& lc, cudaStream_t st, int nsm, bool big_tiles) {
   if (mode == MODE_SPLIT) {
-    k_scatter<MODE_SPLIT, SP_TILE, SP_NT, SP_MINB, 1><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
+    k_scatter<MODE_SPLIT, RX_TILE, RX_NT, RX_MINB, RX_STAGES><<<nsm * RX_MINB, RX_NT, smem_scatter(RX_TILE, RX_STAGES), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   } else if (mode == MODE_LEARN) {
     k_scatter<MODE_LEARN, SP_TILE, SP_NT, SP_MINB, 1><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
