@@ -271,6 +271,21 @@ def cpu_pmpsm(w, div: int):
             "seconds": round(dt, 3), "phases_ms": [round(x, 1) for x in ms], "result": [c, k]}
 
 
+def aggregate_replicas(ms_local: float, units_local: int, dist=None, device="cpu"):
+    """(ms, M units/s) of N independent replicas: the units of all ranks over the
+    slowest rank's time (weak scaling, no data-path collective)."""
+    ms, units = ms_local, units_local
+    if dist is not None:
+        import torch
+
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([units_local], dtype=torch.int64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, units = float(t.item()), int(u.item())
+    return ms, units / (ms / 1e3) / 1e6
+
+
 # ------------------------------------------------------------------ reference arm
 
 
@@ -371,13 +386,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_units = units * ws
-    value = total_units / (ms / 1e3) / 1e6
+    ms, value = aggregate_replicas(e0.elapsed_time(e1) / args.steps, units, dist, dev)
 
     # ---- per-kernel device time (CUDA events around every launch, separate instrumented steps)
     plan.set_flags(kernel_timing=True)
@@ -446,12 +455,8 @@ def run_ours(args):
         f1.record(stream)
         f1.synchronize()
         barrier()
-        ems = f0.elapsed_time(f1) / args.steps
-        if dist:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": total_units / (ems / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": units * 16,
+        ems, evalue = aggregate_replicas(f0.elapsed_time(f1) / args.steps, units, dist, dev)
+        e2e = {"value": evalue, "unit": UNIT, "h2d_bytes_per_step": units * 16,
                "d2h_bytes_per_step": 16, "ms_per_step": ems}
 
     balance = partition_balance(plan, st) if args.splitter != "learned" else None
@@ -503,6 +508,11 @@ def run_batch(args):
     ws, rank, local = dist_env()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     jobs = gen.batch_jobs(256, seed=args.seed + rank)
     tot_r = sum(j.n_r for j in jobs)
     tot_s = sum(j.n_s for j in jobs)
@@ -530,6 +540,8 @@ def run_batch(args):
     for _ in range(args.warmup):
         got = plan.join_batch(pairs)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     with ClockSampler(local) as clk:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -537,7 +549,9 @@ def run_batch(args):
             got = plan.join_batch(pairs)
         e1.record(stream)
         e1.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        dist.barrier()
+    ms, value = aggregate_replicas(e0.elapsed_time(e1) / args.steps, units, dist, dev)
     launches = plan.stats()["launches"]
     # the same jobs one after another through mpsm_join (plain single-join path)
     plan.set_tuning()
@@ -554,20 +568,23 @@ def run_batch(args):
     want = expect.get("v")
     res = list(zip(*got))
     parity = (res == want and seq == want) if want is not None else None
-    value = units / (ms / 1e3) / 1e6
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
         "config": {"workload": BATCH_CONFIG, "jobs": len(jobs), "n_r": tot_r, "n_s": tot_s, "tuple_bytes": 16,
-                   "tuning": tuning, "l2": "inputs far exceed L2; no flush", "parallelism": "single"},
+                   "tuning": tuning, "l2": "inputs far exceed L2; no flush",
+                   "parallelism": "replicas" if ws > 1 else "single"},
         "parity": parity, "gpu_launches": launches * args.steps,
         "sequential": {"value": units / (seq_ms / 1e3) / 1e6, "ms": seq_ms,
                        "what": "the same 256 joins one after another through mpsm_join"},
         "autotune_ms": tune_ms, "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     plan.close()
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
