@@ -44,6 +44,17 @@ def test_autotuned_batch_matches_oracle():
         assert [p.join(r, s) for r, s in jobs[:6]] == want[:6]
 
 
+@pytest.mark.parametrize("opts", [{"search_mode": 2}, {"splitter_mode": 2}, {"splitter_mode": 2, "search_mode": 2}])
+def test_batch_with_interpolation_search_and_equi_height_splitters(opts):
+    jobs, want = make_jobs(12, 3)
+    tr = sum(len(r) for r, _ in jobs)
+    ts = sum(len(s) for _, s in jobs)
+    with Plan(tr, ts, max_jobs=len(jobs), **opts) as p:
+        for _ in range(2):  # capture, then replay
+            c, k = p.join_batch(jobs)
+            assert list(zip(c, k)) == want
+
+
 def test_learned_batch_matches_oracle():
     jobs, want = make_jobs(10, 2)
     tr = sum(len(r) for r, _ in jobs)

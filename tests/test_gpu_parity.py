@@ -275,6 +275,14 @@ def test_interpolation_search_probes_on_uniform_runs():
     assert probes[M.SEARCH_INTERP] < 10
 
 
+def test_equi_height_with_more_partitions_requested_than_fine_buckets():
+    w = gen.zipf(80_000, 300_000, 0.9, seed=37)
+    R, S = w.r_host(), w.s_host()
+    with Plan(w.n_r, w.n_s, splitter_mode=M.SPLIT_EQUI_HEIGHT, fine_bits=3, partitions_s=20) as p:
+        assert p.join(to_dev(R), to_dev(S)) == oracle.join(R, S)
+        assert 1 <= p.stats()["partitions_s"] <= 8
+
+
 # ------------------------------------------------------------------ pairs
 
 

@@ -56,3 +56,16 @@ def test_reversed_roles_through_host_buffers():
     Sh = torch.from_numpy(S.view(np.int64)).pin_memory()
     with Plan(w.n_r, w.n_s, partition_side=M.PART_R) as p:
         assert p.join_host(Rh, Sh) == oracle.join(R, S)
+
+
+def test_reversed_roles_report_pair_capacity_like_the_default():
+    w = gen.plain(10_000, 40_000, seed=12)
+    R, S = to_dev(w.r_host()), to_dev(w.s_host())
+    for side in (M.PART_S, M.PART_R, M.PART_SMALLER):
+        small = torch.zeros((100, 2), dtype=torch.int64, device="cuda")
+        with Plan(w.n_r, w.n_s, partition_side=side) as p:
+            with pytest.raises(M.MPSMError) as e:
+                p.join(R, S, pairs=small)
+        assert e.value.status == M.ERR_CAPACITY and "40000" in str(e.value)
+        assert small.abs().sum().item() == 0
+
