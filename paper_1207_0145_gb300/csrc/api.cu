@@ -76,6 +76,11 @@ struct mpsm_plan {
   // data buffers
   Tuple *xr = nullptr, *xs = nullptr, *y = nullptr;
   Tuple *stage_r = nullptr, *stage_s = nullptr;
+  // mpsm_join_host: the partitioned side's copy runs on its own stream, so the run
+  // side's sort overlaps it; the join waits for it before it first reads that side
+  cudaStream_t st_copy = nullptr;
+  cudaEvent_t ev_run_copied = nullptr, ev_part_copied = nullptr;
+  bool part_copy_pending = false;
   // job / run tables
   Job *d_jobs = nullptr, *h_jobs = nullptr;
   Run *d_runs = nullptr, *h_runs = nullptr;
@@ -537,7 +542,18 @@ int phase_runs(mpsm_plan* p) {
 
 // Learned model of each job: S sample sorted by the sub-plan (the same sort
 // kernels as phase 1), fit data, training, tabulation and leaves.
+// the partitioned side's host copy must land before its first reader (the learned
+// sample, else the fine histogram)
+int wait_part_copy(mpsm_plan* p) {
+  if (p->part_copy_pending) {
+    CK(cudaStreamWaitEvent(p->st, p->ev_part_copied, 0));
+    p->part_copy_pending = false;
+  }
+  return MPSM_OK;
+}
+
 int phase_learn(mpsm_plan* p) {
+  if (int rc = wait_part_copy(p)) return rc;
   if (!p->learn) {
     record(p, EV_LEARN);
     return MPSM_OK;
@@ -592,6 +608,7 @@ int phase_splitters_learned(mpsm_plan* p) {
 }
 
 int phase_splitters(mpsm_plan* p) {
+  if (int rc = wait_part_copy(p)) return rc;
   if (split_learned(p)) return phase_splitters_learned(p);
   const u32 nj = p->njobs;
   CK(cudaMemsetAsync(p->d_rc, 0, (u64)nj * (FINE_MAX + 1) * sizeof(u64), p->st));
@@ -819,6 +836,12 @@ MPSM_API void mpsm_plan_destroy(mpsm_plan_t* p) {
     for (u32 i = 0; i < 2 * KT_POOL; ++i) cudaEventDestroy(p->kt_ev[i]);
     delete[] p->kt_ev;
   }
+  if (p->st_copy) {
+    cudaStreamSynchronize(p->st_copy);
+    cudaStreamDestroy(p->st_copy);
+  }
+  if (p->ev_run_copied) cudaEventDestroy(p->ev_run_copied);
+  if (p->ev_part_copied) cudaEventDestroy(p->ev_part_copied);
   if (p->own_stream && p->st) cudaStreamDestroy(p->st);
   delete p;
 }
@@ -1060,12 +1083,32 @@ MPSM_API int mpsm_join_host(mpsm_plan_t* p, const mpsm_tuple_t* R_host, uint64_t
   if ((nR && !R_host) || (nS && !S_host) || nR > p->max_nR || nS > p->max_nS) return MPSM_ERR_INVALID_ARG;
   if (!p->stage_r && dalloc(&p->stage_r, p->max_nR)) return MPSM_ERR_OOM;
   if (!p->stage_s && dalloc(&p->stage_s, p->max_nS)) return MPSM_ERR_OOM;
-  if (nR) CK(cudaMemcpyAsync(p->stage_r, R_host, nR * sizeof(Tuple), cudaMemcpyHostToDevice, p->st));
-  if (nS) CK(cudaMemcpyAsync(p->stage_s, S_host, nS * sizeof(Tuple), cudaMemcpyHostToDevice, p->st));
+  if (!p->st_copy) {
+    CK(cudaStreamCreateWithFlags(&p->st_copy, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&p->ev_run_copied, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&p->ev_part_copied, cudaEventDisableTiming));
+  }
+  const bool rev = reverse_roles(p, nR, nS);
+  // the run side first, on the plan's stream, where its sort follows; the partitioned
+  // side after it on the copy stream (the host link is the bound: one copy at a time
+  // gets all of it), so the run-side sort runs while the larger copy is in flight
+  Tuple* run_dst = rev ? p->stage_s : p->stage_r;
+  Tuple* part_dst = rev ? p->stage_r : p->stage_s;
+  const void* run_src = rev ? static_cast<const void*>(S_host) : static_cast<const void*>(R_host);
+  const void* part_src = rev ? static_cast<const void*>(R_host) : static_cast<const void*>(S_host);
+  const u64 n_run = rev ? nS : nR, n_part = rev ? nR : nS;
+  if (n_run) CK(cudaMemcpyAsync(run_dst, run_src, n_run * sizeof(Tuple), cudaMemcpyHostToDevice, p->st));
+  CK(cudaEventRecord(p->ev_run_copied, p->st));  // also after every earlier reader of the staging buffers
+  CK(cudaStreamWaitEvent(p->st_copy, p->ev_run_copied, 0));
+  if (n_part) CK(cudaMemcpyAsync(part_dst, part_src, n_part * sizeof(Tuple), cudaMemcpyHostToDevice, p->st_copy));
+  CK(cudaEventRecord(p->ev_part_copied, p->st_copy));
+  p->part_copy_pending = true;
   const mpsm_tuple_t* r = reinterpret_cast<const mpsm_tuple_t*>(p->stage_r);
   const mpsm_tuple_t* sd = reinterpret_cast<const mpsm_tuple_t*>(p->stage_s);
-  if (reverse_roles(p, nR, nS)) return join_device(p, sd, nS, r, nR, out_count, out_checksum, nullptr);
-  return join_device(p, r, nR, sd, nS, out_count, out_checksum, nullptr);
+  const int rc = rev ? join_device(p, sd, nS, r, nR, out_count, out_checksum, nullptr)
+                     : join_device(p, r, nR, sd, nS, out_count, out_checksum, nullptr);
+  if (int rw = wait_part_copy(p)) return rw;  // an early error return never reached the wait
+  return rc;
 }
 
 MPSM_API int mpsm_join_batch(mpsm_plan_t* p, const mpsm_job_t* jobs, uint32_t njobs, uint64_t* out_counts,
