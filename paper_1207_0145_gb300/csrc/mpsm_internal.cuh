@@ -170,6 +170,34 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* total, T* s_warp /* >=
   return warp_prefix + x - v;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v);
+
+// Exclusive scan over the block with one barrier: every warp scans its values, then
+// sums the totals of the warps before it (and of all warps) from shared memory on its
+// own.  The caller must pass a barrier before s_warp is written again.
+template <typename T, int NT>
+__device__ __forceinline__ T block_exclusive_scan_1b(T v, T* total, T* s_warp /* >= NT/32 */) {
+  static_assert(NT / 32 <= 32, "one warp sums the warp totals");
+  const u32 lane = lane_id(), wid = warp_id();
+  T x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= (u32)d) x += y;
+  }
+  if (lane == 31) s_warp[wid] = x;
+  __syncthreads();
+  T before = 0, all = 0;
+  if (lane < (u32)(NT / 32)) {
+    all = s_warp[lane];
+    before = lane < wid ? all : T(0);
+  }
+  before = warp_sum(before);
+  *total = warp_sum(all);
+  return before + x - v;
+}
+
 // In-place exclusive scan of n <= NT*ITEMS u32/u64 values in shared memory.
 template <typename T, int NT, int ITEMS>
 __device__ __forceinline__ T smem_exclusive_scan(T* a, u32 n, T* s_warp) {
@@ -183,14 +211,14 @@ __device__ __forceinline__ T smem_exclusive_scan(T* a, u32 n, T* s_warp) {
     sum += loc[i];
   }
   T total;
-  T pre = block_exclusive_scan<T, NT>(sum, &total, s_warp);
+  T pre = block_exclusive_scan_1b<T, NT>(sum, &total, s_warp);
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const u32 k = base + i;
     if (k < n) a[k] = pre;
     pre += loc[i];
   }
-  __syncthreads();
+  __syncthreads();  // the scanned values are visible, and s_warp may be written again
   return total;
 }
 
