@@ -375,6 +375,9 @@ def run_ours(args):
             dist.barrier()
 
     # ---- device-timed steps
+    # the host computes the expected result alongside the warm-up; it must be done
+    # before the timed steps, whose launches and pass-count reads need the host cores
+    th.join()
     torch.cuda.synchronize()
     barrier()
     with ClockSampler(local) as clk:
@@ -539,6 +542,7 @@ def run_batch(args):
         tuning, tune_ms = plan.autotune(pairs, reps=1)
     for _ in range(args.warmup):
         got = plan.join_batch(pairs)
+    th.join()  # the expected results are computed on the host cores before the timed steps
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
