@@ -1013,15 +1013,51 @@ __global__ void k_fences(const Tuple* xr, u64 n, u64* fence) {
 }
 
 // first position of run [off, off + len) whose key is >= key (upper: > key), minus off;
-// the fences are searched by bisection or (interp) by interpolation search
+// the fences are searched by bisection or (interp) by interpolation search.  With
+// `from` (an upper bound after the lower bound of a key <= this one), the fence search
+// gallops forward from the fence the lower bound stopped at, *from, instead: a window
+// is short, so its end is a fence or two on, in lines the lower bound brought into L2.
+// `at` receives the fence the search stopped at.
 __device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 off, u64 len, u64 key, bool upper,
-                                         u32& probes, bool interp = false) {
+                                         u32& probes, bool interp = false, const u64* from = nullptr,
+                                         u64* at = nullptr) {
   const u64 end = off + len;
   u64 lo = off, hi = end;
   const u64 g0 = (off + 63) / 64, g1 = len ? (end - 1) / 64 + 1 : g0;
   if (g0 < g1) {
     u64 a = g0, m = g1 - g0;
-    if (interp) {
+    if (from && *from >= g0 && *from <= g1) {
+      // every fence before *from is below the earlier key, so not past this one
+      a = *from;
+      u64 step = 1;
+      for (;;) {
+        if (a >= g1) {
+          m = 0;
+          break;
+        }
+        ++probes;
+        const u64 f = fence[a];
+        if (upper ? f > key : f >= key) {
+          m = 0;
+          break;
+        }
+        const u64 next = a + step;
+        if (next >= g1) {  // the answer is in (a, g1]
+          m = g1 - (a + 1);
+          a = a + 1;
+          break;
+        }
+        ++probes;
+        const u64 fn = fence[next];
+        if (upper ? fn > key : fn >= key) {  // the answer is in (a, next]
+          m = next - (a + 1);
+          a = a + 1;
+          break;
+        }
+        a = next + 1;
+        step <<= 1;
+      }
+    } else if (interp) {
       if (upper && key == ~0ull) {
         a = g1;
       } else {
@@ -1041,8 +1077,11 @@ __device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 
         m = h;
       }
     }
+    if (at) *at = a;
     if (a > g0) lo = (a - 1) * 64 + 1;
     if (a < g1) hi = a * 64;
+  } else if (at) {
+    *at = g0;
   }
   u64 m = hi - lo;
   while (m > 0) {
@@ -1092,8 +1131,9 @@ __global__ void k_seg_search(const Seg* segs, const u32* nseg_ptr, u32 cap, cons
       swin[2 * idx] = (u32)lo;
       swin[2 * idx + 1] = (u32)hi;
     } else {  // fences by bisection, or by interpolation search (Sec. 3.2.2)
-      swin[2 * idx] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmin, false, probes, lc.interp);
-      swin[2 * idx + 1] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmax, true, probes, lc.interp);
+      u64 a = 0;
+      swin[2 * idx] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmin, false, probes, lc.interp, nullptr, &a);
+      swin[2 * idx + 1] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmax, true, probes, lc.interp, &a);
     }
     nsearch += 2;
   }
