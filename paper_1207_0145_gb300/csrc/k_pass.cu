@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
   const u32 tid = threadIdx.x, lane = lane_id(), wid = warp_id();
   if (tid == 0) {
     mbar_init(&mbar, 1);
-    if (!FUSE) s_item[0] = atomicAdd(work, 1u);
+    s_item[0] = atomicAdd(work, 1u);
   }
   u32 slot = 0;
   u32 phase = 0;
@@ -805,23 +805,34 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
   for (;;) {
     // order this block's earlier generic-proxy use of the buffers before the next bulk copy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (FUSE) {  // fetch the item now (measured faster here than fetching one ahead)
-      if (tid == 0) s_item[slot] = atomicAdd(work, 1u);
-      __syncthreads();
-    } else {  // publish the item thread 0 fetched during the previous one
-      __syncthreads();
-    }
+    __syncthreads();  // publishes the item thread 0 fetched during the previous one
     const u32 item = s_item[slot];
-    if (FUSE) __syncthreads();
     if (item >= n_items) break;
-    if (!FUSE) {  // the next item, read after the next pass through the barrier above
-      if (tid == 0) s_item[slot ^ 1u] = atomicAdd(work, 1u);
-      slot ^= 1u;
-    }
+    u32 nxt = 0;
+    if (tid == 0) nxt = atomicAdd(work, 1u);  // the next item; its value is needed only below
+    const u32 nslot = slot ^ 1u;
+    slot ^= 1u;
+    // thread 0 publishes the next item (read after the barrier that ends this one) and
+    // asks L2 for the start of its data, so its bulk copy finds it there
+    auto publish_next = [&]() {
+      if (tid == 0) {
+        s_item[nslot] = nxt;
+        if (FUSE && nxt < n_items) {
+          const Seg ns = segs[nxt];
+          const Tuple* nsrc = seg_src(bufs, jobs, ns.flags & 7u, ns.job, ns.off);
+          const u32 nbytes = (u32)((ns.len < CAP ? ns.len : (u64)CAP) * sizeof(Tuple));
+          if (nbytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(nsrc), "r"(nbytes) : "memory");
+        }
+      }
+    };
+    bool published = false;
     const Seg sg = segs[item];
     const bool constant = (sg.flags & SEG_EXACT) && sg.kmin == sg.kmax;
     // the other class (the fused small class takes every segment, big ones in pieces)
-    if (SMALL ? (!FUSE && !constant && sg.len > CAP) : (constant || sg.len <= NMAX / 2)) continue;
+    if (SMALL ? (!FUSE && !constant && sg.len > CAP) : (constant || sg.len <= NMAX / 2)) {
+      publish_next();
+      continue;
+    }
     if (FUSE && sg.job != acc_job) {  // block-uniform: sg is the block's segment
       flush_job_result<NT>(acc_cnt, acc_chk, acc_job, fc, s_red);
       acc_job = sg.job;
@@ -831,6 +842,7 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     const u32 n = (u32)sg.len;
     const bool inplace = (src == dst);
     if (constant) {
+      publish_next();
       if (FUSE) {
         seg_join_const<NT>(src, n, sg.kmin, sg, item, fc, s_red, acc_cnt, acc_chk);
       } else if (!inplace) {
@@ -840,6 +852,7 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     }
     if (!FUSE && sg.len > CAP) {
       if (tid == 0) atomicOr(err, (u32)DERR_SEG_TOO_BIG);
+      publish_next();
       continue;
     }
     // The fused join is exact for any split of S into pieces joined against windows
@@ -848,6 +861,10 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     for (u32 p0 = 0; p0 < n; p0 += CAP) {
     const u32 n = (sg.len - p0 < CAP) ? (u32)(sg.len - p0) : CAP;  // this piece
     if (tid == 0) tma_load_1d(tup, src + p0, n * (u32)sizeof(Tuple), &mbar);
+    if (!published) {
+      publish_next();
+      published = true;
+    }
     const bool ok = mbar_wait(&mbar, phase, SPIN_LIMIT);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) {
