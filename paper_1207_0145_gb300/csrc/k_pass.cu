@@ -817,11 +817,15 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     auto publish_next = [&]() {
       if (tid == 0) {
         s_item[nslot] = nxt;
-        if (FUSE && nxt < n_items) {
+        if (nxt < n_items) {
           const Seg ns = segs[nxt];
+          const bool nconst = (ns.flags & SEG_EXACT) && ns.kmin == ns.kmax;
+          // only a segment of this class (the same test as the skip below)
+          const bool mine = SMALL ? !(!FUSE && !nconst && ns.len > CAP) : !(nconst || ns.len <= NMAX / 2);
           const Tuple* nsrc = seg_src(bufs, jobs, ns.flags & 7u, ns.job, ns.off);
           const u32 nbytes = (u32)((ns.len < CAP ? ns.len : (u64)CAP) * sizeof(Tuple));
-          if (nbytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(nsrc), "r"(nbytes) : "memory");
+          if (mine && nbytes)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(nsrc), "r"(nbytes) : "memory");
         }
       }
     };
