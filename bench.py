@@ -211,13 +211,28 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash(files=None):
-    """Hash of the CUDA sources a kernel is built from (all of csrc when not named)."""
+def _code_only(text: str) -> str:
+    """C/CUDA source without comments and with whitespace collapsed: a comment edit
+    does not change the kernel, so it must not invalidate a recorded measurement."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_source_hash(files=None, texts=None):
+    """Hash of the code (comments dropped) of the CUDA sources a kernel is built from
+    (all of csrc when not named); `texts` supplies other versions of the files."""
     d = os.path.join(ROOT, "paper_1207_0145_gb300", "csrc")
     h = hashlib.sha256()
     for fn in sorted(files or os.listdir(d)):
-        with open(os.path.join(d, fn), "rb") as f:
-            h.update(f.read())
+        if texts and fn in texts:
+            text = texts[fn]
+        else:
+            with open(os.path.join(d, fn), encoding="utf-8") as f:
+                text = f.read()
+        h.update(_code_only(text).encode())
     return h.hexdigest()[:16]
 
 

@@ -428,8 +428,8 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
 
 // ---------------------------------------------------------------- scatter
 // Per chunk (worker): tiles of SC_TILE tuples arrive by bulk async copy into
-// shared memory (with two blocks per SM one block's copy overlaps the other's
-// work).  Each tuple gets
+// shared memory (with two buffers the next tile's copy overlaps this tile's work;
+// with one, two blocks per SM overlap each other's).  Each tuple gets
 // (bucket, rank) from a shared-memory counter; an exclusive scan gives the
 // tile's bucket starts; a permutation index orders the tile by bucket so the
 // write-out stores runs of consecutive destinations (coalesced 16-byte stores).
@@ -589,7 +589,11 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
 // and stores them coalesced.  Two instantiations share the work list: CAP =
 // 4096 (two blocks per SM, so one block's copy overlaps the other's sort)
 // takes segments of at most 4096 tuples and all constant-key segments; CAP =
-// 8192 (one block per SM) takes the rest.
+// 8192 (one block per SM) takes the rest.  The fused instantiation (phases 3
+// and 4 in one kernel) takes every final S segment, in 4096-tuple pieces, and
+// joins it in shared memory instead of writing it out.  A block fetches its next
+// segment one ahead and asks L2 for that segment's data, so the next bulk copy
+// finds it there.
 // sum of one u64 per thread over the block (result valid in thread 0)
 template <u32 NT>
 __device__ __forceinline__ u64 block_sum_u64(u64 v, u64* s_red) {
@@ -647,9 +651,10 @@ __device__ __forceinline__ void flush_job_result(u64& acc_cnt, u64& acc_chk, u32
 
 // Join of a sorted segment (tup in the order ia, n tuples, keys in [mn, mx])
 // against its R windows, added to the calling thread's running count and
-// checksum.  dir (the free ping-pong index array, CAP entries)
-// becomes an order-preserving directory of at most CAP/2 key buckets; rtab (the
-// free digit-count array) stages up to RCH runs' windows at a time.
+// checksum.  dir (the free ping-pong index array, CAP entries) becomes an
+// order-preserving directory of at most CAP/2 key buckets, unless cdir gives the
+// exact per-key starts; rtab (free shared memory) stages up to RCH runs' windows
+// and their prefix sums at a time, so every thread takes any window position.
 constexpr u32 RCH = 128;
 
 template <u32 CAP, u32 NT>
@@ -1120,8 +1125,10 @@ __device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 
 }
 
 // windows of every (final S segment, R run) pair from the segment's key bounds:
-// fence search, or with the learned R-side model its predicted position times
-// the run length followed by an exact exponential + binary search
+// fence search for the start and a gallop over the fences to the end (or the
+// paper's interpolation search over the fences), or with the learned R-side
+// model its predicted position times the run length followed by an exact
+// exponential + binary search
 __global__ void k_seg_search(const Seg* segs, const u32* nseg_ptr, u32 cap, const Job* jobs, const Run* runs,
                              const Tuple* xr, const u64* fence, u32* swin, u32 maxT, LearnCtx lc) {
   u32 nseg = *nseg_ptr;
