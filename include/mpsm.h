@@ -313,6 +313,33 @@ int mpsm_plan_view(mpsm_plan_t* plan, mpsm_view_t* view);
 
 const char* mpsm_strerror(int status);
 
+/* ---- device-side checks -----------------------------------------------------
+ * The paper has no counterpart.  Kernels never trap, assert or spin without end:
+ * an invariant they find violated, an index they find out of bounds (the access
+ * is skipped) or a wait that runs out (a bulk copy not complete after a bounded
+ * number of polls of its shared-memory barrier) sets one of these bits, and the
+ * call returns MPSM_ERR_DEVICE. */
+enum {
+  MPSM_DEVERR_LIST_OVERFLOW = 1u,   /* a segment work list ran out of capacity            */
+  MPSM_DEVERR_SEGMENT_TOO_BIG = 2u, /* a final segment larger than a shared-memory sort    */
+  MPSM_DEVERR_WAIT_TIMEOUT = 4u,    /* a bounded wait gave up                              */
+  MPSM_DEVERR_LEVELS = 8u,          /* radix passes exhausted with big segments left       */
+  MPSM_DEVERR_HIST_OVERFLOW = 16u,  /* a pass needed more histogram entries than allocated */
+  MPSM_DEVERR_LEARN = 32u,          /* a learned-model invariant was violated              */
+  MPSM_DEVERR_BOUNDS = 64u          /* an index check inside a kernel failed               */
+};
+
+/* The MPSM_DEVERR_* bits of the plan's last call that returned MPSM_ERR_DEVICE,
+ * 0 after a call that did not (HOST). */
+int mpsm_plan_device_errors(const mpsm_plan_t* plan, uint32_t* flags);
+
+/* Self-test of the bounded waits, on `cuda_stream` (NULL = the default stream): one
+ * block waits on a shared-memory barrier that nothing will complete, gives up
+ * after spin_limit polls (0 = 1000), sets MPSM_DEVERR_WAIT_TIMEOUT and returns.
+ * Returns MPSM_ERR_DEVICE with *flags = MPSM_DEVERR_WAIT_TIMEOUT; the CUDA context
+ * stays usable.  Allocates and frees 4 bytes of device memory.  Synchronises. */
+int mpsm_selftest_wait_timeout(void* cuda_stream, uint32_t spin_limit, uint32_t* flags);
+
 /* ---- allocation-free run sort ------------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that must
  * not allocate device memory -- code that runs under a memory pool owned by

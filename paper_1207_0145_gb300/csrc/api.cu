@@ -81,6 +81,7 @@ struct mpsm_plan {
   cudaStream_t st_copy = nullptr;
   cudaEvent_t ev_run_copied = nullptr, ev_part_copied = nullptr;
   bool part_copy_pending = false;
+  u32 device_errors = 0;            // MPSM_DEVERR_* bits read back by the last call
   // job / run tables
   Job *d_jobs = nullptr, *h_jobs = nullptr;
   Run *d_runs = nullptr, *h_runs = nullptr;
@@ -462,6 +463,7 @@ int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
   CK(cudaStreamSynchronize(p->st));
   p->levels_r = p->levels_s = 0;
   p->launches = 0;
+  p->device_errors = 0;
   p->kt_n = 0;
   p->learn = split_learned(p) || search_learned(p);
   CK(cudaMemsetAsync(p->d_lstat, 0, 8 * sizeof(u64), p->st));
@@ -713,8 +715,8 @@ int read_err(mpsm_plan* p) {
   if (sub)
     CK(cudaMemcpyAsync(&p->sub->h_cnt[C_ERR], &p->sub->d_cnt[C_ERR], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
   CK(cudaStreamSynchronize(p->st));
-  if (sub && p->sub->h_cnt[C_ERR]) return MPSM_ERR_DEVICE;
-  return p->h_cnt[C_ERR] ? MPSM_ERR_DEVICE : MPSM_OK;
+  p->device_errors = p->h_cnt[C_ERR] | (sub ? p->sub->h_cnt[C_ERR] : 0u);
+  return p->device_errors ? MPSM_ERR_DEVICE : MPSM_OK;
 }
 
 int phase_join(mpsm_plan* p, uint64_t* out_count, uint64_t* out_checksum, mpsm_pairs_t* pairs) {
@@ -1356,6 +1358,38 @@ MPSM_API int mpsm_plan_view(mpsm_plan_t* p, mpsm_view_t* v) {
   v->join_tile = p->tile;
   v->windows = p->d_win + 2 * J.win_base;
   return MPSM_OK;
+}
+
+static_assert(DERR_SEG_OVERFLOW == MPSM_DEVERR_LIST_OVERFLOW && DERR_SEG_TOO_BIG == MPSM_DEVERR_SEGMENT_TOO_BIG &&
+                  DERR_TMA_TIMEOUT == MPSM_DEVERR_WAIT_TIMEOUT && DERR_LEVELS == MPSM_DEVERR_LEVELS &&
+                  DERR_HIST_OVERFLOW == MPSM_DEVERR_HIST_OVERFLOW && DERR_LEARN == MPSM_DEVERR_LEARN &&
+                  DERR_BOUNDS == MPSM_DEVERR_BOUNDS,
+              "device check bits match the ABI");
+
+MPSM_API int mpsm_plan_device_errors(const mpsm_plan_t* p, uint32_t* flags) {
+  if (!p || !flags) return MPSM_ERR_INVALID_ARG;
+  *flags = p->device_errors;
+  return MPSM_OK;
+}
+
+MPSM_API int mpsm_selftest_wait_timeout(void* stream, uint32_t spin_limit, uint32_t* flags) {
+  if (!flags) return MPSM_ERR_INVALID_ARG;
+  *flags = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  u32* d_flag = nullptr;
+  if (cudaMalloc(&d_flag, sizeof(u32)) != cudaSuccess) return MPSM_ERR_OOM;
+  u32 h = 0;
+  cudaError_t e = cudaMemsetAsync(d_flag, 0, sizeof(u32), st);
+  if (e == cudaSuccess) {
+    launch_wait_selftest(d_flag, spin_limit ? spin_limit : 1000u, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_flag, sizeof(u32), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_flag);
+  if (e != cudaSuccess) return MPSM_ERR_CUDA;
+  *flags = h;
+  return h ? MPSM_ERR_DEVICE : MPSM_OK;
 }
 
 MPSM_API const char* mpsm_strerror(int status) {

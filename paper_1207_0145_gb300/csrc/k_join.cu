@@ -503,6 +503,18 @@ void launch_swap_pairs(Tuple* pairs, u64 n, cudaStream_t st, int nsm) {
   if (n) k_swap_pairs<<<nsm * 8, 256, 0, st>>>(pairs, n);
 }
 
+// One block waits on a shared-memory barrier that no copy will complete: the bounded
+// wait every kernel uses gives up after `limit` polls and the block reports it.
+__global__ void k_wait_selftest(u32* flag, u32 limit) {
+  __shared__ __align__(8) u64 bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, limit);
+  if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicOr(flag, (u32)DERR_TMA_TIMEOUT);
+}
+
+void launch_wait_selftest(u32* flag, u32 limit, cudaStream_t st) { k_wait_selftest<<<1, 32, 0, st>>>(flag, limit); }
+
 void launch_pair_offsets(Job* jobs, u32 njobs, const u64* totals, const u64* tile_cnt, u64* tile_out,
                          u64* pair_total, cudaStream_t st) {
   k_pair_offsets<<<1, 1024, 0, st>>>(jobs, njobs, totals, tile_cnt, tile_out, pair_total);

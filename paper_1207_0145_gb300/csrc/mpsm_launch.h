@@ -57,6 +57,7 @@ void launch_join(u32 mode, Job* jobs, u32 njobs, const Run* runs, const Tuple* x
                  const u64* totals, const u32* win, u64* tile_cnt, const u64* tile_out, Tuple* pairs,
                  u32* err, cudaStream_t st, int nsm);
 void launch_swap_pairs(Tuple* pairs, u64 n, cudaStream_t st, int nsm);
+void launch_wait_selftest(u32* flag, u32 limit, cudaStream_t st);  // bounded-wait self-test
 void launch_pair_offsets(Job* jobs, u32 njobs, const u64* totals, const u64* tile_cnt, u64* tile_out,
                          u64* pair_total, cudaStream_t st);
 

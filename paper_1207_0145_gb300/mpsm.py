@@ -16,6 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmpsm.so")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_DEVICE, ERR_STATE = range(7)
+# device check bits (include/mpsm.h, MPSM_DEVERR_*)
+DEVERR_LIST_OVERFLOW, DEVERR_SEGMENT_TOO_BIG, DEVERR_WAIT_TIMEOUT, DEVERR_LEVELS = 1, 2, 4, 8
+DEVERR_HIST_OVERFLOW, DEVERR_LEARN, DEVERR_BOUNDS = 16, 32, 64
 SPLIT_HIST, SPLIT_LEARNED, SPLIT_EQUI_HEIGHT = 0, 1, 2
 SEARCH_BINARY, SEARCH_LEARNED, SEARCH_INTERP = 0, 1, 2
 PART_S, PART_R, PART_SMALLER = 0, 1, 2
@@ -110,6 +113,8 @@ def lib():
             "mpsm_plan_stats": ([_p, P(Stats)], ctypes.c_int),
             "mpsm_plan_view": ([_p, P(View)], ctypes.c_int),
             "mpsm_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "mpsm_plan_device_errors": ([_p, P(_u32)], ctypes.c_int),
+            "mpsm_selftest_wait_timeout": ([_p, _u32, P(_u32)], ctypes.c_int),
             "mpsm_plan_set_flags": ([_p, _u32], ctypes.c_int),
             "mpsm_plan_kernel_times": ([_p, P(KernelTime), _u32, P(_u32)], ctypes.c_int),
             "mpsm_sort_runs_noalloc": ([_p, _u64, _u32, _p, _p], ctypes.c_int),
@@ -343,6 +348,12 @@ class Plan(_RmiMixin):
         flags = (FLAG_TIMING if timing else 0) | (FLAG_KERNEL_TIMING if kernel_timing else 0) | extra
         _check(lib().mpsm_plan_set_flags(self.handle, flags), "mpsm_plan_set_flags")
 
+    def device_errors(self) -> int:
+        """MPSM_DEVERR_* bits of the last call that returned MPSM_ERR_DEVICE (0 otherwise)."""
+        f = _u32()
+        _check(lib().mpsm_plan_device_errors(self.handle, ctypes.byref(f)), "mpsm_plan_device_errors")
+        return f.value
+
     def kernel_times(self) -> dict:
         """{family: (launches, ms)} of the last call made with kernel timing on."""
         arr = (KernelTime * 64)()
@@ -354,6 +365,14 @@ class Plan(_RmiMixin):
         v = View()
         _check(lib().mpsm_plan_view(self.handle, ctypes.byref(v)), "mpsm_plan_view")
         return v
+
+
+def selftest_wait_timeout(spin_limit: int = 1000, stream: Optional[int] = None) -> Tuple[int, int]:
+    """(status, MPSM_DEVERR_* bits) of the bounded-wait self-test: a kernel waits on a
+    barrier nothing completes and gives up; expect (ERR_DEVICE, DEVERR_WAIT_TIMEOUT)."""
+    f = _u32()
+    rc = lib().mpsm_selftest_wait_timeout(stream, spin_limit, ctypes.byref(f))
+    return rc, f.value
 
 
 def sort_runs_noalloc(R, runs: int, out, stream: Optional[int] = None):

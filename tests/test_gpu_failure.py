@@ -1,0 +1,34 @@
+"""Failure detection without a GPU fault: the bounded waits of the kernels give up
+and report, and the context stays usable; a device-side check failure is reported
+as MPSM_ERR_DEVICE with its MPSM_DEVERR_* bits."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from helpers import to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1207_0145_gb300 import Plan, mpsm as M  # noqa: E402
+
+
+@pytest.mark.parametrize("limit", [1, 1000, 100_000])
+def test_bounded_wait_gives_up_and_the_context_stays_usable(limit):
+    rc, flags = M.selftest_wait_timeout(limit)
+    assert rc == M.ERR_DEVICE and flags == M.DEVERR_WAIT_TIMEOUT
+    w = gen.plain(20_000, 80_000, seed=41)
+    R, S = w.r_host(), w.s_host()
+    with Plan(w.n_r, w.n_s) as p:
+        assert p.join(to_dev(R), to_dev(S)) == oracle.join(R, S)
+        assert p.device_errors() == 0
+
+
+def test_device_errors_are_cleared_by_a_good_call():
+    w = gen.zipf(30_000, 90_000, 0.9, seed=42)
+    R, S = w.r_host(), w.s_host()
+    with Plan(w.n_r, w.n_s) as p:
+        for _ in range(2):
+            assert p.join(to_dev(R), to_dev(S)) == oracle.join(R, S)
+            assert p.device_errors() == 0
