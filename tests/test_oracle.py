@@ -132,7 +132,9 @@ def test_closed_form_plain_config0():
 
 
 @pytest.mark.parametrize("w", [gen.zipf(50_000, 200_000, 0.9, seed=5), gen.sparse(40_000, 60_000, seed=6),
-                               gen.plain(3, 1000, seed=1), gen.zipf(1, 50, 0.8, seed=2)])
+                               gen.plain(3, 1000, seed=1), gen.zipf(1, 50, 0.8, seed=2),
+                               gen.negcorr(60_000, 240_000, seed=7), gen.negcorr(2, 30, seed=8),
+                               gen.locskew(50_003, 150_000, seed=9), gen.locskew(5, 40, seed=10)])
 def test_closed_form_matches_join(w):
     R, S = w.r_host(), w.s_host()
     assert oracle.join(R, S) == oracle.closed_form(w)
