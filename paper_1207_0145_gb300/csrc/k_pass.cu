@@ -433,6 +433,9 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
 // (bucket, rank) from a shared-memory counter; an exclusive scan gives the
 // tile's bucket starts; a permutation index orders the tile by bucket so the
 // write-out stores runs of consecutive destinations (coalesced 16-byte stores).
+// Each thread owns F_MAX / NT_SC buckets in the scan and keeps their write
+// offsets in registers, so one pass over the counters per tile scans them,
+// publishes each bucket's offset and clears the counts.
 template <u32 MODE, u32 SC_TILE, u32 NT_SC, u32 SC_MINB, u32 STAGES>
 __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, const u32* nseg_ptr, const LSeg* ls,
                                                         const u64* totals, u64 chunk, Bufs bufs, const Job* jobs,
@@ -445,8 +448,8 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
   Tuple* stages = reinterpret_cast<Tuple*>(sm_raw);                // STAGES x SC_TILE
   u32* hcnt = reinterpret_cast<u32*>(stages + STAGES * SC_TILE);   // F_MAX
   u32* hb = hcnt + F_MAX;                                          // F_MAX
-  u32* cur = hb + F_MAX;                                           // F_MAX
-  u16* sidx = reinterpret_cast<u16*>(cur + F_MAX);                 // SC_TILE
+  u32* gb = hb + F_MAX;                                            // F_MAX
+  u16* sidx = reinterpret_cast<u16*>(gb + F_MAX);                  // SC_TILE
   u16* sb = sidx + SC_TILE;                                        // SC_TILE
   u16* spl = sb + SC_TILE;                                         // FINE_MAX (MODE_SPLIT)
   __shared__ __align__(8) u64 mbar[STAGES];
@@ -468,10 +471,14 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
     const u32 F = L.F;
     const u64 ci = c - L.chunk_base;
     const u32* orow = hist + L.hist_base + ci * F;
-    for (u32 b = tid; b < F; b += NT_SC) {
-      cur[b] = orow[b];
-      hcnt[b] = 0;
+    constexpr u32 PER = F_MAX / NT_SC;
+    u32 curv[PER];  // write offset (within the segment) of owned bucket tid * PER + i
+#pragma unroll
+    for (u32 i = 0; i < PER; ++i) {
+      const u32 b = tid * PER + i;
+      curv[i] = b < F ? orow[b] : 0u;
     }
+    for (u32 b = tid; b < F; b += NT_SC) hcnt[b] = 0;
     u64 kmin = 0, kmax = ~0ull;
     if (MODE == MODE_SPLIT || MODE == MODE_LEARN) {
       const Job& J = jobs[S.job];
@@ -506,7 +513,7 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
         if (tid == 0) atomicOr(err, (u32)DERR_TMA_TIMEOUT);
         return;
       }
-      // the other buffer's last readers (tile k - 1) passed the fence and barrier that ended it
+      // the other buffer's last readers (tile k - 1) passed their fence and this barrier
       if (STAGES == 2 && tid == 0 && k + 1 < ntile)
         tma_load_1d(stages + (q ^ 1u) * SC_TILE, src + t0 + SC_TILE, tile_len(k + 1) * (u32)sizeof(Tuple), &mbar[q ^ 1u]);
       const Tuple* T = stages + q * SC_TILE;
@@ -535,9 +542,10 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
         br[i] = (b << 16) | atomicAdd(&hcnt[b], 1u);
       }
       __syncthreads();
-      // hb = exclusive scan of hcnt
+      // hb = exclusive scan of hcnt; position p of bucket b goes to offset gb[b] + p
+      // (mod 2^32: gb[b] is the bucket's offset minus hb[b]); counts cleared for the next tile
+      u32 kept;
       {
-        constexpr u32 PER = F_MAX / NT_SC;
         u32 loc[PER], sum = 0;
 #pragma unroll
         for (u32 i = 0; i < PER; ++i) {
@@ -545,12 +553,16 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
           loc[i] = b < F ? hcnt[b] : 0u;
           sum += loc[i];
         }
-        u32 tot;
-        u32 pre = block_exclusive_scan<u32, NT_SC>(sum, &tot, s_warp);
+        u32 pre = block_exclusive_scan_1b<u32, NT_SC>(sum, &kept, s_warp);
 #pragma unroll
         for (u32 i = 0; i < PER; ++i) {
           const u32 b = tid * PER + i;
-          if (b < F) hb[b] = pre;
+          if (b < F) {
+            hb[b] = pre;
+            gb[b] = curv[i] - pre;
+            hcnt[b] = 0;
+          }
+          curv[i] += loc[i];
           pre += loc[i];
         }
       }
@@ -564,18 +576,16 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
         sb[p] = (u16)b;
       }
       __syncthreads();
-      const u32 kept = hb[F - 1] + hcnt[F - 1];
       for (u32 p = tid; p < kept; p += NT_SC) {
-        const u32 b = sb[p];
-        st_tuple(dst + cur[b] + (p - hb[b]), T[sidx[p]]);
+        const u32 off = gb[sb[p]] + p;
+        st_tuple(dst + off, T[sidx[p]]);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      for (u32 b = tid; b < F; b += NT_SC) {
-        cur[b] += hcnt[b];
-        hcnt[b] = 0;
-      }
-      __syncthreads();
+      // one buffer: the next tile's copy is issued before its wait, so every reader of
+      // this one must be done first.  Two buffers: the next tile's barrier (and the
+      // chunk's, after the last tile) comes before any write to this tile's buffer,
+      // counters or index arrays
+      if (STAGES == 1) __syncthreads();
     }
   }
 }
