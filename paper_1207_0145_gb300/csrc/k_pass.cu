@@ -692,7 +692,9 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
   u64* roff = reinterpret_cast<u64*>(rtab + 2 * RCH + 8);    // RCH run offsets
   for (u32 j0 = 0; j0 < T; j0 += RCH) {
     const u32 nr = T - j0 < RCH ? T - j0 : RCH;
-    __syncthreads();  // directory built; the previous chunk's readers are done
+    // directory built; the previous chunk's readers are done (with cdir, the caller's
+    // barrier after the placement comes right before the first chunk)
+    if (j0 || !cdir) __syncthreads();
     if (tid < nr) {
       const u32* w = fc.swin + 2ull * ((u64)item * fc.maxT + j0 + tid);
       wl[tid] = w[0];
@@ -884,6 +886,9 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
       publish_next();
       published = true;
     }
+    // the counting pass's counters, cleared while the copy is in flight (their last
+    // readers passed the barrier before this piece; the one after the wait orders it)
+    for (u32 b = tid; b < 2048u; b += NT) cnt[b] = 0;
     const bool ok = mbar_wait(&mbar, phase, SPIN_LIMIT);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) {
@@ -934,8 +939,6 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     // pass 1: counting sort on the low digit (order within a digit is free here)
     const u32 w1 = bits < 11u ? bits : 11u;
     const u32 F1 = 1u << w1;
-    for (u32 b = tid; b < F1; b += NT) cnt[b] = 0;
-    __syncthreads();
     u32 dr[IT];
 #pragma unroll
     for (u32 i = 0; i < IT; ++i) {
@@ -1031,8 +1034,10 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     } else {
       for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, tup[ia[i]]);
     }
-    __syncthreads();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // before the next piece's bulk copy
+    // every reader of this piece is done before the next bulk copy overwrites it: a
+    // barrier here before the segment's next piece, the loop's own before the next segment
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if ((u64)p0 + CAP < sg.len) __syncthreads();
     }
     if (failed) break;
   }
