@@ -65,7 +65,7 @@ void launch_pair_offsets(Job* jobs, u32 njobs, const u64* totals, const u64* til
 enum RmiKind : u32 {
   RMI_KIND_SAMPLE = 0,  // a sorted sample of S (the sub-plan's runs); fit points = its slice inside R's range
   RMI_KIND_RUNS = 1,    // evenly spaced positions of the job's sorted R runs
-  RMI_KIND_GIVEN = 2    // fit points written by the caller; range given in the task
+  RMI_KIND_GIVEN = 2    // fit points written by the caller; range given in the RmiTask
 };
 struct RmiTask {
   u64 fit_off;          // first fit point (keys / CDF values) of the model
