@@ -36,6 +36,8 @@ def lib():
             "oracle_worker_histograms": ([_p, _p, _u32, _u64, _u64, _u32, _u32, _p], ctypes.c_int),
             "oracle_run_counts": ([_p, _p, _u32, _u64, _u64, _u32, _u32, _p], ctypes.c_int),
             "oracle_log2_q16": ([_u64], _u64),
+            "oracle_log2_q16_big": ([_u64], _u64),
+            "oracle_log2_q16_prec": ([_u64, _u32], ctypes.c_int64),
             "oracle_splitters": ([_p, _p, _u32, _u32, _u32, _p, _p], _u32),
             "oracle_splitters_dp": ([_p, _p, _u32, _u32, _u32], _u64),
             "oracle_splitters_kind": ([_p, _p, _u32, _u32, _u32, _u32, _p, _p], _u32),
@@ -129,7 +131,18 @@ def run_counts(Rs, run_off, kmin, kmax, shift, nb):
 
 
 def log2_q16(n: int) -> int:
+    """floor(2^16 log2 n) (0 for n <= 1), the Q16 logarithm of the splitter cost."""
     return lib().oracle_log2_q16(n)
+
+
+def log2_q16_prec(n: int, F: int) -> int:
+    """The interval bit-by-bit method with F fractional bits alone; -1 if undecided."""
+    return lib().oracle_log2_q16_prec(n, F)
+
+
+def log2_q16_big(n: int) -> int:
+    """The same value straight from its definition, bitlen(n^65536) - 1 (slow)."""
+    return lib().oracle_log2_q16_big(n)
 
 
 def splitters(H, G, P: int, T: int, kind: int = 0):

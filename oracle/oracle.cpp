@@ -208,28 +208,161 @@ OEXPORT int oracle_run_counts(const otuple* Rs, const uint64_t* run_off, uint32_
   return 0;
 }
 
-/* The bit-by-bit binary logarithm: for 1 <= m < 2^11, floor(log2(m) * 2^16),
- * by normalising m to x in [1, 2) and squaring 16 times, each time taking one
- * fractional bit (x >= 2 -> bit 1, halve). */
-static uint64_t log2_q16_small(uint64_t m) {
-  const uint32_t k = bitlen64(m) - 1;
-  uint64_t x = m << (31 - k); /* Q31 in [2^31, 2^32) */
-  uint64_t r = (uint64_t)k << 16;
+/* The binary logarithm of the splitter cost, in Q16: L(n) = floor(2^16 log2 n)
+ * for n >= 2, and 0 for n <= 1.  Sec. 4.3 charges a partition of n tuples
+ * n log n for its sort; the library and this oracle evaluate that term as
+ * n * L(n) in integers, so both choose the same splitters bit for bit.
+ *
+ * Definition: 2^L(n) <= n^65536 < 2^(L(n)+1), i.e. L(n) = bitlen(n^65536) - 1.
+ * oracle_log2_q16_big computes exactly that with plain big-integer products. */
+typedef std::vector<uint32_t> bignum; /* little-endian base-2^32 digits */
+
+static bignum big_mul(const bignum& a, const bignum& b) {
+  bignum r(a.size() + b.size(), 0);
+  for (size_t i = 0; i < a.size(); ++i) {
+    uint64_t carry = 0;
+    for (size_t j = 0; j < b.size(); ++j) {
+      const uint64_t t = (uint64_t)a[i] * b[j] + r[i + j] + carry;
+      r[i + j] = (uint32_t)t;
+      carry = t >> 32;
+    }
+    r[i + b.size()] = (uint32_t)carry;
+  }
+  while (r.size() > 1 && r.back() == 0) r.pop_back();
+  return r;
+}
+
+OEXPORT uint64_t oracle_log2_q16_big(uint64_t n) {
+  if (n <= 1) return 0;
+  bignum x;
+  x.push_back((uint32_t)n);
+  if (n >> 32) x.push_back((uint32_t)(n >> 32));
+  for (int i = 0; i < 16; ++i) x = big_mul(x, x); /* n^(2^16) */
+  return 32ull * (x.size() - 1) + bitlen64(x.back()) - 1;
+}
+
+static bignum big_from(uint64_t v) {
+  bignum x(1, (uint32_t)v);
+  if (v >> 32) x.push_back((uint32_t)(v >> 32));
+  return x;
+}
+
+static bignum big_shl(const bignum& a, unsigned s) {
+  bignum r(s / 32, 0);
+  uint32_t carry = 0;
+  const unsigned b = s % 32;
+  for (uint32_t d : a) {
+    r.push_back(b ? (d << b) | carry : d);
+    carry = b ? d >> (32 - b) : 0;
+  }
+  if (carry) r.push_back(carry);
+  while (r.size() > 1 && r.back() == 0) r.pop_back();
+  return r;
+}
+
+/* floor(a / 2^s); *lost is set when a nonzero bit was shifted out */
+static bignum big_shr(const bignum& a, unsigned s, bool* lost) {
+  const size_t q = s / 32;
+  const unsigned b = s % 32;
+  *lost = false;
+  for (size_t i = 0; i < q && i < a.size(); ++i) *lost = *lost || a[i] != 0;
+  if (q < a.size() && b) *lost = *lost || (a[q] & ((1u << b) - 1)) != 0;
+  bignum r;
+  for (size_t i = q; i < a.size(); ++i) {
+    const uint64_t hi = i + 1 < a.size() ? a[i + 1] : 0;
+    r.push_back((uint32_t)((((uint64_t)hi << 32) | a[i]) >> b));
+  }
+  if (r.empty()) r.push_back(0);
+  while (r.size() > 1 && r.back() == 0) r.pop_back();
+  return r;
+}
+
+static bignum big_inc(bignum a) {
+  for (size_t i = 0; i < a.size(); ++i)
+    if (++a[i] != 0) return a;
+  a.push_back(1);
+  return a;
+}
+
+static int big_cmp(const bignum& a, const bignum& b) {
+  if (a.size() != b.size()) return a.size() < b.size() ? -1 : 1;
+  for (size_t i = a.size(); i-- > 0;)
+    if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
+  return 0;
+}
+
+/* The same value by the bit-by-bit method: with n = 2^k x, x in [1, 2),
+ * log2 n = k + log2 x, and squaring x doubles log2 x, so each squaring yields
+ * the next fractional bit (1 when the square reaches 2, which is then halved).
+ * x is carried as an interval [lo, hi] of numbers with F fractional bits that
+ * holds the true value at every step (squares rounded down for lo, up for hi),
+ * so every bit it takes is certain.  Returns -1 if some square's interval
+ * straddles 2, i.e. F bits cannot decide that bit. */
+static int64_t log2_q16_interval(uint64_t n, unsigned F) {
+  const uint32_t k = bitlen64(n) - 1;
+  bignum lo = big_shl(big_from(n), F - k), hi = lo; /* F >= 64: exact */
+  const bignum two = big_shl(big_from(2), F);
+  int64_t r = (int64_t)k << 16;
+  bool lost;
   for (int i = 15; i >= 0; --i) {
-    x = (x * x) >> 31;
-    if (x >= (1ull << 32)) { x >>= 1; r |= 1ull << i; }
+    const bignum sl = big_shr(big_mul(lo, lo), F, &lost);
+    bignum sh = big_shr(big_mul(hi, hi), F, &lost);
+    if (lost) sh = big_inc(sh);
+    if (big_cmp(sl, two) >= 0) {
+      r |= (int64_t)1 << i;
+      lo = big_shr(sl, 1, &lost);
+      hi = big_shr(sh, 1, &lost);
+      if (lost) hi = big_inc(hi);
+    } else if (big_cmp(sh, two) < 0) {
+      lo = sl;
+      hi = sh;
+    } else {
+      return -1;
+    }
   }
   return r;
 }
 
-/* log2(n) in Q16 for the cost model: the logarithm of n's leading 11 significant
- * bits (exact below 2^11, at most log2(1 + 2^-10) ~ 0.0014 low above), 0 for n <= 1. */
+/* L(n): first the interval method in 62 fractional bits with 128-bit products
+ * (cheap), then in 128, 256, ... bits on big integers, then the definition. */
 OEXPORT uint64_t oracle_log2_q16(uint64_t n) {
   if (n <= 1) return 0;
+  typedef unsigned __int128 u128;
   const uint32_t k = bitlen64(n) - 1;
-  if (k <= 10) return log2_q16_small(n);
-  const uint32_t s = k - 10;
-  return log2_q16_small(n >> s) + ((uint64_t)s << 16);
+  const uint64_t two = 1ull << 63; /* 2.0 in Q62 */
+  uint64_t lo, hi;
+  if (k <= 62) {
+    lo = hi = n << (62 - k); /* exact */
+  } else {
+    lo = n >> 1;
+    hi = lo + (n & 1);
+  }
+  uint64_t r = (uint64_t)k << 16;
+  for (int i = 15; i >= 0; --i) {
+    const u128 sl = ((u128)lo * lo) >> 62;
+    const u128 sh = ((u128)hi * hi + ((((u128)1) << 62) - 1)) >> 62;
+    if (sl >= two) {
+      r |= 1ull << i;
+      lo = (uint64_t)(sl >> 1);
+      hi = (uint64_t)((sh + 1) >> 1);
+    } else if (sh < two) {
+      lo = (uint64_t)sl;
+      hi = (uint64_t)sh;
+    } else {
+      for (unsigned F = 128; F <= 8192; F *= 2) {
+        const int64_t v = log2_q16_interval(n, F);
+        if (v >= 0) return (uint64_t)v;
+      }
+      return oracle_log2_q16_big(n);
+    }
+  }
+  return r;
+}
+
+/* The interval method at a given precision alone (tests). */
+OEXPORT int64_t oracle_log2_q16_prec(uint64_t n, uint32_t F) {
+  if (n <= 1) return 0;
+  return log2_q16_interval(n, F < 64 ? 64 : F);
 }
 
 /* split-relevant cost of a partition (Sec. 4.3), in units of 2^-16 tuples:

@@ -8,6 +8,7 @@
 - exhaustive DP for the splitter objective, and numpy's searchsorted / stable
   argsort for the window and run oracles.
 """
+import decimal
 import math
 import os
 
@@ -211,20 +212,126 @@ def test_fig10_splitters_prefix_sums_and_scatter():
     assert out[7:, 0].tolist() == [12, 18, 21, 9, 14, 16, 27]
 
 
+def test_fine_geometry_closed_form():
+    # bucket = (key - kmin) >> shift with shift = max(0, bitlen(kmax - kmin) - B): the top B bits
+    rng = np.random.default_rng(44)
+    for _ in range(500):
+        kmin = int(rng.integers(0, U64, dtype=np.uint64, endpoint=True))
+        kmax = kmin + int(rng.integers(0, U64 - kmin + 1, dtype=np.uint64)) if kmin < U64 else U64
+        B = int(rng.integers(1, 13))
+        nb, shift = oracle.fine_geometry(kmin, kmax, B)
+        assert shift == max(0, (kmax - kmin).bit_length() - B)
+        assert nb == ((kmax - kmin) >> shift) + 1 and nb <= (1 << B)
+
+
+def test_run_counts_against_searchsorted_and_brute_force():
+    # the run side's tuples per fine bucket: its CDF at the bucket bounds (Sec. 4.1, 4.3),
+    # read here by searchsorted in every sorted run and, on small inputs, by a plain loop
+    rng = np.random.default_rng(45)
+    for case in range(60):
+        n = int(rng.integers(0, 4000))
+        T = int(rng.integers(1, 10))
+        domain = int(rng.choice([3, 100, 5000, 1 << 40, 1 << 64]))
+        keys = (rng.integers(0, U64, n, dtype=np.uint64, endpoint=True) if domain == 1 << 64
+                else rng.integers(0, domain, n, dtype=np.uint64))
+        if n and case % 3 == 0:
+            keys[rng.integers(0, n, max(1, n // 20))] = rng.choice(np.array([0, U64, U64 - 1], dtype=np.uint64))
+        off = np.array([(n * j) // T for j in range(T + 1)], dtype=np.uint64)
+        Rs = np.zeros((n, 2), dtype=np.uint64)
+        for j in range(T):
+            a, b = int(off[j]), int(off[j + 1])
+            Rs[a:b, 0] = np.sort(keys[a:b])
+        if n == 0:
+            kmin, kmax = 5, 9
+        elif case % 2:
+            kmin, kmax = int(keys.min()), int(keys.max())
+        else:  # a narrower range: keys outside it are not counted
+            lo_, hi_ = sorted(int(x) for x in rng.choice(keys, 2))
+            kmin, kmax = lo_, hi_
+        B = int(rng.integers(1, 13))
+        nb, shift = oracle.fine_geometry(kmin, kmax, B)
+        G = oracle.run_counts(Rs, off, kmin, kmax, shift, nb)
+        want = np.zeros(nb, dtype=np.int64)
+        for j in range(T):
+            run = Rs[int(off[j]):int(off[j + 1]), 0]
+            # rank of each bound in the run; the last bucket ends after kmax
+            lo = [int(np.searchsorted(run, np.uint64(kmin + (f << shift)), side="left")) for f in range(nb)]
+            lo.append(int(np.searchsorted(run, np.uint64(kmax), side="right")))
+            want += np.diff(np.array(lo, dtype=np.int64))
+        assert (G.astype(np.int64) == want).all(), case
+        if n <= 600:
+            brute = [0] * nb
+            for k in Rs[:, 0].tolist():
+                if kmin <= k <= kmax:
+                    brute[(k - kmin) >> shift] += 1
+            assert G.tolist() == brute, case
+
+
 # ------------------------------------------------------------------ phase 2: cost and solver
 
 
-def test_log2_q16_against_math():
-    for n in list(range(1, 3000)) + [2 ** k for k in range(1, 63)] + [3 ** 20, (1 << 40) - 1, 12345678901]:
-        exact = math.log2(n) * 65536
-        got = oracle.log2_q16(n)
-        # floor of the exact value below 2^11; leading 11 significant bits above
-        slack = 1.0 if n < (1 << 11) else 65536 * math.log2(1 + 2 ** -10) + 1.0
-        assert got <= exact + 1e-6 and exact - got < slack + 1e-6, n
-        if n < (1 << 11):
-            assert got == math.floor(exact + 1e-9), n
-        if n & (n - 1) == 0:
-            assert got == int(math.log2(n)) * 65536
+def exact_log2_q16(n: int) -> int:
+    """floor(2^16 log2 n) from an 80-digit natural logarithm (Python's decimal rounds
+    ln correctly); the fraction is asserted far from an integer, so the floor is certain."""
+    if n <= 1:
+        return 0
+    if n & (n - 1) == 0:
+        return (n.bit_length() - 1) << 16
+    with decimal.localcontext() as ctx:
+        ctx.prec = 80
+        v = decimal.Decimal(n).ln() / decimal.Decimal(2).ln() * 65536
+        f = int(v)
+        frac = v - f
+        assert decimal.Decimal("1e-60") < frac < 1 - decimal.Decimal("1e-60"), n
+    return f
+
+
+def boundary_n(L: int) -> int:
+    """The smallest integer n with 2^16 log2 n >= L: where the floor steps to L."""
+    with decimal.localcontext() as ctx:
+        ctx.prec = 80
+        return int((decimal.Decimal(2) ** (decimal.Decimal(L) / 65536)).to_integral_value(decimal.ROUND_CEILING))
+
+
+def test_log2_q16_is_the_exact_floor():
+    # the Q16 logarithm of the splitter cost is floor(2^16 log2 n), exactly (Sec. 4.3's n log n)
+    rng = np.random.default_rng(41)
+    ns = list(range(0, 1 << 13)) + [2 ** k + d for k in range(1, 64) for d in (-1, 0, 1)]
+    ns += [int(x) for x in rng.integers(2, U64, 3000, dtype=np.uint64, endpoint=True)]
+    ns += [int(x) >> int(s) for x, s in zip(rng.integers(2, U64, 2000, dtype=np.uint64), rng.integers(0, 62, 2000))]
+    for n in ns:
+        assert oracle.log2_q16(n) == exact_log2_q16(n), n
+
+
+def test_log2_q16_at_the_steps_of_the_floor():
+    # the n where floor(2^16 log2 n) changes: the hardest inputs for a finite-precision method
+    rng = np.random.default_rng(42)
+    for L in [int(x) for x in rng.integers(65536, 64 * 65536, 3000)] + [65536 * k + 1 for k in range(1, 64)]:
+        n = boundary_n(L)
+        if n > U64:
+            continue
+        # n is the first integer at or past the step to L (small n pass several steps at once)
+        assert oracle.log2_q16(n) == exact_log2_q16(n) >= L, (L, n)
+        assert oracle.log2_q16(n - 1) == exact_log2_q16(n - 1) < L, (L, n)
+        if n > 1 << 17:  # consecutive integers there differ by less than one step
+            assert oracle.log2_q16(n) == L, (L, n)
+
+
+def test_log2_q16_invariants():
+    rng = np.random.default_rng(43)
+    for n in [int(x) for x in rng.integers(2, 1 << 32, 2000)]:
+        a, b = oracle.log2_q16(n), oracle.log2_q16(n * n)
+        assert b in (2 * a, 2 * a + 1), n  # floor(2x) is 2 floor(x) or one more
+        assert oracle.log2_q16(2 * n) == a + 65536, n  # doubling adds exactly one
+        assert oracle.log2_q16(n + 1) >= a
+    for k in range(64):
+        assert oracle.log2_q16(1 << k) == k << 16
+
+
+def test_log2_q16_big_integer_definition():
+    # the definition the interval method falls back to: bitlen(n^65536) - 1
+    for n in (2, 3, 5, 7, 10, 100, 255, 1000, 4097):
+        assert oracle.log2_q16_big(n) == exact_log2_q16(n) == oracle.log2_q16(n), n
 
 
 def test_splitters_optimal_against_exhaustive_dp():
