@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--parts", type=int, default=0, help="P, partitions of S (0 = automatic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-arms", action="store_true", help="skip the learned and batched comparison arms")
     ap.add_argument("--cpu-sample", type=int, default=16, help="CPU baseline runs 1/this of the workload")
     ap.add_argument("--splitter", default="hist", choices=["hist", "learned", "equi-height"])
     ap.add_argument("--fine-bits", type=int, default=0, help="B, fine histogram bits of S (0 = 12)")
@@ -254,6 +255,76 @@ def recorded_traffic(kernel: str, config: str):
         return None
 
 
+def traffic_per_tuple(config: str):
+    """DRAM bytes per (R + S) tuple of one whole join, summed over the kernel families
+    of a committed ncu traffic record, if every source file it names is unchanged."""
+    path = os.path.join(ROOT, "profiles", f"step_traffic_{config}.txt")
+    try:
+        vals = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.lstrip().startswith("#"):
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        files = vals.get("sources", "").split() or None
+        if vals.get("source_hash") != kernel_source_hash(files):
+            return None
+        return float(vals["dram_bytes_per_tuple"]), vals.get("measured_on", "")
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def host_numa_of(ptr: int):
+    """NUMA node(s) holding the pages of the host mapping that contains ptr (Linux numa_maps)."""
+    try:
+        best = None
+        with open("/proc/self/numa_maps") as f:
+            for line in f:
+                parts = line.split()
+                a = int(parts[0], 16)
+                if a <= ptr and (best is None or a > best[0]):
+                    best = (a, [p for p in parts[1:] if p[:1] == "N" and "=" in p])
+        return " ".join(best[1]) if best else None
+    except (OSError, ValueError):
+        return None
+
+
+def gpu_host_numa(dev: int):
+    """The host NUMA node closest to the GPU (cudaDevAttrHostNumaId), or None."""
+    import ctypes
+
+    for name in ("libcudart.so", "libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            rt = ctypes.CDLL(name)
+            break
+        except OSError:
+            rt = None
+    if rt is None:
+        return None
+    v = ctypes.c_int(-1)
+    return v.value if rt.cudaDeviceGetAttribute(ctypes.byref(v), 134, dev) == 0 else None
+
+
+def measure_h2d(host, dev, stream, nbytes: int = 4 << 30, reps: int = 3):
+    """Host-to-device GB/s of plain copies from the pinned buffer `host` (best of reps)."""
+    import torch
+
+    n = min(nbytes, host.numel() * host.element_size())
+    src = host.view(torch.uint8).reshape(-1)[:n]
+    dst = torch.empty(n, dtype=torch.uint8, device=dev)
+    best = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+        e1.synchronize()
+        best = max(best, n / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del dst
+    return best
+
+
 def cpu_baseline(w, div: int):
     import oracle
 
@@ -299,6 +370,78 @@ def aggregate_replicas(ms_local: float, units_local: int, dist=None, device="cpu
         dist.all_reduce(u, op=dist.ReduceOp.SUM)
         ms, units = float(t.item()), int(u.item())
     return ms, units / (ms / 1e3) / 1e6
+
+
+# ------------------------------------------------------------------ comparison arms
+
+ARM_WARMUP, ARM_STEPS = 3, 5
+
+
+def time_joins(plan, R, S, stream, steps: int, warmup: int, local: int):
+    """(ms per join, results, clock summary) of `steps` joins after `warmup` untimed ones."""
+    import torch
+
+    for _ in range(warmup):
+        plan.join(R, S)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [plan.join(R, S) for _ in range(steps)]
+        e1.record(stream)
+        e1.synchronize()
+    return e0.elapsed_time(e1) / steps, res, clk.summary()
+
+
+def arm_modes(config: str, modes, seed: int, dev, local: int):
+    """One workload joined under each of `modes` (label, plan options), the first being
+    the plain form; every result checked against the generator's closed form."""
+    import torch
+
+    import oracle
+    from paper_1207_0145_gb300 import Plan
+
+    w = workload(config, seed)
+    units = w.n_r + w.n_s
+    expect = {}
+    th = threading.Thread(target=lambda: expect.setdefault("v", oracle.closed_form(w)), daemon=True)
+    th.start()
+    stream = torch.cuda.Stream(device=dev)
+    R = torch.empty((w.n_r, 2), dtype=torch.int64, device=dev)
+    S = torch.empty((w.n_s, 2), dtype=torch.int64, device=dev)
+    with torch.cuda.stream(stream):
+        w.fill_r_device(R.data_ptr(), stream.cuda_stream)
+        w.fill_s_device(S.data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+    out = {"workload": config, "n_r": w.n_r, "n_s": w.n_s}
+    results = []
+    for label, opts in modes:
+        plan = Plan(w.n_r, w.n_s, stream=stream.cuda_stream, **opts)
+        if label == modes[0][0]:
+            th.join()  # the host's expected result is ready before the first timed joins
+        ms, res, clk = time_joins(plan, R, S, stream, ARM_STEPS, ARM_WARMUP, local)
+        plan.set_flags(timing=True)
+        plan.join(R, S)
+        st = plan.stats()
+        plan.close()
+        results += res
+        out[label] = {"ms_per_step": ms, "value": units / (ms / 1e3) / 1e6, "unit": UNIT, "steps": ARM_STEPS,
+                      "warmup": ARM_WARMUP, "options": opts, "clocks": clk,
+                      "imbalance": st["imbalance"], "partitions_s": st["partitions_s"],
+                      "levels": [st["levels_r"], st["levels_s"]], "ms_learn": round(st["ms_learn"], 3),
+                      "search_probes": st["search_probes"], "part_probes": st["part_probes"],
+                      "phases_ms": {k: round(st[k], 3) for k in ("ms_sort_runs", "ms_splitters", "ms_scatter",
+                                                                 "ms_sort_partitions", "ms_search", "ms_join")}}
+    th.join()
+    want = expect.get("v")
+    out["parity"] = all(r == want for r in results) if want is not None else None
+    out["result"] = list(results[-1])
+    a, b = modes[0][0], modes[1][0]
+    out["speedup"] = out[a]["ms_per_step"] / out[b]["ms_per_step"]
+    out["what"] = f"{b} vs {a} on the same inputs; speedup = ms({a}) / ms({b})"
+    del R, S
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------ reference arm
@@ -474,14 +617,53 @@ def run_ours(args):
         f1.synchronize()
         barrier()
         ems, evalue = aggregate_replicas(f0.elapsed_time(f1) / args.steps, units, dist, dev)
+        # the host link as this run saw it, right after the timed steps: plain copies from the
+        # same pinned buffer, and where that buffer's pages and the GPU sit
+        h2d = measure_h2d(Sh, dev, stream)
         e2e = {"value": evalue, "unit": UNIT, "h2d_bytes_per_step": units * 16,
-               "d2h_bytes_per_step": 16, "ms_per_step": ems}
+               "d2h_bytes_per_step": 16, "ms_per_step": ems,
+               "h2d_gbs_measured": round(h2d, 1),
+               "copy_bound_ms": round(units * 16 / (h2d * 1e9) * 1e3, 2),
+               "over_copy_bound": round(ems / (units * 16 / (h2d * 1e9) * 1e3), 3),
+               "host_numa_pinned": host_numa_of(Sh.data_ptr()), "gpu_host_numa": gpu_host_numa(local),
+               "what": "mpsm_join_host: R and S copied from pinned host memory every step, then joined; "
+                       "copy_bound_ms = the step's input bytes at the measured host-to-device rate"}
+        del Rh, Sh
 
     balance = partition_balance(plan, st) if args.splitter != "learned" else None
+    plan.close()
+    R = S = pairs = None  # noqa: F841 (the device inputs are freed before the comparison arms)
+    torch.cuda.empty_cache()
     cpu = cpu_mt = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, args.cpu_sample)
         cpu_mt = cpu_pmpsm(w, args.cpu_sample)
+    # the whole step's DRAM traffic from the committed per-kernel ncu record, over the step time
+    tr = traffic_per_tuple(args.config)
+    hbm_sched = None
+    if tr is not None:
+        step_bytes = tr[0] * (w.n_r + w.n_s)
+        hbm_sched = {"dram_bytes_per_step": step_bytes, "achieved": step_bytes / (ms / 1e3) / 1e9,
+                     "peak": peak, "frac": step_bytes / (ms / 1e3) / 1e9 / peak, "unit": "GB/s",
+                     "source": f"profiles/step_traffic_{args.config}.txt ({tr[1]})"}
+    # learned and batched forms against the plain form (the metric's comparison), default run only
+    arms = None
+    if ws == 1 and not args.no_arms and args.config == "plain-400M-1600M":
+        arms = {
+            "zipf": arm_modes("zipf0.9-200M-800M", [("hist", {"splitter_mode": 0}), ("learned", {"splitter_mode": 1})],
+                              args.seed, dev, local),
+            "sparse": arm_modes("sparse-1600M-1600M", [("binary", {"search_mode": 0}), ("learned", {"search_mode": 1})],
+                                args.seed, dev, local),
+        }
+        b = batch_measure(args.seed, ARM_STEPS, ARM_WARMUP, True, dev, local)
+        arms["batch"] = {"workload": BATCH_CONFIG, "n_r": b["n_r"], "n_s": b["n_s"], "jobs": b["jobs"],
+                         "graph": {"ms_per_step": b["ms"], "value": b["value"], "unit": UNIT, "clocks": b["clocks"],
+                                   "tuning": b["tuning"], "autotune_ms": b["autotune_ms"]},
+                         "sequential": {"ms_per_step": b["seq_ms"], "value": b["seq_value"], "unit": UNIT,
+                                        "clocks": b["seq_clocks"]},
+                         "parity": b["parity"], "speedup": b["seq_ms"] / b["ms"],
+                         "what": "one CUDA-graph launch of all 256 jobs vs 256 mpsm_join calls; "
+                                 "speedup = ms(sequential) / ms(graph)"}
 
     if rank == 0:
         line = {
@@ -493,7 +675,7 @@ def run_ours(args):
                        "l2": "inputs (33.5 GB at the default size) far exceed L2; no flush",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "parity": parity, "result": list(results[-1]),
-            "roofline": roof, "roofline_step": roof_step,
+            "roofline": roof, "roofline_step": roof_step, "hbm_frac_schedule": hbm_sched, "arms": arms,
             "cpu_baseline": cpu, "cpu_pmpsm": cpu_mt, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches_per_step * args.steps,
             "phases_ms": {k: round(st[k], 3) for k in ("ms_sort_runs", "ms_splitters", "ms_scatter",
@@ -508,13 +690,12 @@ def run_ours(args):
                                            "search_probes", "search_err", "part_max")},
         }
         print(json.dumps(line), flush=True)
-    plan.close()
     if dist:
         dist.destroy_process_group()
     return 0
 
 
-def run_batch(args):
+def batch_measure(seed: int, steps: int, warmup: int, tune: bool, dev, local: int, dist=None):
     """256 independent joins of uneven sizes in one CUDA-graph launch, against the
     same 256 joins run one after another through the single-join entry point."""
     import torch
@@ -523,15 +704,7 @@ def run_batch(args):
     import oracle
     from paper_1207_0145_gb300 import Plan
 
-    ws, rank, local = dist_env()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    jobs = gen.batch_jobs(256, seed=args.seed + rank)
+    jobs = gen.batch_jobs(256, seed=seed)
     tot_r = sum(j.n_r for j in jobs)
     tot_s = sum(j.n_s for j in jobs)
     units = tot_r + tot_s
@@ -553,9 +726,9 @@ def run_batch(args):
     stream.synchronize()
     plan = Plan(tot_r, tot_s, max_jobs=len(jobs), stream=stream.cuda_stream)
     tuning, tune_ms = None, None
-    if not args.no_tune:
+    if tune:
         tuning, tune_ms = plan.autotune(pairs, reps=1)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         got = plan.join_batch(pairs)
     th.join()  # the expected results are computed on the host cores before the timed steps
     torch.cuda.synchronize()
@@ -564,44 +737,64 @@ def run_batch(args):
     with ClockSampler(local) as clk:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             got = plan.join_batch(pairs)
         e1.record(stream)
         e1.synchronize()
     if dist:
         dist.barrier()
-    ms, value = aggregate_replicas(e0.elapsed_time(e1) / args.steps, units, dist, dev)
+    ms, value = aggregate_replicas(e0.elapsed_time(e1) / steps, units, dist, dev)
     launches = plan.stats()["launches"]
     # the same jobs one after another through mpsm_join (plain single-join path)
     plan.set_tuning()
     for r, s_ in pairs[:4]:
         plan.join(r, s_)
     torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    seq = [plan.join(r, s_) for r, s_ in pairs]
-    f1.record(stream)
-    f1.synchronize()
+    with ClockSampler(local) as clk2:
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        seq = [plan.join(r, s_) for r, s_ in pairs]
+        f1.record(stream)
+        f1.synchronize()
     seq_ms = f0.elapsed_time(f1)
-    th.join()
     want = expect.get("v")
     res = list(zip(*got))
     parity = (res == want and seq == want) if want is not None else None
+    plan.close()
+    del R, S, pairs
+    torch.cuda.empty_cache()
+    return {"ms": ms, "value": value, "units": units, "jobs": len(jobs), "n_r": tot_r, "n_s": tot_s,
+            "tuning": tuning, "autotune_ms": tune_ms, "parity": parity, "launches": launches,
+            "clocks": clk.summary(), "seq_ms": seq_ms, "seq_value": units / (seq_ms / 1e3) / 1e6,
+            "seq_clocks": clk2.summary()}
+
+
+def run_batch(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    b = batch_measure(args.seed + rank, args.steps, args.warmup, not args.no_tune, dev, local, dist)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic",
-        "config": {"workload": BATCH_CONFIG, "jobs": len(jobs), "n_r": tot_r, "n_s": tot_s, "tuple_bytes": 16,
-                   "tuning": tuning, "l2": "inputs far exceed L2; no flush",
+        "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": b["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": BATCH_CONFIG, "jobs": b["jobs"], "n_r": b["n_r"], "n_s": b["n_s"], "tuple_bytes": 16,
+                   "tuning": b["tuning"], "l2": "inputs far exceed L2; no flush",
                    "parallelism": "replicas" if ws > 1 else "single"},
-        "parity": parity, "gpu_launches": launches * args.steps,
-        "sequential": {"value": units / (seq_ms / 1e3) / 1e6, "ms": seq_ms,
+        "parity": b["parity"], "gpu_launches": b["launches"] * args.steps,
+        "sequential": {"value": b["seq_value"], "ms": b["seq_ms"],
                        "what": "the same 256 joins one after another through mpsm_join"},
-        "autotune_ms": tune_ms, "clocks": clk.summary(),
+        "autotune_ms": b["autotune_ms"], "clocks": b["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if dist:
         dist.destroy_process_group()
     return 0

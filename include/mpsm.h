@@ -77,7 +77,13 @@ enum {
   MPSM_FLAG_UNFUSED = 4u          /* mpsm_join / mpsm_join_batch: run phase 3 and phase 4 as separate
                                      kernels (sorted S written back, then searched and joined)
                                      instead of joining each S segment while its sort still holds
-                                     it in shared memory; same results                            */
+                                     it in shared memory; same results                            */,
+  MPSM_FLAG_BOUNDS_TEST = 8u      /* test only: before phase 3's final in-shared-memory sorts, narrow
+                                     the recorded key bounds of one S segment so that its largest
+                                     key lies beyond them; the sort kernels then report
+                                     MPSM_DEVERR_BOUNDS and the call returns MPSM_ERR_DEVICE.  It
+                                     exercises the kernels' own check of those bounds; no access
+                                     leaves its array                                          */
 };
 
 typedef struct {
@@ -121,7 +127,15 @@ int mpsm_join(mpsm_plan_t* plan, const mpsm_tuple_t* R, uint64_t nR, const mpsm_
               uint64_t nS, uint64_t* out_count, uint64_t* out_checksum, mpsm_pairs_t* opt_pairs);
 
 /* Same as mpsm_join with R and S in HOST memory (pinned memory copies fastest):
- * the plan copies them to device staging buffers on its stream first. */
+ * the plan copies them to device staging buffers (allocated on the first call)
+ * and joins them there.  The run side is copied first and sorted while the
+ * partitioned side is still on the host link.  When the partitioned side holds at
+ * least 2^28 tuples (and no learned mode or MPSM_FLAG_UNFUSED is set), it is copied
+ * in pieces of 2^27 tuples (more once 64 pieces would not cover it), and each piece
+ * is range-partitioned, sorted and joined against the sorted runs while the next
+ * one is in flight; the result is the same, since the join sums over the pairs of
+ * each piece.  mpsm_plan_stats then describes the last piece's partitioning.
+ * Synchronises the plan's stream. */
 int mpsm_join_host(mpsm_plan_t* plan, const mpsm_tuple_t* R_host, uint64_t nR,
                    const mpsm_tuple_t* S_host, uint64_t nS, uint64_t* out_count,
                    uint64_t* out_checksum);
@@ -339,6 +353,18 @@ int mpsm_plan_device_errors(const mpsm_plan_t* plan, uint32_t* flags);
  * Returns MPSM_ERR_DEVICE with *flags = MPSM_DEVERR_WAIT_TIMEOUT; the CUDA context
  * stays usable.  Allocates and frees 4 bytes of device memory.  Synchronises. */
 int mpsm_selftest_wait_timeout(void* cuda_stream, uint32_t spin_limit, uint32_t* flags);
+
+/* Self-test of the splitter cost's logarithm.  Sec. 4.3 charges a partition of n
+ * tuples n log n for its sort; the library evaluates that term as
+ * n * floor(2^16 log2 n) in integers, so its splitters are reproducible bit for
+ * bit.  For each of the `count` values n[i] (DEVICE array of uint64, 8-byte
+ * aligned) this writes out[i] (DEVICE, count values) = floor(2^16 log2 n[i]), 0 for
+ * n[i] <= 1, computed exactly as k_splitters computes it.  wide != 0 takes the
+ * 126-bit path for every value (the library itself takes it only when the 62-bit
+ * path cannot decide a bit); UINT64_MAX marks a value that the path used could not
+ * decide.  Runs on cuda_stream (NULL = the default stream) and synchronises it.
+ * Returns MPSM_ERR_INVALID_ARG for null or misaligned arrays. */
+int mpsm_selftest_log2_q16(const uint64_t* n, uint64_t count, uint64_t* out, uint32_t wide, void* cuda_stream);
 
 /* ---- allocation-free run sort ------------------------------------------------
  * The paper has no counterpart: this entry point exists for callers that must

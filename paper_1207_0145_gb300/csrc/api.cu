@@ -81,6 +81,9 @@ struct mpsm_plan {
   cudaStream_t st_copy = nullptr;
   cudaEvent_t ev_run_copied = nullptr, ev_part_copied = nullptr;
   bool part_copy_pending = false;
+  // piecewise host join: one event per piece of the partitioned side that has landed
+  static constexpr u32 MAX_PIECES = 64;
+  cudaEvent_t ev_piece[MAX_PIECES] = {};
   u32 device_errors = 0;            // MPSM_DEVERR_* bits read back by the last call
   // job / run tables
   Job *d_jobs = nullptr, *h_jobs = nullptr;
@@ -653,9 +656,17 @@ int phase_scatter(mpsm_plan* p) {
   return MPSM_OK;
 }
 
+// MPSM_FLAG_BOUNDS_TEST: one final S segment's recorded bounds made inexact
+int narrow_bounds_test(mpsm_plan* p) {
+  if (p->opt.flags & MPSM_FLAG_BOUNDS_TEST) launch_narrow_bounds_test(p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, p->st);
+  CK(cudaGetLastError());
+  return MPSM_OK;
+}
+
 int phase_sort_parts(mpsm_plan* p) {
   int rc = run_levels(p, W_XS, W_XS, &p->levels_s);
   if (rc) return rc;
+  if ((rc = narrow_bounds_test(p))) return rc;
   rc = final_sort(p, W_XS);
   if (rc) return rc;
   record(p, EV_SORTS);
@@ -672,6 +683,7 @@ int read_err(mpsm_plan* p);
 int phase_sort_join(mpsm_plan* p) {
   int rc = run_levels(p, W_XS, W_XS, &p->levels_s, true);
   if (rc) return rc;
+  if ((rc = narrow_bounds_test(p))) return rc;
   record(p, EV_SORTS);
   u64 totR = 0;
   for (u32 i = 0; i < p->njobs; ++i) totR += p->h_jobs[i].nR;
@@ -844,6 +856,8 @@ MPSM_API void mpsm_plan_destroy(mpsm_plan_t* p) {
   }
   if (p->ev_run_copied) cudaEventDestroy(p->ev_run_copied);
   if (p->ev_part_copied) cudaEventDestroy(p->ev_part_copied);
+  for (u32 i = 0; i < mpsm_plan::MAX_PIECES; ++i)
+    if (p->ev_piece[i]) cudaEventDestroy(p->ev_piece[i]);
   if (p->own_stream && p->st) cudaStreamDestroy(p->st);
   delete p;
 }
@@ -1079,6 +1093,58 @@ MPSM_API int mpsm_join(mpsm_plan_t* p, const mpsm_tuple_t* R, uint64_t nR, const
   return rc;
 }
 
+// tuples of the partitioned side per piece of a host-buffer join (2 GiB)
+constexpr u64 HOST_PIECE = 1ull << 27;
+
+// Host-buffer join with the partitioned side copied in pieces.  The run side is
+// copied and sorted first; then piece i is range-partitioned, sorted and joined
+// against the sorted runs while piece i + 1 is still on the host link.  Exact for
+// any split of the partitioned side: each pair (r, s) is found by the piece that
+// holds s, and count and checksum are sums over the pairs.  The join waits only
+// for the last piece's copy, so the step ends one piece's work after the link.
+static int join_host_pieces(mpsm_plan* p, Tuple* run_dst, const Tuple* run_src, u64 n_run, Tuple* part_dst,
+                            const Tuple* part_src, u64 n_part, uint64_t* out_count, uint64_t* out_checksum) {
+  u64 piece = HOST_PIECE;
+  while ((n_part + piece - 1) / piece > mpsm_plan::MAX_PIECES) piece *= 2;
+  const u32 K = (u32)((n_part + piece - 1) / piece);
+  for (u32 i = 0; i < K; ++i)
+    if (!p->ev_piece[i]) CK(cudaEventCreateWithFlags(&p->ev_piece[i], cudaEventDisableTiming));
+  if (n_run) CK(cudaMemcpyAsync(run_dst, run_src, n_run * sizeof(Tuple), cudaMemcpyHostToDevice, p->st));
+  CK(cudaEventRecord(p->ev_run_copied, p->st));  // also after every earlier reader of the staging buffers
+  CK(cudaStreamWaitEvent(p->st_copy, p->ev_run_copied, 0));
+  for (u32 i = 0; i < K; ++i) {
+    const u64 a = (u64)i * piece, len = std::min(piece, n_part - a);
+    CK(cudaMemcpyAsync(part_dst + a, part_src + a, len * sizeof(Tuple), cudaMemcpyHostToDevice, p->st_copy));
+    CK(cudaEventRecord(p->ev_piece[i], p->st_copy));
+  }
+  CK(cudaEventRecord(p->ev_part_copied, p->st_copy));
+  p->part_copy_pending = false;  // each piece waits for its own copy
+  int rc = MPSM_OK;
+  do {
+    Jobh j{run_dst, part_dst, n_run, std::min(piece, n_part)};
+    p->fused = true;
+    if ((rc = setup_jobs(p, &j, 1))) break;
+    if ((rc = phase_runs(p))) break;
+    for (u32 i = 0; i < K && rc == MPSM_OK; ++i) {
+      const u64 a = (u64)i * piece, len = std::min(piece, n_part - a);
+      if (i) {
+        launch_set_part(p->d_jobs, p->d_split, part_dst + a, len, p->st);
+        if ((rc = cuda_status(cudaGetLastError()))) break;
+        p->h_jobs[0].S = part_dst + a;
+        p->h_jobs[0].nS = len;
+      }
+      if ((rc = cuda_status(cudaStreamWaitEvent(p->st, p->ev_piece[i], 0)))) break;
+      if ((rc = phase_learn(p)) || (rc = phase_splitters(p)) || (rc = phase_scatter(p)) ||
+          (rc = phase_sort_join(p)))
+        break;
+    }
+    if (rc == MPSM_OK) rc = fused_results(p, out_count, out_checksum);
+  } while (false);
+  // nothing later on the plan's stream may overlap the copies, on the error paths too
+  CK(cudaStreamWaitEvent(p->st, p->ev_part_copied, 0));
+  return rc;
+}
+
 MPSM_API int mpsm_join_host(mpsm_plan_t* p, const mpsm_tuple_t* R_host, uint64_t nR, const mpsm_tuple_t* S_host,
                             uint64_t nS, uint64_t* out_count, uint64_t* out_checksum) {
   if (!p) return MPSM_ERR_INVALID_ARG;
@@ -1099,6 +1165,9 @@ MPSM_API int mpsm_join_host(mpsm_plan_t* p, const mpsm_tuple_t* R_host, uint64_t
   const void* run_src = rev ? static_cast<const void*>(S_host) : static_cast<const void*>(R_host);
   const void* part_src = rev ? static_cast<const void*>(R_host) : static_cast<const void*>(S_host);
   const u64 n_run = rev ? nS : nR, n_part = rev ? nR : nS;
+  if (n_part >= 2 * HOST_PIECE && !split_learned(p) && !search_learned(p) && !(p->opt.flags & MPSM_FLAG_UNFUSED))
+    return join_host_pieces(p, run_dst, static_cast<const Tuple*>(run_src), n_run, part_dst,
+                            static_cast<const Tuple*>(part_src), n_part, out_count, out_checksum);
   if (n_run) CK(cudaMemcpyAsync(run_dst, run_src, n_run * sizeof(Tuple), cudaMemcpyHostToDevice, p->st));
   CK(cudaEventRecord(p->ev_run_copied, p->st));  // also after every earlier reader of the staging buffers
   CK(cudaStreamWaitEvent(p->st_copy, p->ev_run_copied, 0));
@@ -1265,7 +1334,8 @@ MPSM_API int mpsm_plan_stats(mpsm_plan_t* p, mpsm_stats_t* s) {
 
 MPSM_API int mpsm_plan_set_flags(mpsm_plan_t* p, uint32_t flags) {
   if (!p) return MPSM_ERR_INVALID_ARG;
-  if (flags & ~(u32)(MPSM_FLAG_TIMING | MPSM_FLAG_KERNEL_TIMING | MPSM_FLAG_UNFUSED)) return MPSM_ERR_INVALID_ARG;
+  if (flags & ~(u32)(MPSM_FLAG_TIMING | MPSM_FLAG_KERNEL_TIMING | MPSM_FLAG_UNFUSED | MPSM_FLAG_BOUNDS_TEST))
+    return MPSM_ERR_INVALID_ARG;
   if ((flags & MPSM_FLAG_TIMING) && !p->ev[0])
     for (auto& e : p->ev)
       if (cudaEventCreate(&e) != cudaSuccess) return MPSM_ERR_CUDA;
@@ -1390,6 +1460,19 @@ MPSM_API int mpsm_selftest_wait_timeout(void* stream, uint32_t spin_limit, uint3
   if (e != cudaSuccess) return MPSM_ERR_CUDA;
   *flags = h;
   return h ? MPSM_ERR_DEVICE : MPSM_OK;
+}
+
+MPSM_API int mpsm_selftest_log2_q16(const uint64_t* n, uint64_t count, uint64_t* out, uint32_t wide, void* stream) {
+  if (count && (!n || !out)) return MPSM_ERR_INVALID_ARG;
+  if ((((uintptr_t)n) | ((uintptr_t)out)) & 7u) return MPSM_ERR_INVALID_ARG;
+  if (count == 0) return MPSM_OK;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MPSM_ERR_CUDA;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  launch_log2_selftest(reinterpret_cast<const u64*>(n), count, reinterpret_cast<u64*>(out), wide, st, nsm > 0 ? nsm : 1);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return MPSM_ERR_CUDA;
+  return MPSM_OK;
 }
 
 MPSM_API const char* mpsm_strerror(int status) {

@@ -679,9 +679,15 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
   const u32 dsh = rbits > DB ? rbits - DB : 0u;
   const u32 nbk = (u32)((mx - mn) >> dsh) + 1u;
   if (!cdir) {
+    // the caller checked every key against [mn, mx]; the clamp keeps the writes inside
+    // the nbk + 1 directory entries regardless
+    auto bucket = [&](u32 i) {
+      const u64 b = (tup[ia[i]].key - mn) >> dsh;
+      return b < (u64)nbk ? (u32)b : nbk - 1u;
+    };
     for (u32 i = tid; i < n; i += NT) {
-      const u32 b = (u32)((tup[ia[i]].key - mn) >> dsh);
-      const u32 x0 = i ? (u32)((tup[ia[i - 1]].key - mn) >> dsh) + 1u : 0u;
+      const u32 b = bucket(i);
+      const u32 x0 = i ? bucket(i - 1) + 1u : 0u;
       for (u32 x = x0; x <= b; ++x) dir[x] = (u16)i;
       if (i == n - 1)
         for (u32 x = b + 1u; x <= nbk; ++x) dir[x] = (u16)n;
@@ -940,16 +946,26 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     const u32 w1 = bits < 11u ? bits : 11u;
     const u32 F1 = 1u << w1;
     u32 dr[IT];
+    bool outside = false;  // a key beyond the segment's recorded bounds
 #pragma unroll
     for (u32 i = 0; i < IT; ++i) {
       const u32 e = tid + i * NT;
       if (e < n) {
-        const u32 d = (u32)((tup[e].key - mn) & (u64)(F1 - 1u));
+        const u64 key = tup[e].key;
+        outside |= key < mn || key > mx;
+        const u32 d = (u32)((key - mn) & (u64)(F1 - 1u));
         const u32 r = atomicAdd(&cnt[d], 1u);
         dr[i] = (d << 16) | r;
       }
     }
-    __syncthreads();
+    // Every shared-memory index below is masked to its digit or checked against
+    // [mn, mx]; the recorded bounds are exact by construction, and if they ever were
+    // not, the piece is reported and left instead of being sorted or joined wrongly.
+    if (__syncthreads_or(outside)) {
+      if (tid == 0) atomicOr(err, (u32)DERR_BOUNDS);
+      failed = true;
+      break;
+    }
     smem_exclusive_scan<u32, NT, 2048 / NT>(cnt, F1, s_warp);
     if (tid == 0) cnt[F1] = n;  // with bits <= 11, cnt is then the start of every key value
 #pragma unroll
@@ -1191,6 +1207,32 @@ __global__ void k_seg_search(const Seg* segs, const u32* nseg_ptr, u32 cap, cons
   }
 }
 
+// Test only: narrows the recorded upper bound of the first exact final segment that
+// spans at least three keys to the middle of its range, so its largest key lies
+// beyond it; the sort kernels must report DERR_BOUNDS for that segment.
+__global__ void k_narrow_bounds_test(Seg* segs, const u32* nseg_ptr, u32 cap) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  u32 n = *nseg_ptr;
+  if (n > cap) n = cap;
+  for (u32 i = 0; i < n; ++i) {
+    Seg& s = segs[i];
+    if ((s.flags & SEG_EXACT) && s.len >= 2 && s.kmax - s.kmin >= 2) {
+      s.kmax = s.kmin + (s.kmax - s.kmin) / 2;
+      return;
+    }
+  }
+}
+
+// Points job 0's partitioned input at the next piece of it (the host-buffer join
+// copies that input in pieces and joins each against the sorted runs while the
+// next one is in flight); its count and checksum keep accumulating.
+__global__ void k_set_part(Job* jobs, Seg* split, const Tuple* S, u64 nS) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  jobs[0].S = S;
+  jobs[0].nS = nS;
+  split[0] = Seg{jobs[0].s_base, nS, 0ull, 0ull, 0u, W_SIN};
+}
+
 __global__ void k_check_empty(const u32* cnt, u32* err, u32 flag) {
   if (threadIdx.x == 0 && *cnt != 0) atomicOr(err, flag);
 }
@@ -1333,6 +1375,14 @@ void launch_fences(const Tuple* xr, u64 n, u64* fence, cudaStream_t st, int nsm)
 void launch_seg_search(const Seg* segs, const u32* nseg, u32 cap, const Job* jobs, const Run* runs, const Tuple* xr,
                        const u64* fence, u32* swin, u32 maxT, const LearnCtx& lc, cudaStream_t st, int nsm) {
   k_seg_search<<<nsm * 8, 256, 0, st>>>(segs, nseg, cap, jobs, runs, xr, fence, swin, maxT, lc);
+}
+
+void launch_narrow_bounds_test(Seg* segs, const u32* nseg, u32 cap, cudaStream_t st) {
+  k_narrow_bounds_test<<<1, 32, 0, st>>>(segs, nseg, cap);
+}
+
+void launch_set_part(Job* jobs, Seg* split, const Tuple* S, u64 nS, cudaStream_t st) {
+  k_set_part<<<1, 32, 0, st>>>(jobs, split, S, nS);
 }
 
 void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st) {

@@ -33,6 +33,8 @@ void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, 
 void launch_seg_sort(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs,
                      u32 dst_where, u32* err, cudaStream_t st, int nsm);
 void launch_check_empty(const u32* cnt, u32* err, u32 flag, cudaStream_t st);
+void launch_set_part(Job* jobs, Seg* split, const Tuple* S, u64 nS, cudaStream_t st);  // piecewise host join
+void launch_narrow_bounds_test(Seg* segs, const u32* nseg, u32 cap, cudaStream_t st);  // MPSM_FLAG_BOUNDS_TEST
 // phases 3 + 4 fused (k_pass.cu): fences of the sorted runs, per (segment, run) windows, sort-and-join
 void launch_fences(const Tuple* xr, u64 n, u64* fence, cudaStream_t st, int nsm);
 void launch_seg_search(const Seg* segs, const u32* nseg, u32 cap, const Job* jobs, const Run* runs, const Tuple* xr,
@@ -45,6 +47,7 @@ void launch_run_bounds(Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, c
 void launch_run_cdf(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, u64* rc, cudaStream_t st);
 void launch_splitters(Job* jobs, u32 njobs, const u64* fine_s, const u64* rc, u64* fine_r, u32* sp,
                       u32* part_fstart, u32* err, cudaStream_t st, bool equi_height = false);
+void launch_log2_selftest(const u64* n, u64 count, u64* out, u32 wide, cudaStream_t st, int nsm);
 void launch_fold(const Seg* segs, const u32* nseg, const LSeg* ls_fine, const LSeg* ls_split, const u64* totals,
                  const Job* jobs, const u32* hist_fine, const u32* part_fstart, u32* hist_split, cudaStream_t st,
                  int nsm);

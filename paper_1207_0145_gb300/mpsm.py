@@ -25,6 +25,7 @@ PART_S, PART_R, PART_SMALLER = 0, 1, 2
 FLAG_TIMING = 1
 FLAG_KERNEL_TIMING = 2
 FLAG_UNFUSED = 4
+FLAG_BOUNDS_TEST = 8  # test only: one segment's recorded bounds made inexact
 
 _u64 = ctypes.c_uint64
 _u32 = ctypes.c_uint32
@@ -115,6 +116,7 @@ def lib():
             "mpsm_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "mpsm_plan_device_errors": ([_p, P(_u32)], ctypes.c_int),
             "mpsm_selftest_wait_timeout": ([_p, _u32, P(_u32)], ctypes.c_int),
+            "mpsm_selftest_log2_q16": ([_p, _u64, _p, _u32, _p], ctypes.c_int),
             "mpsm_plan_set_flags": ([_p, _u32], ctypes.c_int),
             "mpsm_plan_kernel_times": ([_p, P(KernelTime), _u32, P(_u32)], ctypes.c_int),
             "mpsm_sort_runs_noalloc": ([_p, _u64, _u32, _p, _p], ctypes.c_int),
@@ -373,6 +375,15 @@ def selftest_wait_timeout(spin_limit: int = 1000, stream: Optional[int] = None) 
     f = _u32()
     rc = lib().mpsm_selftest_wait_timeout(stream, spin_limit, ctypes.byref(f))
     return rc, f.value
+
+
+def selftest_log2_q16(n, out, wide: bool = False, stream: Optional[int] = None):
+    """floor(2^16 log2 n[i]) into out[i] as the splitter kernel computes it (both 1-D
+    64-bit CUDA tensors); `wide` forces the 126-bit path."""
+    if n.numel() > out.numel():
+        raise ValueError("out is smaller than n")
+    _check(lib().mpsm_selftest_log2_q16(n.data_ptr(), n.numel(), out.data_ptr(), int(bool(wide)), stream or None),
+           "mpsm_selftest_log2_q16")
 
 
 def sort_runs_noalloc(R, runs: int, out, stream: Optional[int] = None):

@@ -32,3 +32,21 @@ def test_device_errors_are_cleared_by_a_good_call():
         for _ in range(2):
             assert p.join(to_dev(R), to_dev(S)) == oracle.join(R, S)
             assert p.device_errors() == 0
+
+
+@pytest.mark.parametrize("flags", [0, M.FLAG_UNFUSED])
+def test_inexact_segment_bounds_are_reported_not_used(flags):
+    # one final S segment's recorded key range narrowed on purpose: the sort kernels
+    # check every key against it, report MPSM_DEVERR_BOUNDS and leave the segment
+    # (every shared-memory index stays masked or range-checked; nothing faults)
+    w = gen.plain(100_000, 400_000, seed=43)
+    R, S = w.r_host(), w.s_host()
+    want = oracle.join(R, S)
+    with Plan(w.n_r, w.n_s, flags=flags | M.FLAG_BOUNDS_TEST) as p:
+        with pytest.raises(M.MPSMError) as e:
+            p.join(to_dev(R), to_dev(S))
+        assert e.value.status == M.ERR_DEVICE
+        assert p.device_errors() & M.DEVERR_BOUNDS
+    with Plan(w.n_r, w.n_s, flags=flags) as p:  # the context stays usable
+        assert p.join(to_dev(R), to_dev(S)) == want
+        assert p.device_errors() == 0
