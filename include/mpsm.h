@@ -380,9 +380,10 @@ int mpsm_selftest_log2_q16(const uint64_t* n, uint64_t count, uint64_t* out, uin
  * Limits: 1 <= runs <= 1024 and every run at most 8192 tuples
  * (ceil(nR / runs) <= 8192); larger sizes return MPSM_ERR_INVALID_ARG.  Pointers
  * must be 16-byte aligned.  Work goes on `stream` (a cudaStream_t, NULL = legacy
- * default stream); the call synchronises it before returning.  The first call on
- * a device looks up the array's address and sets kernel attributes, so make that
- * first call before any stream capture.  Every call shares the array: calls
+ * default stream); every call reads its error flag back and synchronises that
+ * stream before returning, so no call of it can be made inside a stream capture.
+ * The first call on a device also looks up the array's address and sets kernel
+ * attributes.  Every call shares the array: calls
  * whose work overlaps on the GPU (other streams, other host threads) race. */
 int mpsm_sort_runs_noalloc(const mpsm_tuple_t* R, uint64_t nR, uint32_t runs, mpsm_tuple_t* out, void* stream);
 

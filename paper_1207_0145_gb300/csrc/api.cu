@@ -46,14 +46,14 @@ enum Kid {
   K_SAMPLE, K_PLAN, K_INIT, K_HIST_RADIX, K_SCAN_RADIX, K_SCATTER_RADIX, K_SEG_SORT, K_RUN_BOUNDS, K_HIST_FINE,
   K_RUN_CDF, K_SPLITTERS, K_FOLD, K_SCAN_SPLIT, K_SCATTER_SPLIT, K_TILES, K_SEARCH, K_JOIN, K_PAIR_OFFSETS, K_CHECK,
   K_SAMPLE_S, K_RMI_DATA, K_RMI_GRAD, K_RMI_ADAM, K_RMI_TAB, K_RMI_LEAF, K_LEARN_BOUNDS, K_HIST_LEARN, K_SCAN_LEARN,
-  K_SCATTER_LEARN, K_FENCES, K_SEG_SEARCH, K_SORT_JOIN, K_NUM
+  K_SCATTER_LEARN, K_FENCES, K_SEG_SEARCH, K_SORT_JOIN, K_RMI_TRAIN, K_NUM
 };
 const char* const KNAME[K_NUM] = {"sample_bounds", "level_plan", "init_buckets", "hist_radix", "scan_radix",
                                   "scatter_radix", "seg_sort", "run_bounds", "hist_fine", "run_cdf", "splitters",
                                   "fold", "scan_split", "scatter_split", "tiles", "search", "join", "pair_offsets",
                                   "check_empty", "sample_s", "rmi_data", "rmi_grad", "rmi_adam", "rmi_tabulate",
                                   "rmi_leaves", "learn_bounds", "hist_learn", "scan_learn", "scatter_learn",
-                                  "fences", "seg_search", "sort_join"};
+                                  "fences", "seg_search", "sort_join", "rmi_train"};
 // learned model: sample and training sizes
 constexpr u32 RMI_SAMPLE_MAX = 1u << 21;  // largest sample per model
 constexpr u32 RMI_STEPS = 200;            // full-batch Adam steps
@@ -145,6 +145,8 @@ struct mpsm_plan {
   RmiTask *d_tasks = nullptr, *h_tasks = nullptr;
   void* d_leafacc = nullptr;
   float *d_tx = nullptr, *d_ty = nullptr, *d_partial = nullptr;
+  u32* d_trainbar = nullptr;        // barrier words of the one-launch trainer, 2 per model
+  u32 train_cap = 0;                // its blocks that fit on the device at once
   u64* d_fitk = nullptr;
   float* d_fity = nullptr;
   u64 fit_cap = 0;
@@ -324,8 +326,10 @@ int alloc_learn(mpsm_plan* p) {
       dalloc(&p->d_partial, nm * RMI_GMAX * RMI_NPAD) || dalloc(&p->d_fitk, p->fit_cap) ||
       dalloc(&p->d_fity, p->fit_cap) || dalloc(&p->d_samp, p->samp_cap) || dalloc(&p->d_samp_off, p->max_jobs) ||
       halloc(&p->h_samp_off, p->max_jobs) || dalloc(&p->d_samp_n, p->max_jobs) || halloc(&p->h_samp_n, p->max_jobs) ||
-      dalloc(&p->d_bnd, (u64)p->max_jobs * P_MAX) || dalloc(&p->d_brank, 2ull * p->max_jobs * P_MAX))
+      dalloc(&p->d_bnd, (u64)p->max_jobs * P_MAX) || dalloc(&p->d_brank, 2ull * p->max_jobs * P_MAX) ||
+      dalloc(&p->d_trainbar, 2 * nm))
     return MPSM_ERR_OOM;
+  p->train_cap = rmi_train_capacity(p->device);
   CK(cudaMemsetAsync(p->d_models, 0, nm * sizeof(RmiModel), p->st));
   mpsm_options_t so;
   mpsm_options_default(&so);
@@ -362,6 +366,27 @@ int setup_learn(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
   CK(cudaMemcpyAsync(p->d_samp_n, p->h_samp_n, njobs * sizeof(u32), cudaMemcpyHostToDevice, p->st));
   CK(cudaStreamSynchronize(p->st));
   if (sl) return setup_jobs(p->sub, sj.data(), njobs);
+  return MPSM_OK;
+}
+
+// Adam steps of the first nm models: every step in one cooperative launch when all
+// its blocks fit on the device together and no graph is being captured, else a
+// gradient and an update launch per step.  losses (device, optional): the loss
+// before each step of model 0.
+int train_models(mpsm_plan* p, u32 nm, u32 steps, float lr, float* losses) {
+  if (!steps) return MPSM_OK;
+  if (!p->graph_mode && p->d_trainbar && (u64)RMI_GMAX * nm <= p->train_cap) {
+    LAUNCH(K_RMI_TRAIN, CK(launch_rmi_train(p->d_models, nm, p->d_tx, p->d_ty, p->d_partial, p->d_trainbar, steps, lr,
+                                            losses, &p->d_cnt[C_ERR], p->st)));
+    return MPSM_OK;
+  }
+  for (u32 t = 1; t <= steps; ++t) {
+    LAUNCH(K_RMI_GRAD, launch_rmi_grad(p->d_models, nm, p->d_tx, p->d_ty, p->d_partial, p->st));
+    LAUNCH(K_RMI_ADAM, launch_rmi_adam(p->d_models, nm, p->d_partial, t, lr, p->st));
+    if (losses)
+      CK(cudaMemcpyAsync(losses + (t - 1), &p->d_models[0].loss, sizeof(float), cudaMemcpyDeviceToDevice, p->st));
+  }
+  CK(cudaGetLastError());
   return MPSM_OK;
 }
 
@@ -577,10 +602,7 @@ int phase_learn(mpsm_plan* p) {
                                      p->sub ? p->sub->xr : nullptr, p->d_fitk, p->d_fity, p->st, p->nsm));
   LAUNCH(K_RMI_DATA, launch_train_data(p->d_models, nm, p->d_fitk, p->d_fity, p->d_tx, p->d_ty, p->st));
   const u32 steps = p->opt.learn_steps ? p->opt.learn_steps : RMI_STEPS;
-  for (u32 t = 1; t <= steps; ++t) {
-    LAUNCH(K_RMI_GRAD, launch_rmi_grad(p->d_models, nm, p->d_tx, p->d_ty, p->d_partial, p->st));
-    LAUNCH(K_RMI_ADAM, launch_rmi_adam(p->d_models, nm, p->d_partial, t, RMI_LR, p->st));
-  }
+  if (int rc = train_models(p, nm, steps, RMI_LR, nullptr)) return rc;
   LAUNCH(K_RMI_TAB, launch_rmi_tabulate(p->d_models, nm, p->st));
   LAUNCH(K_RMI_LEAF, launch_leaf_fit(p->d_models, nm, p->d_leafacc, p->d_fitk, p->d_fity, p->st, p->nsm));
   CK(cudaGetLastError());
@@ -833,6 +855,7 @@ MPSM_API void mpsm_plan_destroy(mpsm_plan_t* p) {
   dfree(p->d_tx);
   dfree(p->d_ty);
   dfree(p->d_partial);
+  dfree(p->d_trainbar);
   dfree(p->d_fitk);
   dfree(p->d_fity);
   dfree(p->d_samp);
@@ -1541,13 +1564,9 @@ MPSM_API int mpsm_rmi_train(mpsm_plan_t* p, const float* x, const float* y, uint
   int rc = rmi_points(p, x, y, n, theta);
   if (rc) return rc;
   if (losses && steps > p->fit_cap) return MPSM_ERR_INVALID_ARG;
-  for (u32 t = 1; t <= steps; ++t) {
-    launch_rmi_grad(p->d_models, 1, p->d_tx, p->d_ty, p->d_partial, p->st);
-    launch_rmi_adam(p->d_models, 1, p->d_partial, t, lr, p->st);
-    if (losses)
-      CK(cudaMemcpyAsync(p->d_fity + (t - 1), &p->d_models[0].loss, sizeof(float), cudaMemcpyDeviceToDevice, p->st));
-  }
-  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(&p->d_cnt[C_ERR], 0, sizeof(u32), p->st));
+  if ((rc = train_models(p, 1, steps, lr, losses ? p->d_fity : nullptr))) return rc;
+  if ((rc = read_err(p))) return rc;
   CK(cudaMemcpyAsync(theta, p->d_models[0].theta, RMI_NP * sizeof(float), cudaMemcpyDeviceToDevice, p->st));
   if (losses && steps) CK(cudaMemcpyAsync(losses, p->d_fity, steps * sizeof(float), cudaMemcpyDeviceToHost, p->st));
   CK(cudaStreamSynchronize(p->st));
@@ -1568,15 +1587,12 @@ MPSM_API int mpsm_rmi_fit(mpsm_plan_t* p, const uint64_t* keys, const float* y, 
   }
   launch_fit_data(p->d_models, p->d_tasks, 1, p->d_jobs, p->d_runs, p->xr, nullptr, p->d_fitk, p->d_fity, p->st, p->nsm);
   launch_train_data(p->d_models, 1, p->d_fitk, p->d_fity, p->d_tx, p->d_ty, p->st);
-  for (u32 t = 1; t <= steps; ++t) {
-    launch_rmi_grad(p->d_models, 1, p->d_tx, p->d_ty, p->d_partial, p->st);
-    launch_rmi_adam(p->d_models, 1, p->d_partial, t, lr, p->st);
-  }
+  CK(cudaMemsetAsync(&p->d_cnt[C_ERR], 0, sizeof(u32), p->st));
+  if ((rc = train_models(p, 1, steps, lr, nullptr))) return rc;
   launch_rmi_tabulate(p->d_models, 1, p->st);
   launch_leaf_fit(p->d_models, 1, p->d_leafacc, p->d_fitk, p->d_fity, p->st, p->nsm);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(p->st));
-  return MPSM_OK;
+  return read_err(p);
 }
 
 MPSM_API int mpsm_rmi_predict(mpsm_plan_t* p, uint32_t slot, const uint64_t* keys, uint64_t n, float* yhat,

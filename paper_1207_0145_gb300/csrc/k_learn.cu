@@ -182,9 +182,11 @@ __global__ void k_train_data(RmiModel* models, const u64* fitk, const float* fit
 constexpr u32 GP = 33;
 constexpr size_t SMEM_GRAD = (RMI_NPAD + 4 * RMI_GT * GP + 3 * RMI_GT) * sizeof(float);
 
-__global__ void __launch_bounds__(RMI_GT) k_rmi_grad(const RmiModel* models, const float* X, const float* Y,
-                                                     float* partial) {
-  extern __shared__ __align__(16) float gsm[];
+// Partial gradient (and loss) of model mdl over its training points [blk RMI_GT,
+// (blk + 1) RMI_GT) into out[RMI_NPAD], the weights already in gsm[0, RMI_NPAD).
+// Every thread of the block calls it; a block without points writes zeros.
+__device__ __forceinline__ void grad_block(const RmiModel& M, u32 mdl, u32 blk, const float* X, const float* Y,
+                                           float* out, float* gsm) {
   float* th = gsm;
   float* sh1 = th + RMI_NPAD;
   float* sh2 = sh1 + RMI_GT * GP;
@@ -193,26 +195,22 @@ __global__ void __launch_bounds__(RMI_GT) k_rmi_grad(const RmiModel* models, con
   float* sx = sda1 + RMI_GT * GP;
   float* sg = sx + RMI_GT;
   float* sl = sg + RMI_GT;
-  const RmiModel& M = models[blockIdx.y];
-  float* out = partial + ((u64)blockIdx.y * RMI_GMAX + blockIdx.x) * RMI_NPAD;
   const u32 tid = threadIdx.x;
   const u32 n = M.active ? M.train_n : 0u;
-  if (blockIdx.x * RMI_GT >= n) {  // no points in this block: a zero partial
+  if (blk * RMI_GT >= n) {  // no points in this block: a zero partial
     for (u32 p = tid; p < RMI_NPAD; p += RMI_GT) out[p] = 0.0f;
     return;
   }
-  for (u32 p = tid; p < RMI_NPAD; p += RMI_GT) th[p] = M.theta[p];
-  __syncthreads();
-  const u32 q = blockIdx.x * RMI_GT + tid;
+  const u32 q = blk * RMI_GT + tid;
   const bool valid = q < n;
-  const float x = valid ? X[(u64)blockIdx.y * RMI_TRAIN_MAX + q] : 0.0f;
-  const float yv = valid ? Y[(u64)blockIdx.y * RMI_TRAIN_MAX + q] : 0.0f;
+  const float x = valid ? X[(u64)mdl * RMI_TRAIN_MAX + q] : 0.0f;
+  const float yv = valid ? Y[(u64)mdl * RMI_TRAIN_MAX + q] : 0.0f;
   float a1[RMI_H], h2[RMI_H];
 #pragma unroll
   for (u32 k = 0; k < RMI_H; ++k) a1[k] = fmaf(th[RO_W1 + k], x, th[RO_B1 + k]);
   float yh = th[RO_B3];
-#pragma unroll 4
-  for (u32 j = 0; j < RMI_H; ++j) {
+#pragma unroll
+  for (u32 j = 0; j < RMI_H; ++j) {  // fully unrolled: h2 stays in registers
     float a = th[RO_B2 + j];
 #pragma unroll
     for (u32 k = 0; k < RMI_H; ++k) a = fmaf(th[RO_W2 + j * RMI_H + k], fmaxf(a1[k], 0.0f), a);
@@ -241,14 +239,22 @@ __global__ void __launch_bounds__(RMI_GT) k_rmi_grad(const RmiModel* models, con
     sh1[tid * GP + k] = valid ? fmaxf(a1[k], 0.0f) : 0.0f;
   }
   __syncthreads();
-  // dW2[j][k] = sum_i da2[i][j] h1[i][k]: 8 entries per thread (warp: fixed j, k = lane)
+  // dW2[j][k] = sum_i da2[i][j] h1[i][k]: entries e = tid + r RMI_GT, r < 8 (warp: fixed j, k = lane),
+  // summed over i in order, all eight in one pass over the points
+  {
+    constexpr u32 R = (RMI_H * RMI_H) / RMI_GT;
+    const u32 k = tid & 31u, j0 = tid >> 5;  // entry r: j = j0 + r RMI_GT / 32
+    float acc[R];
 #pragma unroll
-  for (u32 r8 = 0; r8 < (RMI_H * RMI_H) / RMI_GT; ++r8) {
-    const u32 e = tid + r8 * RMI_GT;
-    const u32 j = e >> 5, k = e & 31u;
-    float s = 0.0f;
-    for (u32 i = 0; i < RMI_GT; ++i) s = fmaf(sda2[i * GP + j], sh1[i * GP + k], s);
-    out[RO_W2 + e] = s;
+    for (u32 r = 0; r < R; ++r) acc[r] = 0.0f;
+#pragma unroll 4
+    for (u32 i = 0; i < RMI_GT; ++i) {
+      const float h = sh1[i * GP + k];
+#pragma unroll
+      for (u32 r = 0; r < R; ++r) acc[r] = fmaf(sda2[i * GP + j0 + r * (RMI_GT / 32)], h, acc[r]);
+    }
+#pragma unroll
+    for (u32 r = 0; r < R; ++r) out[RO_W2 + tid + r * RMI_GT] = acc[r];
   }
   if (tid < 32) {
     float w = 0.0f, b = 0.0f;
@@ -279,6 +285,19 @@ __global__ void __launch_bounds__(RMI_GT) k_rmi_grad(const RmiModel* models, con
   } else if (tid < 64 + 1 + (RMI_NPAD - RMI_NP - 1)) {
     out[RMI_NP + (tid - 64)] = 0.0f;  // padding slots
   }
+  __syncthreads();  // the shared arrays may be written again
+}
+
+__global__ void __launch_bounds__(RMI_GT) k_rmi_grad(const RmiModel* models, const float* X, const float* Y,
+                                                     float* partial) {
+  extern __shared__ __align__(16) float gsm[];
+  const RmiModel& M = models[blockIdx.y];
+  const u32 n = M.active ? M.train_n : 0u;
+  if (blockIdx.x * RMI_GT < n) {
+    for (u32 p = threadIdx.x; p < RMI_NPAD; p += RMI_GT) gsm[p] = M.theta[p];
+    __syncthreads();
+  }
+  grad_block(M, blockIdx.y, blockIdx.x, X, Y, partial + ((u64)blockIdx.y * RMI_GMAX + blockIdx.x) * RMI_NPAD, gsm);
 }
 
 // sum of the block partials of one model, in block order (deterministic)
@@ -313,6 +332,218 @@ __global__ void __launch_bounds__(1024) k_rmi_adam(RmiModel* models, const float
 __global__ void __launch_bounds__(1024) k_rmi_reduce(const float* partial, float* grad, float* loss) {
   for (u32 p = threadIdx.x; p < RMI_NP; p += blockDim.x) grad[p] = sum_partial(partial, 0, p);
   if (threadIdx.x == 0) *loss = sum_partial(partial, 0, RMI_NP);
+}
+
+// The same partial gradient with four threads per point (RMI_GT4 threads): thread
+// sub = tid & 3 of point tid >> 2 owns hidden units j = 4 jj + sub (and k = 4 kk + sub),
+// so every thread's chains are a quarter as long.  Shared memory: th[RMI_NPAD] |
+// W2 again with rows padded to 36 (bank-conflict free for the four threads) |
+// h1, h2, da2, da1 [RMI_GT][33] | x, g, l [RMI_GT].  The sums over points run in
+// point order; the output yhat adds the four threads' shares.
+constexpr u32 RMI_GT4 = 4 * RMI_GT;
+constexpr u32 W2S = 36;
+constexpr size_t SMEM_GRAD4 = (RMI_NPAD + RMI_H * W2S + 4 * RMI_GT * GP + 3 * RMI_GT) * sizeof(float);
+
+__device__ __forceinline__ void grad_block4(const RmiModel& M, u32 mdl, u32 blk, const float* X, const float* Y,
+                                            float* out, float* gsm) {
+  float* th = gsm;
+  float* w2 = th + RMI_NPAD;
+  float* sh1 = w2 + RMI_H * W2S;
+  float* sh2 = sh1 + RMI_GT * GP;
+  float* sda2 = sh2 + RMI_GT * GP;
+  float* sda1 = sda2 + RMI_GT * GP;
+  float* sx = sda1 + RMI_GT * GP;
+  float* sg = sx + RMI_GT;
+  float* sl = sg + RMI_GT;
+  const u32 tid = threadIdx.x;
+  const u32 n = M.active ? M.train_n : 0u;
+  if (blk * RMI_GT >= n) {
+    for (u32 p = tid; p < RMI_NPAD; p += RMI_GT4) out[p] = 0.0f;
+    return;
+  }
+  for (u32 e = tid; e < RMI_H * RMI_H; e += RMI_GT4) w2[(e >> 5) * W2S + (e & 31u)] = th[RO_W2 + e];
+  __syncthreads();
+  const u32 pt = tid >> 2, sub = tid & 3u;
+  const u32 q = blk * RMI_GT + pt;
+  const bool valid = q < n;
+  const float x = valid ? X[(u64)mdl * RMI_TRAIN_MAX + q] : 0.0f;
+  const float yv = valid ? Y[(u64)mdl * RMI_TRAIN_MAX + q] : 0.0f;
+  float a1[RMI_H];
+#pragma unroll
+  for (u32 k = 0; k < RMI_H; ++k) a1[k] = fmaf(th[RO_W1 + k], x, th[RO_B1 + k]);
+  float a2[RMI_H / 4];
+  float part = 0.0f;
+#pragma unroll
+  for (u32 jj = 0; jj < RMI_H / 4; ++jj) {
+    const u32 j = 4 * jj + sub;
+    float a = th[RO_B2 + j];
+#pragma unroll
+    for (u32 k = 0; k < RMI_H; ++k) a = fmaf(w2[j * W2S + k], fmaxf(a1[k], 0.0f), a);
+    a2[jj] = a;
+    part = fmaf(th[RO_W3 + j], fmaxf(a, 0.0f), part);
+  }
+  part += __shfl_xor_sync(0xffffffffu, part, 1);
+  part += __shfl_xor_sync(0xffffffffu, part, 2);
+  const float yh = th[RO_B3] + part;
+  const float r = yh - yv;
+  const float g = valid ? 2.0f * r / (float)n : 0.0f;
+  if (sub == 0) {
+    sx[pt] = x;
+    sg[pt] = g;
+    sl[pt] = valid ? r * r / (float)n : 0.0f;
+  }
+  // dL/da2 = g W3 [a2 > 0]; h2 = relu(a2)
+#pragma unroll
+  for (u32 jj = 0; jj < RMI_H / 4; ++jj) {
+    const u32 j = 4 * jj + sub;
+    const bool on = a2[jj] > 0.0f;
+    sda2[pt * GP + j] = on ? g * th[RO_W3 + j] : 0.0f;
+    sh2[pt * GP + j] = on ? a2[jj] : 0.0f;
+  }
+  __syncwarp();
+  // dL/da1 = [a1 > 0] W2^T da2, for k = 4 kk + sub
+#pragma unroll
+  for (u32 kk = 0; kk < RMI_H / 4; ++kk) {
+    const u32 k = 4 * kk + sub;
+    float t = 0.0f;
+#pragma unroll 8
+    for (u32 j = 0; j < RMI_H; ++j) t = fmaf(w2[j * W2S + k], sda2[pt * GP + j], t);
+    const float ak = fmaf(th[RO_W1 + k], x, th[RO_B1 + k]);  // a1[k], recomputed: k depends on the thread
+    sda1[pt * GP + k] = (ak > 0.0f && valid) ? t : 0.0f;
+    sh1[pt * GP + k] = valid ? fmaxf(ak, 0.0f) : 0.0f;
+  }
+  __syncthreads();
+  // dW2[j][k] = sum_i da2[i][j] h1[i][k]: entries tid and tid + RMI_GT4 (warp: fixed j, k = lane)
+  {
+    constexpr u32 R = (RMI_H * RMI_H) / RMI_GT4;
+    const u32 k = tid & 31u, j0 = tid >> 5;
+    float acc[R];
+#pragma unroll
+    for (u32 rr = 0; rr < R; ++rr) acc[rr] = 0.0f;
+#pragma unroll 4
+    for (u32 i = 0; i < RMI_GT; ++i) {
+      const float h = sh1[i * GP + k];
+#pragma unroll
+      for (u32 rr = 0; rr < R; ++rr) acc[rr] = fmaf(sda2[i * GP + j0 + rr * (RMI_GT4 / 32)], h, acc[rr]);
+    }
+#pragma unroll
+    for (u32 rr = 0; rr < R; ++rr) out[RO_W2 + tid + rr * RMI_GT4] = acc[rr];
+  }
+  // the other parameters: one sum over the points per thread
+  if (tid < 32) {
+    float w = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) w = fmaf(sda1[i * GP + tid], sx[i], w);
+    out[RO_W1 + tid] = w;
+  } else if (tid < 64) {
+    float b = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) b += sda1[i * GP + tid - 32];
+    out[RO_B1 + tid - 32] = b;
+  } else if (tid < 96) {
+    float b = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) b += sda2[i * GP + tid - 64];
+    out[RO_B2 + tid - 64] = b;
+  } else if (tid < 128) {
+    float w = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) w = fmaf(sg[i], sh2[i * GP + tid - 96], w);
+    out[RO_W3 + tid - 96] = w;
+  } else if (tid == 128) {
+    float b = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) b += sg[i];
+    out[RO_B3] = b;
+  } else if (tid == 129) {
+    float l = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) l += sl[i];
+    out[RMI_NP] = l;
+  } else if (tid < 130 + (RMI_NPAD - RMI_NP - 1)) {
+    out[RMI_NP + 1 + (tid - 130)] = 0.0f;  // padding slots
+  }
+  __syncthreads();
+}
+
+// Barrier of the RMI_GMAX blocks of one model, which a cooperative launch keeps
+// resident together: each block adds one to the model's arrival count, which only
+// grows, and waits until it reaches RMI_GMAX times the number of barriers passed so
+// far; it polls at most `limit` times and then gives up (false).
+__device__ __forceinline__ bool model_barrier(u32* cnt, u32& phase, u32 limit) {
+  __shared__ u32 s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u32 ok = 1;
+    const u32 target = (phase + 1u) * RMI_GMAX;
+    __threadfence();  // this block's partials and parameters before its arrival
+    atomicAdd(cnt, 1u);
+    u32 it = 0;
+    while (*reinterpret_cast<volatile u32*>(cnt) < target) {
+      if (++it >= limit) {
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  ++phase;
+  return s_ok != 0;
+}
+
+constexpr u32 ADAM_SLICE = (RMI_NP + 1 + RMI_GMAX - 1) / RMI_GMAX;  // parameters (and the loss) per block
+
+// Every Adam step of the active models in one launch: grid (RMI_GMAX, models).
+// Per step each block writes its partial gradient; after a barrier, block b sums
+// the partials of parameters [b ADAM_SLICE, (b + 1) ADAM_SLICE) -- each in a fixed
+// order, one warp per parameter -- and applies the same update as k_rmi_adam to
+// them; after a second barrier every block reads the new weights.  bar holds two
+// zeroed words per model; a barrier that gives up sets DERR_TMA_TIMEOUT in err.
+// losses (optional, one model): the loss before each step.
+__global__ void __launch_bounds__(RMI_GT4, 2) k_rmi_train(RmiModel* models, const float* X, const float* Y,
+                                                      float* partial, u32* bar, u32 steps, float lr, u32 limit,
+                                                      float* losses, u32* err) {
+  extern __shared__ __align__(16) float gsm[];
+  RmiModel& M = models[blockIdx.y];
+  if (!M.active || M.train_n == 0) return;  // the same for every block of the model
+  const u32 tid = threadIdx.x, lane = lane_id(), wid = warp_id();
+  const u32 blk = blockIdx.x, mdl = blockIdx.y;
+  u32* cnt = bar + 2 * mdl;
+  u32 phase = 0;
+  float* out = partial + ((u64)mdl * RMI_GMAX + blk) * RMI_NPAD;
+  const float* all = partial + (u64)mdl * RMI_GMAX * RMI_NPAD;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (u32 step = 1; step <= steps; ++step) {
+    for (u32 p = tid; p < RMI_NPAD; p += RMI_GT4) gsm[p] = __ldcg(&M.theta[p]);  // other blocks wrote them
+    __syncthreads();
+    grad_block4(M, mdl, blk, X, Y, out, gsm);
+    if (!model_barrier(cnt, phase, limit)) {
+      if (tid == 0) atomicOr(err, (u32)DERR_TMA_TIMEOUT);
+      return;
+    }
+    const float c1 = 1.0f - powf(b1, (float)step);
+    const float c2 = 1.0f - powf(b2, (float)step);
+    for (u32 k = wid; k < ADAM_SLICE; k += RMI_GT4 / 32) {
+      const u32 p = blk * ADAM_SLICE + k;
+      if (p > RMI_NP) break;  // the same for the whole warp
+      float g = 0.0f;
+      for (u32 b = lane; b < RMI_GMAX; b += 32) g += __ldcg(&all[(u64)b * RMI_NPAD + p]);
+      g = warp_sum(g);
+      if (lane == 0) {
+        if (p == RMI_NP) {  // the loss slot
+          M.loss = g;
+          if (step == 1) M.loss0 = g;
+          if (losses) losses[step - 1] = g;
+        } else {
+          const float m = b1 * M.m[p] + (1.0f - b1) * g;
+          const float v = b2 * M.v[p] + (1.0f - b2) * g * g;
+          M.m[p] = m;
+          M.v[p] = v;
+          M.theta[p] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+        }
+      }
+    }
+    if (!model_barrier(cnt, phase, limit)) {
+      if (tid == 0) atomicOr(err, (u32)DERR_TMA_TIMEOUT);
+      return;
+    }
+  }
 }
 
 __global__ void k_rmi_tabulate(RmiModel* models) {
@@ -459,8 +690,9 @@ __global__ void k_learn_bounds(Job* jobs, const RmiModel* models, const u64* fit
 }
 
 // Fine-cell table: for each fine bucket [lo, hi] of the job's key range, the
-// partition its keys fall in when no boundary lies in [lo, hi], else the first
-// partition it reaches, marked LCELL_SPLIT (those keys search the boundaries).
+// partition its keys fall in when no boundary lies in [lo, hi], else the first and
+// last partitions it reaches, marked LCELL_SPLIT (and LCELL_HOT when every boundary
+// inside is the same key).
 __global__ void k_learn_cells(const Job* jobs, const u64* bnd, u32* cell) {
   const Job& J = jobs[blockIdx.x];
   const u32 nb = J.parts ? J.parts - 1u : 0u;
@@ -472,7 +704,8 @@ __global__ void k_learn_cells(const Job* jobs, const u64* bnd, u32* cell) {
     const u64 hi = (J.kmax - lo < w) ? J.kmax : lo + w;
     const u32 plo = (u32)lower_bound_at(at, nb, lo);                                    // #bnd < lo
     const u32 phi = hi == ~0ull ? nb : (u32)lower_bound_at(at, nb, hi + 1ull);          // #bnd <= hi
-    cell[J.fine_base + f] = plo == phi ? plo : (plo | LCELL_SPLIT);
+    const u32 hot = (plo < phi && b[plo] == b[phi - 1]) ? LCELL_HOT : 0u;  // one key is every boundary here
+    cell[J.fine_base + f] = plo == phi ? plo : (plo | (phi << 16) | LCELL_SPLIT | hot);
   }
 }
 
@@ -515,6 +748,29 @@ void launch_rmi_predict(const RmiModel* M, const u64* keys, u64 n, float* yhat, 
 
 void init_attrs_learn() {
   cudaFuncSetAttribute(k_rmi_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GRAD);
+  cudaFuncSetAttribute(k_rmi_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GRAD4);
+}
+
+// blocks of k_rmi_train that can be resident at once on this device
+u32 rmi_train_capacity(int dev) {
+  int per_sm = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rmi_train, RMI_GT4, SMEM_GRAD4) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (u32)(per_sm > 0 ? per_sm : 0) * (u32)(nsm > 0 ? nsm : 0);
+}
+
+// All steps in one cooperative launch (bar: 2 u32 per model, zeroed here first).
+cudaError_t launch_rmi_train(RmiModel* models, u32 nmodels, const float* X, const float* Y, float* partial, u32* bar,
+                             u32 steps, float lr, float* losses, u32* err, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2ull * nmodels * sizeof(u32), st);
+  if (e != cudaSuccess) return e;
+  u32 limit = 1u << 22;  // polls of a barrier (at least 64 ns each) before it gives up
+  void* args[] = {&models, &X, &Y, &partial, &bar, &steps, &lr, &limit, &losses, &err};
+  return cudaLaunchCooperativeKernel((const void*)k_rmi_train, dim3(RMI_GMAX, nmodels), dim3(RMI_GT4), args,
+                                     SMEM_GRAD4, st);
 }
 
 size_t leaf_acc_bytes() { return sizeof(LeafAcc) * RMI_LEAVES; }

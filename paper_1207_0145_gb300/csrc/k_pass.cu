@@ -238,7 +238,9 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
   u64* smin = reinterpret_cast<u64*>(sm_raw);
   u64* smax = smin + FCAP;
   u32* scnt = reinterpret_cast<u32*>(smax + FCAP);
-  u16* scell = reinterpret_cast<u16*>(scnt + FCAP);  // MODE_LEARN: fine cell -> partition (FINE_MAX)
+  u32* scell = scnt + FCAP;                              // MODE_LEARN: fine-cell table (FINE_MAX)
+  u64* sbnd = reinterpret_cast<u64*>(scell + FINE_MAX);  // MODE_LEARN: partition boundaries (P_MAX)
+  u32* srank = reinterpret_cast<u32*>(sbnd + P_MAX);     // MODE_LEARN: their sample ranks (2 P_MAX)
   __shared__ u32 s_seg;
   const u64 nch = totals[0];
   const u32 nseg = *nseg_ptr;
@@ -265,9 +267,16 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
     }
     const u64 row0 = S.off - jobs[S.job].s_base;  // MODE_LEARN: row of the tuple in the job's S
     u32 probes = 0, keys = 0;
+    u32 fit_n = 0;
     if (MODE == MODE_LEARN) {
       const Job& J = jobs[S.job];
-      for (u32 f = threadIdx.x; f < J.nfine; f += NT_PASS) scell[f] = (u16)lc.cell[J.fine_base + f];
+      for (u32 f = threadIdx.x; f < J.nfine; f += NT_PASS) scell[f] = lc.cell[J.fine_base + f];
+      for (u32 q = threadIdx.x; q + 1u < F; q += NT_PASS) {
+        sbnd[q] = lc.bnd[(u64)S.job * P_MAX + q];
+        srank[2 * q] = lc.brank[(u64)S.job * 2 * P_MAX + 2 * q];
+        srank[2 * q + 1] = lc.brank[(u64)S.job * 2 * P_MAX + 2 * q + 1];
+      }
+      fit_n = lc.models[2 * S.job].fit_n;
       __syncthreads();
     }
     for (u64 t0 = a + threadIdx.x; t0 < e; t0 += NT_PASS * 4) {
@@ -287,11 +296,8 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
           b = d >= F ? F - 1u : (u32)d;
         } else if (MODE == MODE_LEARN) {
           if (k[i] < kmin || k[i] > kmax) continue;
-          const u32 e = scell[(k[i] - kmin) >> L.shift];
-          b = e;
-          if (e & LCELL_SPLIT)
-            b = learned_part(&lc.models[2 * S.job], lc.bnd + (u64)S.job * P_MAX, lc.brank + (u64)S.job * 2 * P_MAX, F,
-                             k[i], row0 + t, lc.seed, probes, e & ~LCELL_SPLIT);
+          b = learned_cell_part(scell[(k[i] - kmin) >> L.shift], sbnd, srank, F, fit_n, k[i], row0 + t, lc.seed,
+                                probes);
           ++keys;
         } else {
           if (k[i] < kmin || k[i] > kmax) continue;
@@ -451,7 +457,10 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
   u32* gb = hb + F_MAX;                                            // F_MAX
   u16* sidx = reinterpret_cast<u16*>(gb + F_MAX);                  // SC_TILE
   u16* sb = sidx + SC_TILE;                                        // SC_TILE
-  u16* spl = sb + SC_TILE;                                         // FINE_MAX (MODE_SPLIT)
+  u16* spl = sb + SC_TILE;                                         // FINE_MAX u16 (MODE_SPLIT) or
+  u32* spl32 = reinterpret_cast<u32*>(spl);                        //   FINE_MAX u32 (MODE_LEARN)
+  u64* sbnd = reinterpret_cast<u64*>(spl32 + FINE_MAX);            // P_MAX (MODE_LEARN)
+  u32* srank = reinterpret_cast<u32*>(sbnd + P_MAX);               // 2 P_MAX (MODE_LEARN)
   __shared__ __align__(8) u64 mbar[STAGES];
   __shared__ u32 s_seg;
   __shared__ u32 s_warp[NT_SC / 32 + 1];
@@ -484,7 +493,19 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
       const Job& J = jobs[S.job];
       kmin = J.kmin;
       kmax = J.kmax;
-      for (u32 f = tid; f < J.nfine; f += NT_SC) spl[f] = (u16)(MODE == MODE_SPLIT ? sp : lc.cell)[J.fine_base + f];
+      if (MODE == MODE_SPLIT)
+        for (u32 f = tid; f < J.nfine; f += NT_SC) spl[f] = (u16)sp[J.fine_base + f];
+      else
+        for (u32 f = tid; f < J.nfine; f += NT_SC) spl32[f] = lc.cell[J.fine_base + f];
+    }
+    u32 fit_n = 0;
+    if (MODE == MODE_LEARN) {
+      for (u32 q = tid; q + 1u < F; q += NT_SC) {
+        sbnd[q] = lc.bnd[(u64)S.job * P_MAX + q];
+        srank[2 * q] = lc.brank[(u64)S.job * 2 * P_MAX + 2 * q];
+        srank[2 * q + 1] = lc.brank[(u64)S.job * 2 * P_MAX + 2 * q + 1];
+      }
+      fit_n = lc.models[2 * S.job].fit_n;
     }
     const u64 row0 = S.off - jobs[S.job].s_base;  // MODE_LEARN: row of the segment's first tuple in the job's S
     u32 probes = 0;
@@ -530,11 +551,8 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
           b = d >= F ? F - 1u : (u32)d;
         } else if (MODE == MODE_LEARN) {
           if (key < kmin || key > kmax) continue;
-          const u32 e = spl[(key - kmin) >> L.shift];
-          b = e;
-          if (e & LCELL_SPLIT)
-            b = learned_part(&lc.models[2 * S.job], lc.bnd + (u64)S.job * P_MAX, lc.brank + (u64)S.job * 2 * P_MAX, F,
-                             key, row0 + t0 + x, lc.seed, probes, e & ~LCELL_SPLIT);
+          b = learned_cell_part(spl32[(key - kmin) >> L.shift], sbnd, srank, F, fit_n, key, row0 + t0 + x, lc.seed,
+                                probes);
         } else {
           if (key < kmin || key > kmax) continue;
           b = spl[(key - kmin) >> L.shift];
@@ -1237,9 +1255,14 @@ __global__ void k_check_empty(const u32* cnt, u32* err, u32 flag) {
   if (threadIdx.x == 0 && *cnt != 0) atomicOr(err, flag);
 }
 
-constexpr size_t smem_scatter(u32 tile, u32 stages = 1) {
-  return stages * tile * sizeof(Tuple) + 3 * F_MAX * sizeof(u32) + 2 * tile * sizeof(u16) + FINE_MAX * sizeof(u16);
+constexpr size_t smem_scatter(u32 tile, u32 stages = 1, bool learn = false) {
+  return stages * tile * sizeof(Tuple) + 3 * F_MAX * sizeof(u32) + 2 * tile * sizeof(u16) +
+         FINE_MAX * (learn ? sizeof(u32) : sizeof(u16)) + (learn ? P_MAX * (sizeof(u64) + 2 * sizeof(u32)) : 0);
 }
+// the learned partitioning pass: two 4096-tuple buffers per block (one block per SM), so
+// the partition boundaries and their ranks fit beside them in shared memory
+constexpr u32 LN_TILE = 4096, LN_NT = 1024;
+constexpr size_t SMEM_HIST_LEARN = F_MAX * 20 + FINE_MAX * 4 + P_MAX * (sizeof(u64) + 2 * sizeof(u32));
 constexpr size_t smem_sort(u32 cap, u32 nt) { return cap * sizeof(Tuple) + 2 * cap * sizeof(u16) + (nt / 32) * 256 * sizeof(u32); }
 constexpr u32 NT_BIG = 512;  // threads of the 8192-tuple class (one block per SM; 1024 measured slower)
 constexpr size_t SMEM_SCAN = (3 * F_MAX + 1) * sizeof(u64);
@@ -1258,9 +1281,9 @@ void init_attrs_pass() {
 
   set_smem(k_hist<MODE_RADIX, F_MAX>, F_MAX * 20);
   set_smem(k_hist<MODE_FINE, FINE_MAX>, FINE_MAX * 20);
-  set_smem(k_hist<MODE_LEARN, F_MAX>, F_MAX * 20 + FINE_MAX * 2);
+  set_smem(k_hist<MODE_LEARN, F_MAX>, SMEM_HIST_LEARN);
   set_smem(k_scan<MODE_LEARN>, SMEM_SCAN);
-  set_smem(k_scatter<MODE_LEARN, SP_TILE, SP_NT, SP_MINB, 1>, smem_scatter(SP_TILE));
+  set_smem(k_scatter<MODE_LEARN, LN_TILE, LN_NT, 1, 2>, smem_scatter(LN_TILE, 2, true));
   set_smem(k_scan<MODE_RADIX>, SMEM_SCAN);
   set_smem(k_scan<MODE_SPLIT>, SMEM_SCAN);
   set_smem(k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB, RX_STAGES>, smem_scatter(RX_TILE, RX_STAGES));
@@ -1300,9 +1323,8 @@ void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, con
     k_hist<MODE_RADIX, F_MAX><<<nsm * 4, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs, src_where,
                                                              hist, bmin, bmax, btot, lc);
   } else if (mode == MODE_LEARN) {
-    const size_t sm = F_MAX * 20 + FINE_MAX * 2;
-    k_hist<MODE_LEARN, F_MAX><<<nsm * 4, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs, src_where,
-                                                             hist, bmin, bmax, btot, lc);
+    k_hist<MODE_LEARN, F_MAX><<<nsm * 2, NT_PASS, SMEM_HIST_LEARN, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
+                                                                       src_where, hist, bmin, bmax, btot, lc);
   } else {
     const size_t sm = FINE_MAX * 20;
     k_hist<MODE_FINE, FINE_MAX><<<nsm * 2, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
@@ -1339,7 +1361,7 @@ void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, 
     k_scatter<MODE_SPLIT, RX_TILE, RX_NT, RX_MINB, RX_STAGES><<<nsm * RX_MINB, RX_NT, smem_scatter(RX_TILE, RX_STAGES), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   } else if (mode == MODE_LEARN) {
-    k_scatter<MODE_LEARN, SP_TILE, SP_NT, SP_MINB, 1><<<nsm * SP_MINB, SP_NT, smem_scatter(SP_TILE), st>>>(
+    k_scatter<MODE_LEARN, LN_TILE, LN_NT, 1, 2><<<nsm, LN_NT, smem_scatter(LN_TILE, 2, true), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   } else if (big_tiles) {
     k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB, RX_STAGES><<<nsm * RX_MINB, RX_NT, smem_scatter(RX_TILE, RX_STAGES), st>>>(
@@ -1440,8 +1462,9 @@ void* g_noalloc_addr[128];  // device address of the scratch array, per device o
 
 /* See include/mpsm.h.  The first call on a device looks up the scratch array's
  * device address (cudaGetSymbolAddress, with that device current) and sets the
- * sort kernels' shared-memory limits; make that first call before any stream
- * capture.  Calls whose work overlaps on the GPU share the array and race. */
+ * sort kernels' shared-memory limits.  Every call reads the error flag back and
+ * synchronises its stream, so none can run inside a stream capture.  Calls whose
+ * work overlaps on the GPU share the array and race. */
 extern "C" __attribute__((visibility("default"))) int mpsm_sort_runs_noalloc(const mpsm_tuple_t* R, uint64_t nR,
                                                                              uint32_t runs, mpsm_tuple_t* out,
                                                                              void* stream) {

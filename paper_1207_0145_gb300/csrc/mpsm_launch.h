@@ -88,6 +88,10 @@ void launch_train_data(RmiModel* models, u32 nmodels, const u64* fitk, const flo
 void launch_rmi_grad(const RmiModel* models, u32 nmodels, const float* X, const float* Y, float* partial,
                      cudaStream_t st);
 void launch_rmi_adam(RmiModel* models, u32 nmodels, const float* partial, u32 step, float lr, cudaStream_t st);
+// every Adam step in one cooperative launch when rmi_train_capacity(dev) >= RMI_GMAX * nmodels
+u32 rmi_train_capacity(int dev);
+cudaError_t launch_rmi_train(RmiModel* models, u32 nmodels, const float* X, const float* Y, float* partial, u32* bar,
+                             u32 steps, float lr, float* losses, u32* err, cudaStream_t st);
 void launch_rmi_reduce(const float* partial, float* grad, float* loss, cudaStream_t st);
 void launch_rmi_tabulate(RmiModel* models, u32 nmodels, cudaStream_t st);
 void launch_leaf_fit(RmiModel* models, u32 nmodels, void* acc, const u64* fitk, const float* fity, cudaStream_t st,

@@ -1,4 +1,4 @@
-"""The allocation-free run sort (mpsm_sort_runs_noalloc) against mpsm_sort_runs.
+"""The allocation-free run sort (mpsm_sort_runs_noalloc) against mpsm_sort_runs and the oracle.
 
 Some callers cannot allocate device memory (a framework owns the pool, or a
 cudaMalloc's device-wide synchronisation is not acceptable on their path); for
@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import gen
+import oracle
 from tests.helpers import from_dev_ptr, random_tuples, same_multiset, to_dev
 
 torch = pytest.importorskip("torch")
@@ -66,3 +67,31 @@ def test_noalloc_sort_rejects_sizes_beyond_the_limit():
         M.sort_runs_noalloc(R, 1025, out)
     rc = M.lib().mpsm_sort_runs_noalloc(R.data_ptr() + 8, 10, 1, out.data_ptr(), None)
     assert rc == M.ERR_INVALID_ARG  # misaligned
+
+
+@pytest.mark.parametrize("run_len", [4096, 8192])
+def test_noalloc_sort_in_place_matches_oracle(run_len):
+    # out == R (allowed by the header), runs of exactly 4096 and 8192 tuples, equal keys
+    rng = np.random.default_rng(run_len)
+    runs = 5
+    R_host = random_tuples(rng, runs * run_len, 1000)
+    want, off = oracle.sort_runs(R_host, runs)
+    R = to_dev(R_host)
+    for call in range(2):
+        M.sort_runs_noalloc(R, runs, R)
+        got = R.cpu().numpy().view(np.uint64)
+        assert (got[:, 0] == want[:, 0]).all(), call
+        for j in range(runs):
+            a, b = int(off[j]), int(off[j + 1])
+            assert same_multiset(got[a:b], want[a:b]), (call, j)
+        R = to_dev(R_host)
+
+
+def test_noalloc_sort_matches_oracle_unique_keys():
+    w = gen.plain(150_000, 10, seed=78)
+    R_host = w.r_host()
+    want, _ = oracle.sort_runs(R_host, 37)
+    R = to_dev(R_host)
+    out = torch.full_like(R, -1)
+    M.sort_runs_noalloc(R, 37, out)
+    assert (out.cpu().numpy().view(np.uint64) == want).all()
