@@ -734,7 +734,7 @@ int fused_results(mpsm_plan* p, uint64_t* out_count, uint64_t* out_checksum) {
 }
 
 int phase_search(mpsm_plan* p) {
-  LAUNCH(K_TILES, launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, p->st));
+  LAUNCH(K_TILES, launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, &p->d_cnt[C_ERR], p->st));
   LAUNCH(K_SEARCH, launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win,
                                  lctx(p, search_learned(p)), p->st, p->nsm));
   CK(cudaGetLastError());
@@ -1250,7 +1250,7 @@ MPSM_API int mpsm_join_batch(mpsm_plan_t* p, const mpsm_job_t* jobs, uint32_t nj
     if (!prc && p->fused) prc = phase_sort_join(p);
     if (!prc && !p->fused) prc = phase_sort_parts(p);
     if (!prc && !p->fused) {
-      LAUNCH(K_TILES, launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, p->st));
+      LAUNCH(K_TILES, launch_tiles(p->d_jobs, p->njobs, p->tile, p->d_tot + T_TILES, &p->d_cnt[C_ERR], p->st));
       LAUNCH(K_SEARCH, launch_search(p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win,
                                      lctx(p, search_learned(p)), p->st, p->nsm));
       LAUNCH(K_JOIN, launch_join(JOIN_AGG, p->d_jobs, p->njobs, p->d_runs, p->xr, p->xs, p->tile, p->d_tot + T_TILES, p->d_win,

@@ -61,10 +61,16 @@ __device__ __forceinline__ u32 find_job(const Job* jobs, u32 njobs, u64 q, F fie
   return lo;
 }
 
-__global__ void __launch_bounds__(1024) k_tiles(Job* jobs, u32 njobs, u32 tile, u64* totals) {
+// A device check that failed earlier in the call (err != 0) may have left S or the
+// runs unsorted: then no tile is searched or joined (the call reports the error).
+__global__ void __launch_bounds__(1024) k_tiles(Job* jobs, u32 njobs, u32 tile, u64* totals, const u32* err) {
   __shared__ u64 s_warp[33];
   __shared__ u64 carry[3];
   if (threadIdx.x == 0) carry[0] = carry[1] = carry[2] = 0;
+  if (*err) {
+    if (threadIdx.x == 0) totals[0] = totals[1] = totals[2] = 0;
+    return;
+  }
   __syncthreads();
   for (u32 base = 0; base < njobs; base += 1024) {
     const u32 i = base + threadIdx.x;
@@ -321,8 +327,14 @@ __global__ void __launch_bounds__(NT_JOIN, 2) k_join(Job* jobs, u32 njobs, const
     for (u32 i = 0; i < IT; ++i) {
       const u32 k = i * NT_JOIN + tid;
       if (k < n) {
-        const u32 b = (u32)((keys[k] - kmin) >> dsh);
-        const u32 bp = k ? (u32)((keys[k - 1] - kmin) >> dsh) : 0u;
+        // the tile is sorted, so every key lies in [kmin, kmax]; the clamp keeps the
+        // writes inside the nbk + 1 entries even if it were not
+        auto bucket = [&](u32 e) {
+          const u64 d = (keys[e] - kmin) >> dsh;
+          return d < (u64)nbk ? (u32)d : nbk - 1u;
+        };
+        const u32 b = bucket(k);
+        const u32 bp = k ? bucket(k - 1) : 0u;
         for (u32 x = (k ? bp + 1u : 0u); x <= b; ++x) dir[x] = (u16)k;
         if (k == n - 1)
           for (u32 x = b + 1u; x <= nbk; ++x) dir[x] = (u16)n;
@@ -358,6 +370,7 @@ __global__ void __launch_bounds__(NT_JOIN, 2) k_join(Job* jobs, u32 njobs, const
           if (key < kmin || key > kmax) continue;
           const u32 bi = (u32)((key - kmin) >> dsh);
           u32 lb = dir[bi], ub = dir[bi + 1];
+          if (ub <= lb) continue;  // an empty bucket (the directory is non-decreasing)
           if (dsh) {  // a bucket spans several keys: narrow [lb, ub) to `key`
             lb += lower_bound_s(keys + lb, ub - lb, key);
             if (lb >= ub || keys[lb] != key) continue;
@@ -387,6 +400,7 @@ __global__ void __launch_bounds__(NT_JOIN, 2) k_join(Job* jobs, u32 njobs, const
             const u32 bi = (u32)((r.key - kmin) >> dsh);
             lb = dir[bi];
             ub = dir[bi + 1];
+            if (ub < lb) ub = lb;
             if (dsh) {
               lb += lower_bound_s(keys + lb, ub - lb, r.key);
               ub = (lb < ub && keys[lb] == r.key) ? equal_run_end(keys, ub, lb, r.key) : lb;
@@ -466,8 +480,8 @@ void init_attrs_join() {
   cudaFuncSetAttribute(k_join<JOIN_WRITE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
-void launch_tiles(Job* jobs, u32 njobs, u32 tile, u64* totals, cudaStream_t st) {
-  k_tiles<<<1, 1024, 0, st>>>(jobs, njobs, tile, totals);
+void launch_tiles(Job* jobs, u32 njobs, u32 tile, u64* totals, const u32* err, cudaStream_t st) {
+  k_tiles<<<1, 1024, 0, st>>>(jobs, njobs, tile, totals, err);
 }
 
 void launch_search(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,

@@ -65,6 +65,16 @@ __device__ __forceinline__ u64 radix_bucket(const LSeg& L, u64 key) {
   return L.mul ? __umul64hi(d, L.mul) : d >> L.shift;
 }
 
+// smallest key offset (key - lo) of MODE_RADIX bucket b (0 < b < F): b << shift, or
+// with mul the smallest d with mulhi(d, mul) >= b, i.e. ceil(b 2^64 / mul)
+__device__ __forceinline__ u64 bucket_start(const LSeg& L, u32 b) {
+  if (!L.mul) return (u64)b << L.shift;
+  const unsigned __int128 num = ((unsigned __int128)b) << 64;
+  u64 q = (u64)(num / L.mul);
+  if ((unsigned __int128)q * L.mul < num) ++q;
+  return q;
+}
+
 __device__ __forceinline__ u64 ld_key_stream(const Tuple* p) {
   return (u64)__ldcs(reinterpret_cast<const long long*>(&p->key));
 }
@@ -186,7 +196,11 @@ __global__ void __launch_bounds__(1024) k_level_plan(const Seg* segs, u32* nseg_
       L.shift = shift;
       L.F = F;
       L.nchunks = (u32)nch;
-      L.pad = (mode == MODE_FINE) ? 1u : 0u;
+      // dense keys (at most 64 key values per tuple): a bucket's keys fill its key range
+      // closely, so that range serves as the child's bounds, and the histogram keeps
+      // exact extremes only for the two edge buckets, which take every key beyond a
+      // sampled range
+      L.nominal = (mode == MODE_RADIX && (s.kmax - s.kmin) / 64u <= s.len) ? 1u : 0u;
       L.bucket_base = (mode == MODE_FINE) ? jobs[s.job].fine_base : 0ull;
     }
     u64 t0, t1, t2;
@@ -304,6 +318,7 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
           b = (u32)((k[i] - kmin) >> L.shift);
         }
         atomicAdd(&scnt[b], 1u);
+        if (MODE == MODE_RADIX && L.nominal && b - 1u < F - 2u) continue;  // an interior bucket of a dense level
         atomicMin(&smin[b], k[i]);
         atomicMax(&smax[b], k[i]);
       }
@@ -321,7 +336,7 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
     for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
       const u32 cnt = scnt[b];
       hrow[b] = cnt;
-      if (cnt) {
+      if (cnt && !(MODE == MODE_RADIX && L.nominal && b - 1u < F - 2u)) {
         atomicMin(&bmin[L.bucket_base + b], smin[b]);
         atomicMax(&bmax[L.bucket_base + b], smax[b]);
         if (btot) atomicAdd(&btot[L.bucket_base + b], (u64)cnt);
@@ -370,6 +385,9 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
         }
         bkmin[b] = mn;
         bkmax[b] = mx;
+      } else if (MODE == MODE_RADIX && L.nominal && b - 1u < F - 2u) {
+        bkmin[b] = L.lo + bucket_start(L, b);
+        bkmax[b] = L.lo + bucket_start(L, b + 1u) - 1ull;
       } else {
         bkmin[b] = bmin[L.bucket_base + b];
         bkmax[b] = bmax[L.bucket_base + b];
@@ -722,7 +740,7 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
     if (tid < nr) {
       const u32* w = fc.swin + 2ull * ((u64)item * fc.maxT + j0 + tid);
       wl[tid] = w[0];
-      wpre[tid] = w[1] - w[0];
+      wpre[tid] = w[1] > w[0] ? w[1] - w[0] : 0u;  // empty unless the run was sorted (a failed check)
       roff[tid] = fc.runs[run_base + j0 + tid].off;
     }
     __syncthreads();

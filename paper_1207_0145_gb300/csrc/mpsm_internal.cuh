@@ -42,7 +42,8 @@ constexpr u32 SEARCH_TB = 32;     // consecutive tiles one search thread walks t
 // where a segment's tuples live
 enum Where : u32 { W_RIN = 0, W_SIN = 1, W_XR = 2, W_XS = 3, W_Y = 4 };
 // segment flag bits above the 3-bit `where`
-constexpr u32 SEG_EXACT = 8u;     // kmin/kmax are the exact extremes of the segment
+constexpr u32 SEG_EXACT = 8u;     // every key of the segment lies in [kmin, kmax] (the extremes, or the
+                                  // key range of the bucket that made it)
 
 // bucket functions of a partitioning pass
 enum PassMode : u32 { MODE_RADIX = 0, MODE_FINE = 1, MODE_SPLIT = 2, MODE_LEARN = 3 };
@@ -98,7 +99,9 @@ struct LSeg {
   u64 hist_base;            // first histogram entry (chunks x F, chunk-major)
   u64 bucket_base;          // first bucket-bound entry (F)
   u32 shift, F;             // bucket = min(F-1, (key - lo) >> shift), or with mul set:
-  u32 nchunks, pad;
+  u32 nchunks;
+  u32 nominal;              // MODE_RADIX on dense keys: buckets 1..F-2 take the key range their
+                            // bucket function gives them instead of their keys' exact extremes
   u64 mul;                  // bucket = min(F-1, mulhi(key - lo, mul)) (MODE_RADIX)
 };
 

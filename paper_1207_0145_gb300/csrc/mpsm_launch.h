@@ -53,7 +53,7 @@ void launch_fold(const Seg* segs, const u32* nseg, const LSeg* ls_fine, const LS
                  int nsm);
 
 // ---- join (k_join.cu)
-void launch_tiles(Job* jobs, u32 njobs, u32 tile, u64* totals, cudaStream_t st);
+void launch_tiles(Job* jobs, u32 njobs, u32 tile, u64* totals, const u32* err, cudaStream_t st);
 void launch_search(const Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,
                    const u64* totals, u32* win, const LearnCtx& lc, cudaStream_t st, int nsm);
 void launch_join(u32 mode, Job* jobs, u32 njobs, const Run* runs, const Tuple* xr, const Tuple* xs, u32 tile,
