@@ -261,7 +261,7 @@ typedef struct {
  * The learned modes (MPSM_SPLIT_LEARNED, MPSM_SEARCH_LEARNED) train, inside
  * every join, one model per job and side: a root MLP over the normalised key
  * (1 -> 32 -> 32 -> 1, ReLU, FP32 weights; Adam, 200 full-batch steps, learning
- * rate 3e-3, on up to 16384 points) and 4096 linear leaves (least squares on
+ * rate 3e-3, on up to 4096 evenly spaced points) and 4096 linear leaves (least squares on
  * the key's exact offset from the leaf's smallest key).  It stands in for the
  * paper's CDF of the runs (Sec. 4.1-4.2, Fig. 8): the S-side model is trained on
  * a sorted sample of S (1/64 of it, at most 2^21 keys) and its quantiles give
@@ -274,7 +274,7 @@ typedef struct {
  *
  * The entry points below run the same kernels on caller data, using model slot
  * 0 of the plan (slot 1 holds job 0's R-side model after a learned join).  All
- * pointers are DEVICE pointers unless marked HOST; x, y are FP32, n <= 16384
+ * pointers are DEVICE pointers unless marked HOST; x, y are FP32, n <= 4096
  * for the gradient and training calls.  The parameter vector theta has 1153
  * floats: W1[32], b1[32], W2[32][32] (row = output unit), b2[32], W3[32], b3. */
 
@@ -288,7 +288,7 @@ int mpsm_rmi_train(mpsm_plan_t* plan, const float* x, const float* y, uint32_t n
                    float* theta, float* losses);
 /* Builds a whole model in slot 0 from n fit points (keys with their CDF values
  * y, n <= the plan's sample capacity): range [kmin, kmax], initial weights,
- * `steps` Adam steps on up to 16384 evenly spaced points, tabulation, leaves. */
+ * `steps` Adam steps on up to 4096 evenly spaced points, tabulation, leaves. */
 int mpsm_rmi_fit(mpsm_plan_t* plan, const uint64_t* keys, const float* y, uint32_t n, uint64_t kmin, uint64_t kmax,
                  uint32_t steps, float lr);
 /* Predicted CDF values (yhat, n floats) and leaves (leaf, n u32, may be NULL) of

@@ -627,7 +627,7 @@ int phase_splitters_learned(mpsm_plan* p) {
   LAUNCH(K_SCAN_LEARN, launch_scan(MODE_LEARN, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_hist_a, p->d_bmin,
                                    p->d_bmax, nullptr, p->d_big[0], &p->d_cnt[C_BIG0], p->big_cap, p->d_fin,
                                    &p->d_cnt[C_FIN], p->fin_cap, W_XS, p->d_jobs, p->d_part_off, &p->d_cnt[C_ERR],
-                                   p->st, p->nsm, p->fused));
+                                   p->st, p->nsm, p->fused, p->d_bnd));
   CK(cudaGetLastError());
   record(p, EV_SPLIT);
   p->stage = ST_SPLIT;
@@ -668,10 +668,13 @@ int phase_splitters(mpsm_plan* p) {
 
 int phase_scatter(mpsm_plan* p) {
   const bool sl = split_learned(p);
+  // learned partitioning with at most 512 partitions per job takes the larger tiles
+  bool small_p = true;
+  for (u32 i = 0; i < p->njobs; ++i) small_p = small_p && p->h_jobs[i].parts_req <= 512u;
   LAUNCH(sl ? K_SCATTER_LEARN : K_SCATTER_SPLIT,
          launch_scatter(sl ? MODE_LEARN : MODE_SPLIT, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls2, p->d_tot + T_SPLIT,
                         p->ch_s, bufs(p), p->d_jobs, W_SIN, W_XS, p->d_hist_a, p->d_sp, &p->d_cnt[C_ERR],
-                        lctx(p, sl), p->st, p->nsm));
+                        lctx(p, sl), p->st, p->nsm, sl && small_p));
   CK(cudaGetLastError());
   record(p, EV_SCATTER);
   p->stage = ST_SCATTER;

@@ -177,18 +177,26 @@ __global__ void k_train_data(RmiModel* models, const u64* fitk, const float* fit
   }
 }
 
-// Forward and backward pass over one block of RMI_GT points.  Shared memory:
-// th[RMI_NPAD] | h1, h2, da2, da1 [RMI_GT][33] | x, g, l [RMI_GT]
-constexpr u32 GP = 33;
-constexpr size_t SMEM_GRAD = (RMI_NPAD + 4 * RMI_GT * GP + 3 * RMI_GT) * sizeof(float);
-
 // Partial gradient (and loss) of model mdl over its training points [blk RMI_GT,
 // (blk + 1) RMI_GT) into out[RMI_NPAD], the weights already in gsm[0, RMI_NPAD).
-// Every thread of the block calls it; a block without points writes zeros.
+// RMI_TPP threads share a point: thread sub = tid % RMI_TPP of point tid / RMI_TPP
+// owns hidden units sub and sub + RMI_TPP of each layer, so every thread's chains
+// are short and a block keeps 16 warps busy.  Shared memory: th[RMI_NPAD] | W2 with
+// rows padded to GP floats (the owners of a point read different banks) | h1, h2,
+// da2, da1 [RMI_GT][GP] | x, g, l [RMI_GT].  Sums over points run in point order;
+// yhat adds its owners' shares.  Every thread of the block calls it; a block without
+// points writes zeros.
+constexpr u32 GP = 33;
+constexpr u32 RMI_TPP = 16;
+constexpr u32 RMI_NTH = RMI_GT * RMI_TPP;
+static_assert(RMI_H == 2 * RMI_TPP, "two units per owner");
+constexpr size_t SMEM_GRAD = (RMI_NPAD + RMI_H * GP + 4 * RMI_GT * GP + 3 * RMI_GT) * sizeof(float);
+
 __device__ __forceinline__ void grad_block(const RmiModel& M, u32 mdl, u32 blk, const float* X, const float* Y,
                                            float* out, float* gsm) {
   float* th = gsm;
-  float* sh1 = th + RMI_NPAD;
+  float* w2 = th + RMI_NPAD;
+  float* sh1 = w2 + RMI_H * GP;
   float* sh2 = sh1 + RMI_GT * GP;
   float* sda2 = sh2 + RMI_GT * GP;
   float* sda1 = sda2 + RMI_GT * GP;
@@ -198,103 +206,115 @@ __device__ __forceinline__ void grad_block(const RmiModel& M, u32 mdl, u32 blk, 
   const u32 tid = threadIdx.x;
   const u32 n = M.active ? M.train_n : 0u;
   if (blk * RMI_GT >= n) {  // no points in this block: a zero partial
-    for (u32 p = tid; p < RMI_NPAD; p += RMI_GT) out[p] = 0.0f;
+    for (u32 p = tid; p < RMI_NPAD; p += RMI_NTH) out[p] = 0.0f;
     return;
   }
-  const u32 q = blk * RMI_GT + tid;
+  for (u32 e = tid; e < RMI_H * RMI_H; e += RMI_NTH) w2[(e >> 5) * GP + (e & 31u)] = th[RO_W2 + e];
+  __syncthreads();
+  const u32 pt = tid / RMI_TPP, sub = tid % RMI_TPP;
+  const u32 q = blk * RMI_GT + pt;
   const bool valid = q < n;
   const float x = valid ? X[(u64)mdl * RMI_TRAIN_MAX + q] : 0.0f;
   const float yv = valid ? Y[(u64)mdl * RMI_TRAIN_MAX + q] : 0.0f;
-  float a1[RMI_H], h2[RMI_H];
+  float a1[RMI_H];
 #pragma unroll
   for (u32 k = 0; k < RMI_H; ++k) a1[k] = fmaf(th[RO_W1 + k], x, th[RO_B1 + k]);
-  float yh = th[RO_B3];
+  float a2[2];
+  float part = 0.0f;
 #pragma unroll
-  for (u32 j = 0; j < RMI_H; ++j) {  // fully unrolled: h2 stays in registers
+  for (u32 jj = 0; jj < 2; ++jj) {
+    const u32 j = sub + jj * RMI_TPP;
     float a = th[RO_B2 + j];
 #pragma unroll
-    for (u32 k = 0; k < RMI_H; ++k) a = fmaf(th[RO_W2 + j * RMI_H + k], fmaxf(a1[k], 0.0f), a);
-    h2[j] = a;  // pre-activation for now
-    yh = fmaf(th[RO_W3 + j], fmaxf(a, 0.0f), yh);
+    for (u32 k = 0; k < RMI_H; ++k) a = fmaf(w2[j * GP + k], fmaxf(a1[k], 0.0f), a);
+    a2[jj] = a;
+    part = fmaf(th[RO_W3 + j], fmaxf(a, 0.0f), part);
   }
+#pragma unroll
+  for (u32 d = 1; d < RMI_TPP; d <<= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+  const float yh = th[RO_B3] + part;
   const float r = yh - yv;
   const float g = valid ? 2.0f * r / (float)n : 0.0f;
-  sx[tid] = x;
-  sg[tid] = g;
-  sl[tid] = valid ? r * r / (float)n : 0.0f;
-  // dL/da2 = g W3 [a2 > 0]; store h2 = relu(a2) and da2
-#pragma unroll
-  for (u32 j = 0; j < RMI_H; ++j) {
-    const bool on = h2[j] > 0.0f;
-    sda2[tid * GP + j] = on ? g * th[RO_W3 + j] : 0.0f;
-    sh2[tid * GP + j] = on ? h2[j] : 0.0f;
+  if (sub == 0) {
+    sx[pt] = x;
+    sg[pt] = g;
+    sl[pt] = valid ? r * r / (float)n : 0.0f;
   }
-  // dL/da1 = [a1 > 0] W2^T da2
+  // dL/da2 = g W3 [a2 > 0]; h2 = relu(a2)
 #pragma unroll
-  for (u32 k = 0; k < RMI_H; ++k) {
-    float s = 0.0f;
+  for (u32 jj = 0; jj < 2; ++jj) {
+    const u32 j = sub + jj * RMI_TPP;
+    const bool on = a2[jj] > 0.0f;
+    sda2[pt * GP + j] = on ? g * th[RO_W3 + j] : 0.0f;
+    sh2[pt * GP + j] = on ? a2[jj] : 0.0f;
+  }
+  __syncwarp();  // a point's owners share a warp
+  // dL/da1 = [a1 > 0] W2^T da2, for k = sub, sub + RMI_TPP
+#pragma unroll
+  for (u32 kk = 0; kk < 2; ++kk) {
+    const u32 k = sub + kk * RMI_TPP;
+    float t = 0.0f;
 #pragma unroll 8
-    for (u32 j = 0; j < RMI_H; ++j) s = fmaf(th[RO_W2 + j * RMI_H + k], sda2[tid * GP + j], s);
-    sda1[tid * GP + k] = a1[k] > 0.0f ? (valid ? s : 0.0f) : 0.0f;
-    sh1[tid * GP + k] = valid ? fmaxf(a1[k], 0.0f) : 0.0f;
+    for (u32 j = 0; j < RMI_H; ++j) t = fmaf(w2[j * GP + k], sda2[pt * GP + j], t);
+    const float ak = fmaf(th[RO_W1 + k], x, th[RO_B1 + k]);  // a1[k], recomputed: k depends on the thread
+    sda1[pt * GP + k] = (ak > 0.0f && valid) ? t : 0.0f;
+    sh1[pt * GP + k] = valid ? fmaxf(ak, 0.0f) : 0.0f;
   }
   __syncthreads();
-  // dW2[j][k] = sum_i da2[i][j] h1[i][k]: entries e = tid + r RMI_GT, r < 8 (warp: fixed j, k = lane),
-  // summed over i in order, all eight in one pass over the points
+  // dW2[j][k] = sum_i da2[i][j] h1[i][k]: entries tid + r RMI_NTH (warp: fixed j, k = lane)
   {
-    constexpr u32 R = (RMI_H * RMI_H) / RMI_GT;
-    const u32 k = tid & 31u, j0 = tid >> 5;  // entry r: j = j0 + r RMI_GT / 32
+    constexpr u32 R = (RMI_H * RMI_H) / RMI_NTH;
+    const u32 k = tid & 31u, j0 = tid >> 5;
     float acc[R];
 #pragma unroll
-    for (u32 r = 0; r < R; ++r) acc[r] = 0.0f;
-#pragma unroll 4
+    for (u32 rr = 0; rr < R; ++rr) acc[rr] = 0.0f;
+#pragma unroll 8
     for (u32 i = 0; i < RMI_GT; ++i) {
       const float h = sh1[i * GP + k];
 #pragma unroll
-      for (u32 r = 0; r < R; ++r) acc[r] = fmaf(sda2[i * GP + j0 + r * (RMI_GT / 32)], h, acc[r]);
+      for (u32 rr = 0; rr < R; ++rr) acc[rr] = fmaf(sda2[i * GP + j0 + rr * (RMI_NTH / 32)], h, acc[rr]);
     }
 #pragma unroll
-    for (u32 r = 0; r < R; ++r) out[RO_W2 + tid + r * RMI_GT] = acc[r];
+    for (u32 rr = 0; rr < R; ++rr) out[RO_W2 + tid + rr * RMI_NTH] = acc[rr];
   }
+  // the other parameters: one sum over the points per thread
   if (tid < 32) {
-    float w = 0.0f, b = 0.0f;
-    for (u32 i = 0; i < RMI_GT; ++i) {
-      const float d = sda1[i * GP + tid];
-      w = fmaf(d, sx[i], w);
-      b += d;
-    }
+    float w = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) w = fmaf(sda1[i * GP + tid], sx[i], w);
     out[RO_W1 + tid] = w;
-    out[RO_B1 + tid] = b;
   } else if (tid < 64) {
-    const u32 j = tid - 32;
-    float b = 0.0f, w = 0.0f;
-    for (u32 i = 0; i < RMI_GT; ++i) {
-      b += sda2[i * GP + j];
-      w = fmaf(sg[i], sh2[i * GP + j], w);
-    }
-    out[RO_B2 + j] = b;
-    out[RO_W3 + j] = w;
-  } else if (tid == 64) {
-    float b = 0.0f, l = 0.0f;
-    for (u32 i = 0; i < RMI_GT; ++i) {
-      b += sg[i];
-      l += sl[i];
-    }
-    out[RO_B3] = b;
+    float bsum = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) bsum += sda1[i * GP + tid - 32];
+    out[RO_B1 + tid - 32] = bsum;
+  } else if (tid < 96) {
+    float bsum = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) bsum += sda2[i * GP + tid - 64];
+    out[RO_B2 + tid - 64] = bsum;
+  } else if (tid < 128) {
+    float w = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) w = fmaf(sg[i], sh2[i * GP + tid - 96], w);
+    out[RO_W3 + tid - 96] = w;
+  } else if (tid == 128) {
+    float bsum = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) bsum += sg[i];
+    out[RO_B3] = bsum;
+  } else if (tid == 129) {
+    float l = 0.0f;
+    for (u32 i = 0; i < RMI_GT; ++i) l += sl[i];
     out[RMI_NP] = l;
-  } else if (tid < 64 + 1 + (RMI_NPAD - RMI_NP - 1)) {
-    out[RMI_NP + (tid - 64)] = 0.0f;  // padding slots
+  } else if (tid < 130 + (RMI_NPAD - RMI_NP - 1)) {
+    out[RMI_NP + 1 + (tid - 130)] = 0.0f;  // padding slots
   }
   __syncthreads();  // the shared arrays may be written again
 }
 
-__global__ void __launch_bounds__(RMI_GT) k_rmi_grad(const RmiModel* models, const float* X, const float* Y,
-                                                     float* partial) {
+__global__ void __launch_bounds__(RMI_NTH) k_rmi_grad(const RmiModel* models, const float* X, const float* Y,
+                                                      float* partial) {
   extern __shared__ __align__(16) float gsm[];
   const RmiModel& M = models[blockIdx.y];
   const u32 n = M.active ? M.train_n : 0u;
   if (blockIdx.x * RMI_GT < n) {
-    for (u32 p = threadIdx.x; p < RMI_NPAD; p += RMI_GT) gsm[p] = M.theta[p];
+    for (u32 p = threadIdx.x; p < RMI_NPAD; p += RMI_NTH) gsm[p] = M.theta[p];
     __syncthreads();
   }
   grad_block(M, blockIdx.y, blockIdx.x, X, Y, partial + ((u64)blockIdx.y * RMI_GMAX + blockIdx.x) * RMI_NPAD, gsm);
@@ -334,132 +354,6 @@ __global__ void __launch_bounds__(1024) k_rmi_reduce(const float* partial, float
   if (threadIdx.x == 0) *loss = sum_partial(partial, 0, RMI_NP);
 }
 
-// The same partial gradient with four threads per point (RMI_GT4 threads): thread
-// sub = tid & 3 of point tid >> 2 owns hidden units j = 4 jj + sub (and k = 4 kk + sub),
-// so every thread's chains are a quarter as long.  Shared memory: th[RMI_NPAD] |
-// W2 again with rows padded to 36 (bank-conflict free for the four threads) |
-// h1, h2, da2, da1 [RMI_GT][33] | x, g, l [RMI_GT].  The sums over points run in
-// point order; the output yhat adds the four threads' shares.
-constexpr u32 RMI_GT4 = 4 * RMI_GT;
-constexpr u32 W2S = 36;
-constexpr size_t SMEM_GRAD4 = (RMI_NPAD + RMI_H * W2S + 4 * RMI_GT * GP + 3 * RMI_GT) * sizeof(float);
-
-__device__ __forceinline__ void grad_block4(const RmiModel& M, u32 mdl, u32 blk, const float* X, const float* Y,
-                                            float* out, float* gsm) {
-  float* th = gsm;
-  float* w2 = th + RMI_NPAD;
-  float* sh1 = w2 + RMI_H * W2S;
-  float* sh2 = sh1 + RMI_GT * GP;
-  float* sda2 = sh2 + RMI_GT * GP;
-  float* sda1 = sda2 + RMI_GT * GP;
-  float* sx = sda1 + RMI_GT * GP;
-  float* sg = sx + RMI_GT;
-  float* sl = sg + RMI_GT;
-  const u32 tid = threadIdx.x;
-  const u32 n = M.active ? M.train_n : 0u;
-  if (blk * RMI_GT >= n) {
-    for (u32 p = tid; p < RMI_NPAD; p += RMI_GT4) out[p] = 0.0f;
-    return;
-  }
-  for (u32 e = tid; e < RMI_H * RMI_H; e += RMI_GT4) w2[(e >> 5) * W2S + (e & 31u)] = th[RO_W2 + e];
-  __syncthreads();
-  const u32 pt = tid >> 2, sub = tid & 3u;
-  const u32 q = blk * RMI_GT + pt;
-  const bool valid = q < n;
-  const float x = valid ? X[(u64)mdl * RMI_TRAIN_MAX + q] : 0.0f;
-  const float yv = valid ? Y[(u64)mdl * RMI_TRAIN_MAX + q] : 0.0f;
-  float a1[RMI_H];
-#pragma unroll
-  for (u32 k = 0; k < RMI_H; ++k) a1[k] = fmaf(th[RO_W1 + k], x, th[RO_B1 + k]);
-  float a2[RMI_H / 4];
-  float part = 0.0f;
-#pragma unroll
-  for (u32 jj = 0; jj < RMI_H / 4; ++jj) {
-    const u32 j = 4 * jj + sub;
-    float a = th[RO_B2 + j];
-#pragma unroll
-    for (u32 k = 0; k < RMI_H; ++k) a = fmaf(w2[j * W2S + k], fmaxf(a1[k], 0.0f), a);
-    a2[jj] = a;
-    part = fmaf(th[RO_W3 + j], fmaxf(a, 0.0f), part);
-  }
-  part += __shfl_xor_sync(0xffffffffu, part, 1);
-  part += __shfl_xor_sync(0xffffffffu, part, 2);
-  const float yh = th[RO_B3] + part;
-  const float r = yh - yv;
-  const float g = valid ? 2.0f * r / (float)n : 0.0f;
-  if (sub == 0) {
-    sx[pt] = x;
-    sg[pt] = g;
-    sl[pt] = valid ? r * r / (float)n : 0.0f;
-  }
-  // dL/da2 = g W3 [a2 > 0]; h2 = relu(a2)
-#pragma unroll
-  for (u32 jj = 0; jj < RMI_H / 4; ++jj) {
-    const u32 j = 4 * jj + sub;
-    const bool on = a2[jj] > 0.0f;
-    sda2[pt * GP + j] = on ? g * th[RO_W3 + j] : 0.0f;
-    sh2[pt * GP + j] = on ? a2[jj] : 0.0f;
-  }
-  __syncwarp();
-  // dL/da1 = [a1 > 0] W2^T da2, for k = 4 kk + sub
-#pragma unroll
-  for (u32 kk = 0; kk < RMI_H / 4; ++kk) {
-    const u32 k = 4 * kk + sub;
-    float t = 0.0f;
-#pragma unroll 8
-    for (u32 j = 0; j < RMI_H; ++j) t = fmaf(w2[j * W2S + k], sda2[pt * GP + j], t);
-    const float ak = fmaf(th[RO_W1 + k], x, th[RO_B1 + k]);  // a1[k], recomputed: k depends on the thread
-    sda1[pt * GP + k] = (ak > 0.0f && valid) ? t : 0.0f;
-    sh1[pt * GP + k] = valid ? fmaxf(ak, 0.0f) : 0.0f;
-  }
-  __syncthreads();
-  // dW2[j][k] = sum_i da2[i][j] h1[i][k]: entries tid and tid + RMI_GT4 (warp: fixed j, k = lane)
-  {
-    constexpr u32 R = (RMI_H * RMI_H) / RMI_GT4;
-    const u32 k = tid & 31u, j0 = tid >> 5;
-    float acc[R];
-#pragma unroll
-    for (u32 rr = 0; rr < R; ++rr) acc[rr] = 0.0f;
-#pragma unroll 4
-    for (u32 i = 0; i < RMI_GT; ++i) {
-      const float h = sh1[i * GP + k];
-#pragma unroll
-      for (u32 rr = 0; rr < R; ++rr) acc[rr] = fmaf(sda2[i * GP + j0 + rr * (RMI_GT4 / 32)], h, acc[rr]);
-    }
-#pragma unroll
-    for (u32 rr = 0; rr < R; ++rr) out[RO_W2 + tid + rr * RMI_GT4] = acc[rr];
-  }
-  // the other parameters: one sum over the points per thread
-  if (tid < 32) {
-    float w = 0.0f;
-    for (u32 i = 0; i < RMI_GT; ++i) w = fmaf(sda1[i * GP + tid], sx[i], w);
-    out[RO_W1 + tid] = w;
-  } else if (tid < 64) {
-    float b = 0.0f;
-    for (u32 i = 0; i < RMI_GT; ++i) b += sda1[i * GP + tid - 32];
-    out[RO_B1 + tid - 32] = b;
-  } else if (tid < 96) {
-    float b = 0.0f;
-    for (u32 i = 0; i < RMI_GT; ++i) b += sda2[i * GP + tid - 64];
-    out[RO_B2 + tid - 64] = b;
-  } else if (tid < 128) {
-    float w = 0.0f;
-    for (u32 i = 0; i < RMI_GT; ++i) w = fmaf(sg[i], sh2[i * GP + tid - 96], w);
-    out[RO_W3 + tid - 96] = w;
-  } else if (tid == 128) {
-    float b = 0.0f;
-    for (u32 i = 0; i < RMI_GT; ++i) b += sg[i];
-    out[RO_B3] = b;
-  } else if (tid == 129) {
-    float l = 0.0f;
-    for (u32 i = 0; i < RMI_GT; ++i) l += sl[i];
-    out[RMI_NP] = l;
-  } else if (tid < 130 + (RMI_NPAD - RMI_NP - 1)) {
-    out[RMI_NP + 1 + (tid - 130)] = 0.0f;  // padding slots
-  }
-  __syncthreads();
-}
-
 // Barrier of the RMI_GMAX blocks of one model, which a cooperative launch keeps
 // resident together: each block adds one to the model's arrival count, which only
 // grows, and waits until it reaches RMI_GMAX times the number of barriers passed so
@@ -496,7 +390,7 @@ constexpr u32 ADAM_SLICE = (RMI_NP + 1 + RMI_GMAX - 1) / RMI_GMAX;  // parameter
 // them; after a second barrier every block reads the new weights.  bar holds two
 // zeroed words per model; a barrier that gives up sets DERR_TMA_TIMEOUT in err.
 // losses (optional, one model): the loss before each step.
-__global__ void __launch_bounds__(RMI_GT4, 2) k_rmi_train(RmiModel* models, const float* X, const float* Y,
+__global__ void __launch_bounds__(RMI_NTH, 2) k_rmi_train(RmiModel* models, const float* X, const float* Y,
                                                       float* partial, u32* bar, u32 steps, float lr, u32 limit,
                                                       float* losses, u32* err) {
   extern __shared__ __align__(16) float gsm[];
@@ -510,16 +404,16 @@ __global__ void __launch_bounds__(RMI_GT4, 2) k_rmi_train(RmiModel* models, cons
   const float* all = partial + (u64)mdl * RMI_GMAX * RMI_NPAD;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   for (u32 step = 1; step <= steps; ++step) {
-    for (u32 p = tid; p < RMI_NPAD; p += RMI_GT4) gsm[p] = __ldcg(&M.theta[p]);  // other blocks wrote them
+    for (u32 p = tid; p < RMI_NPAD; p += RMI_NTH) gsm[p] = __ldcg(&M.theta[p]);  // other blocks wrote them
     __syncthreads();
-    grad_block4(M, mdl, blk, X, Y, out, gsm);
+    grad_block(M, mdl, blk, X, Y, out, gsm);
     if (!model_barrier(cnt, phase, limit)) {
       if (tid == 0) atomicOr(err, (u32)DERR_TMA_TIMEOUT);
       return;
     }
     const float c1 = 1.0f - powf(b1, (float)step);
     const float c2 = 1.0f - powf(b2, (float)step);
-    for (u32 k = wid; k < ADAM_SLICE; k += RMI_GT4 / 32) {
+    for (u32 k = wid; k < ADAM_SLICE; k += RMI_NTH / 32) {
       const u32 p = blk * ADAM_SLICE + k;
       if (p > RMI_NP) break;  // the same for the whole warp
       float g = 0.0f;
@@ -748,13 +642,13 @@ void launch_rmi_predict(const RmiModel* M, const u64* keys, u64 n, float* yhat, 
 
 void init_attrs_learn() {
   cudaFuncSetAttribute(k_rmi_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GRAD);
-  cudaFuncSetAttribute(k_rmi_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GRAD4);
+  cudaFuncSetAttribute(k_rmi_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_GRAD);
 }
 
 // blocks of k_rmi_train that can be resident at once on this device
 u32 rmi_train_capacity(int dev) {
   int per_sm = 0, nsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rmi_train, RMI_GT4, SMEM_GRAD4) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rmi_train, RMI_NTH, SMEM_GRAD) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -769,8 +663,8 @@ cudaError_t launch_rmi_train(RmiModel* models, u32 nmodels, const float* X, cons
   if (e != cudaSuccess) return e;
   u32 limit = 1u << 22;  // polls of a barrier (at least 64 ns each) before it gives up
   void* args[] = {&models, &X, &Y, &partial, &bar, &steps, &lr, &limit, &losses, &err};
-  return cudaLaunchCooperativeKernel((const void*)k_rmi_train, dim3(RMI_GMAX, nmodels), dim3(RMI_GT4), args,
-                                     SMEM_GRAD4, st);
+  return cudaLaunchCooperativeKernel((const void*)k_rmi_train, dim3(RMI_GMAX, nmodels), dim3(RMI_NTH), args,
+                                     SMEM_GRAD, st);
 }
 
 size_t leaf_acc_bytes() { return sizeof(LeafAcc) * RMI_LEAVES; }
@@ -792,7 +686,7 @@ void launch_train_data(RmiModel* models, u32 nmodels, const u64* fitk, const flo
 
 void launch_rmi_grad(const RmiModel* models, u32 nmodels, const float* X, const float* Y, float* partial,
                      cudaStream_t st) {
-  k_rmi_grad<<<dim3(RMI_GMAX, nmodels), RMI_GT, SMEM_GRAD, st>>>(models, X, Y, partial);
+  k_rmi_grad<<<dim3(RMI_GMAX, nmodels), RMI_NTH, SMEM_GRAD, st>>>(models, X, Y, partial);
 }
 
 void launch_rmi_adam(RmiModel* models, u32 nmodels, const float* partial, u32 step, float lr, cudaStream_t st) {

@@ -282,6 +282,9 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
     const u64 row0 = S.off - jobs[S.job].s_base;  // MODE_LEARN: row of the tuple in the job's S
     u32 probes = 0, keys = 0;
     u32 fit_n = 0;
+    // learned partitions of a dense job (at most 64 key values per S tuple) take their
+    // boundaries as bounds: only the counts are needed here
+    const bool ldense = MODE == MODE_LEARN && (kmax - kmin) / 64u <= jobs[S.job].nS;
     if (MODE == MODE_LEARN) {
       const Job& J = jobs[S.job];
       for (u32 f = threadIdx.x; f < J.nfine; f += NT_PASS) scell[f] = lc.cell[J.fine_base + f];
@@ -319,6 +322,7 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
         }
         atomicAdd(&scnt[b], 1u);
         if (MODE == MODE_RADIX && L.nominal && b - 1u < F - 2u) continue;  // an interior bucket of a dense level
+        if (ldense) continue;
         atomicMin(&smin[b], k[i]);
         atomicMax(&smax[b], k[i]);
       }
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
     for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
       const u32 cnt = scnt[b];
       hrow[b] = cnt;
-      if (cnt && !(MODE == MODE_RADIX && L.nominal && b - 1u < F - 2u)) {
+      if (cnt && !ldense && !(MODE == MODE_RADIX && L.nominal && b - 1u < F - 2u)) {
         atomicMin(&bmin[L.bucket_base + b], smin[b]);
         atomicMax(&bmax[L.bucket_base + b], smax[b]);
         if (btot) atomicAdd(&btot[L.bucket_base + b], (u64)cnt);
@@ -352,7 +356,7 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
                                                   const u64* bmin, const u64* bmax, const u32* part_fstart,
                                                   Seg* big_out, u32* big_cnt, u32 big_cap, Seg* fin_out,
                                                   u32* fin_cnt, u32 fin_cap, u32 dst_where, u32 final_where,
-                                                  Job* jobs, u64* part_off, u32* err) {
+                                                  Job* jobs, u64* part_off, u32* err, const u64* lbnd) {
   extern __shared__ __align__(128) unsigned char sm_raw[];
   u64* start = reinterpret_cast<u64*>(sm_raw);  // F_MAX + 1
   u64* bkmin = start + (F_MAX + 1);             // F_MAX
@@ -385,6 +389,12 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
         }
         bkmin[b] = mn;
         bkmax[b] = mx;
+      } else if (MODE == MODE_LEARN && lbnd && (J.kmax - J.kmin) / 64u <= J.nS) {
+        // a dense job's learned partition b holds keys in [bnd[b - 1], bnd[b]] (a hot key
+        // equal to boundaries is spread over the partitions it bounds)
+        const u64* bj = lbnd + (u64)S.job * P_MAX;
+        bkmin[b] = b == 0 ? J.kmin : bj[b - 1];
+        bkmax[b] = b + 1 == F ? J.kmax : bj[b];
       } else if (MODE == MODE_RADIX && L.nominal && b - 1u < F - 2u) {
         bkmin[b] = L.lo + bucket_start(L, b);
         bkmax[b] = L.lo + bucket_start(L, b + 1u) - 1ull;
@@ -460,7 +470,7 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
 // Each thread owns F_MAX / NT_SC buckets in the scan and keeps their write
 // offsets in registers, so one pass over the counters per tile scans them,
 // publishes each bucket's offset and clears the counts.
-template <u32 MODE, u32 SC_TILE, u32 NT_SC, u32 SC_MINB, u32 STAGES>
+template <u32 MODE, u32 SC_TILE, u32 NT_SC, u32 SC_MINB, u32 STAGES, u32 LPCAP = P_MAX>
 __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, const u32* nseg_ptr, const LSeg* ls,
                                                         const u64* totals, u64 chunk, Bufs bufs, const Job* jobs,
                                                         u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
@@ -475,10 +485,16 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
   u32* gb = hb + F_MAX;                                            // F_MAX
   u16* sidx = reinterpret_cast<u16*>(gb + F_MAX);                  // SC_TILE
   u16* sb = sidx + SC_TILE;                                        // SC_TILE
+  // MODE_LEARN keeps the fine-cell table as u32 entries, or -- with LPCAP < P_MAX, for at
+  // most LPCAP partitions -- as u16 (start partition, LCELL_SPLIT and LCELL_HOT in bits 15
+  // and 14) with the end partition of each cut cell in sphi[start] (cut cells start at
+  // different partitions)
+  constexpr bool LCOMPACT = LPCAP < P_MAX;
   u16* spl = sb + SC_TILE;                                         // FINE_MAX u16 (MODE_SPLIT) or
-  u32* spl32 = reinterpret_cast<u32*>(spl);                        //   FINE_MAX u32 (MODE_LEARN)
-  u64* sbnd = reinterpret_cast<u64*>(spl32 + FINE_MAX);            // P_MAX (MODE_LEARN)
-  u32* srank = reinterpret_cast<u32*>(sbnd + P_MAX);               // 2 P_MAX (MODE_LEARN)
+  u32* spl32 = reinterpret_cast<u32*>(spl);                        //   the MODE_LEARN cell table
+  u64* sbnd = reinterpret_cast<u64*>(LCOMPACT ? (void*)(spl + FINE_MAX) : (void*)(spl32 + FINE_MAX));  // LPCAP
+  u32* srank = reinterpret_cast<u32*>(sbnd + LPCAP);               // 2 LPCAP (MODE_LEARN)
+  u16* sphi = reinterpret_cast<u16*>(srank + 2 * LPCAP);           // LPCAP (compact MODE_LEARN)
   __shared__ __align__(8) u64 mbar[STAGES];
   __shared__ u32 s_seg;
   __shared__ u32 s_warp[NT_SC / 32 + 1];
@@ -511,10 +527,17 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
       const Job& J = jobs[S.job];
       kmin = J.kmin;
       kmax = J.kmax;
-      if (MODE == MODE_SPLIT)
+      if (MODE == MODE_SPLIT) {
         for (u32 f = tid; f < J.nfine; f += NT_SC) spl[f] = (u16)sp[J.fine_base + f];
-      else
+      } else if (LCOMPACT) {
+        for (u32 f = tid; f < J.nfine; f += NT_SC) {
+          const u32 e = lc.cell[J.fine_base + f];
+          spl[f] = (u16)((e & 0x3FFFu) | ((e & LCELL_SPLIT) ? 0x8000u : 0u) | ((e & LCELL_HOT) ? 0x4000u : 0u));
+          if (e & LCELL_SPLIT) sphi[e & 0x3FFFu] = (u16)((e >> 16) & 0x3FFFu);
+        }
+      } else {
         for (u32 f = tid; f < J.nfine; f += NT_SC) spl32[f] = lc.cell[J.fine_base + f];
+      }
     }
     u32 fit_n = 0;
     if (MODE == MODE_LEARN) {
@@ -569,8 +592,15 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
           b = d >= F ? F - 1u : (u32)d;
         } else if (MODE == MODE_LEARN) {
           if (key < kmin || key > kmax) continue;
-          b = learned_cell_part(spl32[(key - kmin) >> L.shift], sbnd, srank, F, fit_n, key, row0 + t0 + x, lc.seed,
-                                probes);
+          u32 e;
+          if (LCOMPACT) {
+            const u32 c = spl[(key - kmin) >> L.shift];
+            e = (c & 0x3FFFu) | ((c & 0x4000u) ? LCELL_HOT : 0u) |
+                ((c & 0x8000u) ? (LCELL_SPLIT | ((u32)sphi[c & 0x3FFFu] << 16)) : 0u);
+          } else {
+            e = spl32[(key - kmin) >> L.shift];
+          }
+          b = learned_cell_part(e, sbnd, srank, F, fit_n, key, row0 + t0 + x, lc.seed, probes);
         } else {
           if (key < kmin || key > kmax) continue;
           b = spl[(key - kmin) >> L.shift];
@@ -1273,10 +1303,13 @@ __global__ void k_check_empty(const u32* cnt, u32* err, u32 flag) {
   if (threadIdx.x == 0 && *cnt != 0) atomicOr(err, flag);
 }
 
-constexpr size_t smem_scatter(u32 tile, u32 stages = 1, bool learn = false) {
+constexpr size_t smem_scatter(u32 tile, u32 stages = 1, bool learn = false, u32 lpcap = P_MAX) {
   return stages * tile * sizeof(Tuple) + 3 * F_MAX * sizeof(u32) + 2 * tile * sizeof(u16) +
-         FINE_MAX * (learn ? sizeof(u32) : sizeof(u16)) + (learn ? P_MAX * (sizeof(u64) + 2 * sizeof(u32)) : 0);
+         FINE_MAX * ((learn && lpcap == P_MAX) ? sizeof(u32) : sizeof(u16)) +
+         (learn ? lpcap * (sizeof(u64) + 2 * sizeof(u32) + (lpcap < P_MAX ? sizeof(u16) : 0)) : 0);
 }
+// the learned partitioning of jobs with at most LN_SMALL partitions: two 5120-tuple buffers
+constexpr u32 LN_SMALL = 512;
 // the learned partitioning pass: two 4096-tuple buffers per block (one block per SM), so
 // the partition boundaries and their ranks fit beside them in shared memory
 constexpr u32 LN_TILE = 4096, LN_NT = 1024;
@@ -1302,6 +1335,8 @@ void init_attrs_pass() {
   set_smem(k_hist<MODE_LEARN, F_MAX>, SMEM_HIST_LEARN);
   set_smem(k_scan<MODE_LEARN>, SMEM_SCAN);
   set_smem(k_scatter<MODE_LEARN, LN_TILE, LN_NT, 1, 2>, smem_scatter(LN_TILE, 2, true));
+  set_smem(k_scatter<MODE_LEARN, RX_TILE, RX_NT, RX_MINB, RX_STAGES, LN_SMALL>,
+           smem_scatter(RX_TILE, RX_STAGES, true, LN_SMALL));
   set_smem(k_scan<MODE_RADIX>, SMEM_SCAN);
   set_smem(k_scan<MODE_SPLIT>, SMEM_SCAN);
   set_smem(k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB, RX_STAGES>, smem_scatter(RX_TILE, RX_STAGES));
@@ -1353,22 +1388,22 @@ void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, con
 void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32* hist, const u64* bmin,
                  const u64* bmax, const u32* part_fstart, Seg* big_out, u32* big_cnt, u32 big_cap, Seg* fin_out,
                  u32* fin_cnt, u32 fin_cap, u32 dst_where, Job* jobs, u64* part_off, u32* err, cudaStream_t st,
-                 int nsm, bool keep_const) {
+                 int nsm, bool keep_const, const u64* lbnd) {
   // constant-key children already at their final place are skipped unless the
   // fused sort-and-join must still see them
   const u32 final_where = (!keep_const && (dst_where == W_XR || dst_where == W_XS)) ? dst_where : 0xFFu;
   if (mode == MODE_SPLIT) {
     k_scan<MODE_SPLIT><<<nsm * 2, NT_PASS, SMEM_SCAN, st>>>(segs, nseg, ls, hist, bmin, bmax, part_fstart, big_out,
                                                             big_cnt, big_cap, fin_out, fin_cnt, fin_cap, dst_where,
-                                                            final_where, jobs, part_off, err);
+                                                            final_where, jobs, part_off, err, lbnd);
   } else if (mode == MODE_LEARN) {
     k_scan<MODE_LEARN><<<nsm * 2, NT_PASS, SMEM_SCAN, st>>>(segs, nseg, ls, hist, bmin, bmax, part_fstart, big_out,
                                                             big_cnt, big_cap, fin_out, fin_cnt, fin_cap, dst_where,
-                                                            final_where, jobs, part_off, err);
+                                                            final_where, jobs, part_off, err, lbnd);
   } else {
     k_scan<MODE_RADIX><<<nsm * 2, NT_PASS, SMEM_SCAN, st>>>(segs, nseg, ls, hist, bmin, bmax, part_fstart, big_out,
                                                             big_cnt, big_cap, fin_out, fin_cnt, fin_cap, dst_where,
-                                                            final_where, jobs, part_off, err);
+                                                            final_where, jobs, part_off, err, lbnd);
   }
 }
 
@@ -1378,6 +1413,10 @@ void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, 
   if (mode == MODE_SPLIT) {
     k_scatter<MODE_SPLIT, RX_TILE, RX_NT, RX_MINB, RX_STAGES><<<nsm * RX_MINB, RX_NT, smem_scatter(RX_TILE, RX_STAGES), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
+  } else if (mode == MODE_LEARN && big_tiles) {  // every job has at most LN_SMALL partitions
+    k_scatter<MODE_LEARN, RX_TILE, RX_NT, RX_MINB, RX_STAGES, LN_SMALL>
+        <<<nsm * RX_MINB, RX_NT, smem_scatter(RX_TILE, RX_STAGES, true, LN_SMALL), st>>>(
+            segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   } else if (mode == MODE_LEARN) {
     k_scatter<MODE_LEARN, LN_TILE, LN_NT, 1, 2><<<nsm, LN_NT, smem_scatter(LN_TILE, 2, true), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);

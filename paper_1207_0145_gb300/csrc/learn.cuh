@@ -29,8 +29,8 @@ constexpr u32 RMI_NPAD = 1156;           // padded; slot RMI_NP carries the loss
 constexpr u32 RMI_LEAVES = 4096;
 constexpr u32 RMI_CELL_BITS = 16;
 constexpr u32 RMI_CELLS = 1u << RMI_CELL_BITS;
-constexpr u32 RMI_TRAIN_MAX = 16384;     // training points per model
-constexpr u32 RMI_GT = 128;              // points per block of the gradient kernel
+constexpr u32 RMI_TRAIN_MAX = 4096;      // training points per model (evenly spaced over its sample)
+constexpr u32 RMI_GT = 32;               // points per block of the gradient kernel
 constexpr u32 RMI_GMAX = RMI_TRAIN_MAX / RMI_GT;
 // parameter vector layout: W1[32], b1[32], W2[32][32] (row = output unit), b2[32], W3[32], b3
 constexpr u32 RO_W1 = 0, RO_B1 = 32, RO_W2 = 64, RO_B2 = 1088, RO_W3 = 1120, RO_B3 = 1152;

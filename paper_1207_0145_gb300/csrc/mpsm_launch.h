@@ -26,7 +26,8 @@ void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, con
 void launch_scan(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, u32* hist, const u64* bmin,
                  const u64* bmax, const u32* part_fstart, Seg* big_out, u32* big_cnt, u32 big_cap, Seg* fin_out,
                  u32* fin_cnt, u32 fin_cap, u32 dst_where, Job* jobs, u64* part_off, u32* err, cudaStream_t st,
-                 int nsm, bool keep_const = false);
+                 int nsm, bool keep_const = false,
+                 const u64* lbnd = nullptr);  // MODE_LEARN: the learned boundaries (P_MAX per job)
 void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                     Bufs bufs, const Job* jobs, u32 src_where, u32 dst_where, const u32* hist, const u32* sp,
                     u32* err, const LearnCtx& lc, cudaStream_t st, int nsm, bool big_tiles = false);
