@@ -235,6 +235,15 @@ typedef struct {
 /* Statistics of the last join (job 0 of a batch).  Synchronises. */
 int mpsm_plan_stats(mpsm_plan_t* plan, mpsm_stats_t* stats);
 
+/* A final S segment of the fused path: `length` tuples at `offset` of the view's
+ * s_buffer ((flags & 7) == 3) or pass_buffer ((flags & 7) == 4), every key in
+ * [key_lo, key_hi] (the bounds its windows are searched for). */
+typedef struct {
+  uint64_t offset, length;
+  uint64_t key_lo, key_hi;
+  uint32_t job, flags;             /* the job; where the tuples are (bits 0-2) and internal flags */
+} mpsm_segment_t;
+
 typedef struct {
   const mpsm_tuple_t* r_runs;      /* device: nR tuples, the T_R sorted runs back to back      */
   const uint64_t* run_offsets;     /* device: T_R + 1 run boundaries                            */
@@ -255,6 +264,15 @@ typedef struct {
   uint64_t tiles;                  /* S tiles of phase 4                                         */
   uint32_t join_tile;              /* S tuples per tile (tile t = [t*join_tile, ...) of s_buffer) */
   const uint32_t* windows;         /* device: tiles x T_R x 2 (start, end) relative to the run    */
+  /* the fused path (mpsm_join without pairs, Sec. 3.2 phases 3 and 4 in one pass): the final S
+   * segments that its last pass sorted and joined in shared memory, and their windows */
+  const mpsm_segment_t* segments;  /* device: n_segments records (order unspecified)             */
+  uint32_t n_segments;
+  uint32_t window_stride;          /* runs per row of seg_windows (>= T_R)                       */
+  const uint32_t* seg_windows;     /* device: n_segments x window_stride x 2: for segment i and run
+                                      j < T_R, [first position with key >= key_lo, first position
+                                      with key > key_hi), relative to the run (Sec. 3.2.2)        */
+  const mpsm_tuple_t* pass_buffer; /* device: the radix passes' ping-pong buffer                  */
 } mpsm_view_t;
 
 /* ---- learned CDF model (two-stage recursive model index) ----------------------

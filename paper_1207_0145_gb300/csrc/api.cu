@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <new>
 #include <vector>
@@ -81,6 +82,8 @@ struct mpsm_plan {
   cudaStream_t st_copy = nullptr;
   cudaEvent_t ev_run_copied = nullptr, ev_part_copied = nullptr;
   bool part_copy_pending = false;
+  bool runs_reused = false;         // a later piece of a host join: the runs' fences and per-bucket
+                                    // counts from the first piece still hold
   // piecewise host join: one event per piece of the partitioned side that has landed
   static constexpr u32 MAX_PIECES = 64;
   cudaEvent_t ev_piece[MAX_PIECES] = {};
@@ -638,7 +641,7 @@ int phase_splitters(mpsm_plan* p) {
   if (int rc = wait_part_copy(p)) return rc;
   if (split_learned(p)) return phase_splitters_learned(p);
   const u32 nj = p->njobs;
-  CK(cudaMemsetAsync(p->d_rc, 0, (u64)nj * (FINE_MAX + 1) * sizeof(u64), p->st));
+  if (!p->runs_reused) CK(cudaMemsetAsync(p->d_rc, 0, (u64)nj * (FINE_MAX + 1) * sizeof(u64), p->st));
   CK(cudaMemsetAsync(p->d_fine_s, 0, (u64)nj * FINE_MAX * sizeof(u64), p->st));
   CK(cudaMemsetAsync(p->d_fine_min, 0xFF, (u64)nj * FINE_MAX * sizeof(u64), p->st));
   CK(cudaMemsetAsync(p->d_fine_max, 0, (u64)nj * FINE_MAX * sizeof(u64), p->st));
@@ -648,7 +651,7 @@ int phase_splitters(mpsm_plan* p) {
                     p->hist_b_cap, ~0ull, &p->d_cnt[C_ERR], p->st));
   LAUNCH(K_HIST_FINE, launch_hist(MODE_FINE, p->d_split, &p->d_cnt[C_SPLIT], p->d_ls, tf, p->ch_s, bufs(p), p->d_jobs, W_SIN,
               p->d_hist_b, p->d_fine_min, p->d_fine_max, p->d_fine_s, lctx(p, false), p->st, p->nsm));
-  LAUNCH(K_RUN_CDF, launch_run_cdf(p->d_jobs, nj, p->d_runs, p->xr, p->d_rc, p->st));
+  if (!p->runs_reused) LAUNCH(K_RUN_CDF, launch_run_cdf(p->d_jobs, nj, p->d_runs, p->xr, p->d_rc, p->st));
   LAUNCH(K_SPLITTERS, launch_splitters(p->d_jobs, nj, p->d_fine_s, p->d_rc, p->d_fine_r, p->d_sp, p->d_fstart, &p->d_cnt[C_ERR], p->st,
                                        p->opt.splitter_mode == MPSM_SPLIT_EQUI_HEIGHT));
   LAUNCH(K_PLAN, launch_level_plan(p->d_split, &p->d_cnt[C_SPLIT], p->max_jobs, p->d_ls2, ts, MODE_SPLIT, p->ch_s, 11, p->d_jobs,
@@ -712,7 +715,7 @@ int phase_sort_join(mpsm_plan* p) {
   record(p, EV_SORTS);
   u64 totR = 0;
   for (u32 i = 0; i < p->njobs; ++i) totR += p->h_jobs[i].nR;
-  LAUNCH(K_FENCES, launch_fences(p->xr, totR, p->d_fence, p->st, p->nsm));
+  if (!p->runs_reused) LAUNCH(K_FENCES, launch_fences(p->xr, totR, p->d_fence, p->st, p->nsm));
   LAUNCH(K_SEG_SEARCH, launch_seg_search(p->d_fin, &p->d_cnt[C_FIN], p->fin_cap, p->d_jobs, p->d_runs, p->xr, p->d_fence,
                                          p->d_swin, p->maxT, lctx(p, search_learned(p)), p->st, p->nsm));
   record(p, EV_SEARCH);
@@ -1153,6 +1156,7 @@ static int join_host_pieces(mpsm_plan* p, Tuple* run_dst, const Tuple* run_src, 
     if ((rc = phase_runs(p))) break;
     for (u32 i = 0; i < K && rc == MPSM_OK; ++i) {
       const u64 a = (u64)i * piece, len = std::min(piece, n_part - a);
+      p->runs_reused = i > 0;  // the run side's fences and per-bucket counts depend on the runs only
       if (i) {
         launch_set_part(p->d_jobs, p->d_split, part_dst + a, len, p->st);
         if ((rc = cuda_status(cudaGetLastError()))) break;
@@ -1166,6 +1170,7 @@ static int join_host_pieces(mpsm_plan* p, Tuple* run_dst, const Tuple* run_src, 
     }
     if (rc == MPSM_OK) rc = fused_results(p, out_count, out_checksum);
   } while (false);
+  p->runs_reused = false;
   // nothing later on the plan's stream may overlap the copies, on the error paths too
   CK(cudaStreamWaitEvent(p->st, p->ev_part_copied, 0));
   return rc;
@@ -1453,8 +1458,21 @@ MPSM_API int mpsm_plan_view(mpsm_plan_t* p, mpsm_view_t* v) {
   v->tiles = J.ntiles;
   v->join_tile = p->tile;
   v->windows = p->d_win + 2 * J.win_base;
+  if (p->fused) {
+    u32 nfin = 0;
+    CK(cudaMemcpy(&nfin, &p->d_cnt[C_FIN], sizeof(u32), cudaMemcpyDeviceToHost));
+    v->segments = reinterpret_cast<const mpsm_segment_t*>(p->d_fin);
+    v->n_segments = std::min(nfin, p->fin_cap);
+    v->window_stride = p->maxT;
+    v->seg_windows = p->d_swin;
+  }
+  v->pass_buffer = reinterpret_cast<const mpsm_tuple_t*>(p->y);
   return MPSM_OK;
 }
+
+static_assert(sizeof(mpsm_segment_t) == sizeof(Seg) && offsetof(mpsm_segment_t, key_hi) == offsetof(Seg, kmax) &&
+                  offsetof(mpsm_segment_t, flags) == offsetof(Seg, flags),
+              "mpsm_segment_t mirrors the segment records");
 
 static_assert(DERR_SEG_OVERFLOW == MPSM_DEVERR_LIST_OVERFLOW && DERR_SEG_TOO_BIG == MPSM_DEVERR_SEGMENT_TOO_BIG &&
                   DERR_TMA_TIMEOUT == MPSM_DEVERR_WAIT_TIMEOUT && DERR_LEVELS == MPSM_DEVERR_LEVELS &&

@@ -85,7 +85,8 @@ class View(ctypes.Structure):
                 ("nfine", _u32), ("fine_shift", _u32), ("fine_s", _p), ("fine_r", _p), ("splitters", _p),
                 ("partitions_s", _u32), ("s_chunks", _u32), ("s_chunk_offsets", _p), ("chunk_offsets", _p),
                 ("part_offsets", _p), ("s_buffer", _p), ("s_kept", _u64), ("tiles", _u64), ("join_tile", _u32),
-                ("windows", _p)]
+                ("windows", _p), ("segments", _p), ("n_segments", _u32), ("window_stride", _u32),
+                ("seg_windows", _p), ("pass_buffer", _p)]
 
 
 _lib = None

@@ -61,7 +61,9 @@ int main(void) {
   F(mpsm_stats_t, launches);
   printf("mpsm_kernel_time_t %zu\n", sizeof(mpsm_kernel_time_t));
   F(mpsm_view_t, key_min); F(mpsm_view_t, fine_s); F(mpsm_view_t, s_chunks); F(mpsm_view_t, windows);
-  F(mpsm_view_t, join_tile); F(mpsm_view_t, s_kept);
+  F(mpsm_view_t, join_tile); F(mpsm_view_t, s_kept); F(mpsm_view_t, segments); F(mpsm_view_t, n_segments);
+  F(mpsm_view_t, window_stride); F(mpsm_view_t, seg_windows);
+  printf("mpsm_segment_t %zu\n", sizeof(mpsm_segment_t));
   return 0;
 }
 """
@@ -81,6 +83,7 @@ def test_ctypes_structs_match_header(tmp_path):
     assert int(got["mpsm_pairs_t"]) == ctypes.sizeof(M.Pairs)
     assert int(got["mpsm_kernel_time_t"]) == ctypes.sizeof(M.KernelTime)
     assert int(got["mpsm_rmi_info_t"]) == ctypes.sizeof(M.RmiInfo)
+    assert int(got["mpsm_segment_t"]) == 40
     for key, val in got.items():
         if "." not in key:
             continue
