@@ -582,7 +582,9 @@ def run_ours(args):
         elif name == "join":
             units_launch = (st["s_kept"] + n_run) * kt_steps / n
         elif name == "seg_sort":
-            units_launch = (n_run + st["s_kept"]) * kt_steps / n  # the two final sorts share the family
+            # the runs' final sort; without the fused sort-and-join the partitions' final sort too
+            sorted_units = n_run if "sort_join" in ktimes else n_run + st["s_kept"]
+            units_launch = sorted_units * kt_steps / n
         else:
             units_launch = (w.n_r + w.n_s) * kt_steps / n
         alg_bytes = per_unit * units_launch
