@@ -21,6 +21,7 @@
 // segment with a bulk async copy (TMA) into shared memory and radix-sorts it
 // there (first digit by an unstable counting pass, further digits by stable
 // warp-ballot ranking), then writes it out in order.
+#include <algorithm>
 #include <mutex>
 
 #include "mpsm.h"
@@ -33,6 +34,7 @@ namespace mpsm {
 namespace {
 
 constexpr u32 NT_PASS = 512;
+constexpr u32 SCAN_UNROLL = 8;  // histogram rows read per group in k_scan
 // scatter geometry (measured): the first radix pass over runs or partitions (fan-out
 // up to 2048) and the range-partition scatter run one 1024-thread block per SM on
 // two 5120-tuple buffers, so the next tile loads while the current one is ranked and
@@ -372,12 +374,17 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
     u32* h = hist + L.hist_base;
     const Job J = jobs[S.job];
     for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
-      u64 run = 0;
-      for (u64 c = 0; c < C; ++c) {
-        const u32 v = h[c * F + b];
-        h[c * F + b] = (u32)run;
-        run += v;
+      // the bucket's total over the chunks; its per-chunk offsets are written below,
+      // once the bucket's start is known (loads issued in groups, not one per round trip)
+      u64 run = 0, c = 0;
+      for (; c + SCAN_UNROLL <= C; c += SCAN_UNROLL) {
+        u32 v[SCAN_UNROLL];
+#pragma unroll
+        for (u32 q = 0; q < SCAN_UNROLL; ++q) v[q] = h[(c + q) * F + b];
+#pragma unroll
+        for (u32 q = 0; q < SCAN_UNROLL; ++q) run += v[q];
       }
+      for (; c < C; ++c) run += h[c * F + b];
       start[b] = run;
       if (MODE == MODE_SPLIT) {
         const u32 fa = part_fstart[J.part_base + b], fb = part_fstart[J.part_base + b + 1];
@@ -407,9 +414,25 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
     const u64 total = smem_exclusive_scan<u64, NT_PASS, F_MAX / NT_PASS>(start, F, s_warp);
     if (threadIdx.x == 0) start[F] = total;
     __syncthreads();
+    // ps_i[b] = start of bucket b + the counts of chunks k < i (u32: offsets within the segment)
     for (u32 b = threadIdx.x; b < F; b += NT_PASS) {
-      const u32 base = (u32)start[b];
-      for (u64 c = 0; c < C; ++c) h[c * F + b] += base;
+      u32 run = (u32)start[b];
+      u64 c = 0;
+      for (; c + SCAN_UNROLL <= C; c += SCAN_UNROLL) {
+        u32 v[SCAN_UNROLL];
+#pragma unroll
+        for (u32 q = 0; q < SCAN_UNROLL; ++q) v[q] = h[(c + q) * F + b];
+#pragma unroll
+        for (u32 q = 0; q < SCAN_UNROLL; ++q) {
+          h[(c + q) * F + b] = run;
+          run += v[q];
+        }
+      }
+      for (; c < C; ++c) {
+        const u32 v = h[c * F + b];
+        h[c * F + b] = run;
+        run += v;
+      }
     }
     if (MODE == MODE_SPLIT || MODE == MODE_LEARN) {
       for (u32 b = threadIdx.x; b <= F; b += NT_PASS) part_off[J.part_base + b] = start[b];
@@ -733,10 +756,18 @@ __device__ __forceinline__ void flush_job_result(u64& acc_cnt, u64& acc_chk, u32
 // and their prefix sums at a time, so every thread takes any window position.
 constexpr u32 RCH = 128;
 
+// The window of run tid (< RCH) of the block's segment, read by thread tid when the
+// segment starts, so that its latency hides behind the sort; the first RCH runs'
+// windows are staged from these registers.
+struct WinReg {
+  u32 lo, hi;  // window [lo, hi) in the run
+  u64 off;     // the run's first position in xr
+};
+
 template <u32 CAP, u32 NT>
 __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* dir, u32* rtab, const u32* cdir, u32 n,
-                                         u64 mn, u64 mx, const Seg& sg, u32 item, const FuseCtx& fc, u64& cnt,
-                                         u64& chk) {
+                                         u64 mn, u64 mx, const Seg& sg, u32 item, const FuseCtx& fc, const WinReg& wr,
+                                         u64& cnt, u64& chk) {
   constexpr u32 DB = (CAP >= 8192u) ? 12u : 11u;  // 2^DB = CAP / 2 buckets
   const u32 tid = threadIdx.x;
   const Job& J = fc.jobs[sg.job];
@@ -768,10 +799,21 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
     // barrier after the placement comes right before the first chunk)
     if (j0 || !cdir) __syncthreads();
     if (tid < nr) {
-      const u32* w = fc.swin + 2ull * ((u64)item * fc.maxT + j0 + tid);
-      wl[tid] = w[0];
-      wpre[tid] = w[1] > w[0] ? w[1] - w[0] : 0u;  // empty unless the run was sorted (a failed check)
-      roff[tid] = fc.runs[run_base + j0 + tid].off;
+      u32 lo, hi;
+      u64 off;
+      if (j0 == 0) {
+        lo = wr.lo;
+        hi = wr.hi;
+        off = wr.off;
+      } else {
+        const u32* w = fc.swin + 2ull * ((u64)item * fc.maxT + j0 + tid);
+        lo = w[0];
+        hi = w[1];
+        off = fc.runs[run_base + j0 + tid].off;
+      }
+      wl[tid] = lo;
+      wpre[tid] = hi > lo ? hi - lo : 0u;  // empty unless the run was sorted (a failed check)
+      roff[tid] = off;
     }
     __syncthreads();
     if (tid < 32) {  // exclusive scan of the window lengths, 4 per lane
@@ -948,6 +990,7 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
       publish_next();
       continue;
     }
+    WinReg wr{0u, 0u, 0ull};
     // The fused join is exact for any split of S into pieces joined against windows
     // that cover their keys, so a segment above CAP is sorted and joined in pieces.
     bool failed = false;
@@ -957,6 +1000,17 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     if (!published) {
       publish_next();
       published = true;
+      // fused: run tid's window of this segment, read while the copy is in flight and
+      // used by the join after the sort
+      if (FUSE) {
+        const Job& J = fc.jobs[sg.job];
+        if (tid < J.runs && tid < RCH) {
+          const u32* w = fc.swin + 2ull * ((u64)item * fc.maxT + tid);
+          wr.lo = w[0];
+          wr.hi = w[1];
+          wr.off = fc.runs[J.run_base + tid].off;
+        }
+      }
     }
     // the counting pass's counters, cleared while the copy is in flight (their last
     // readers passed the barrier before this piece; the one after the wait orders it)
@@ -1031,6 +1085,14 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
       if (tid == 0) atomicOr(err, (u32)DERR_BOUNDS);
       failed = true;
       break;
+    }
+    // fused: ask L2 for this thread's R window (by 128-byte line), so the join's loads
+    // find it there
+    if (FUSE && p0 == 0 && wr.hi > wr.lo) {
+      const char* wp = reinterpret_cast<const char*>(fc.xr + wr.off + wr.lo);
+      const char* we = reinterpret_cast<const char*>(fc.xr + wr.off + wr.hi);
+      for (const char* q = (const char*)((size_t)wp & ~(size_t)127); q < we; q += 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
     }
     smem_exclusive_scan<u32, NT, 2048 / NT>(cnt, F1, s_warp);
     if (tid == 0) cnt[F1] = n;  // with bits <= 11, cnt is then the start of every key value
@@ -1109,10 +1171,10 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     }
     if (FUSE) {
       if (bits <= 11u)  // one counting pass: its digit starts are an exact per-key directory
-        seg_join<CAP, NT>(tup, ia, nullptr, reinterpret_cast<u32*>(ib), cnt, n, mn, mx, sg, item, fc, acc_cnt,
+        seg_join<CAP, NT>(tup, ia, nullptr, reinterpret_cast<u32*>(ib), cnt, n, mn, mx, sg, item, fc, wr, acc_cnt,
                           acc_chk);
       else
-        seg_join<CAP, NT>(tup, ia, ib, cnt, nullptr, n, mn, mx, sg, item, fc, acc_cnt, acc_chk);
+        seg_join<CAP, NT>(tup, ia, ib, cnt, nullptr, n, mn, mx, sg, item, fc, wr, acc_cnt, acc_chk);
     } else {
       for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, tup[ia[i]]);
     }
@@ -1135,15 +1197,26 @@ __global__ void k_fences(const Tuple* xr, u64 n, u64* fence) {
     fence[g] = xr[g * 64].key;
 }
 
+// Every gs-th fence of one run [g0, g1), staged in shared memory by the block that
+// searches that run: a fence search then bisects ntop shared entries and at most
+// gs - 1 fences instead of all g1 - g0.
+constexpr u32 TOP_CAP = 2048;
+struct TopFences {
+  const u64* top;  // top[t] = fence[g0 + t * gs], t < ntop
+  u32 ntop;
+  u64 gs;
+};
+
 // first position of run [off, off + len) whose key is >= key (upper: > key), minus off;
-// the fences are searched by bisection or (interp) by interpolation search.  With
+// the fences are searched by bisection (narrowed first by `tf`, the run's staged
+// top-level fences, when given) or (interp) by interpolation search.  With
 // `from` (an upper bound after the lower bound of a key <= this one), the fence search
 // gallops forward from the fence the lower bound stopped at, *from, instead: a window
 // is short, so its end is a fence or two on, in lines the lower bound brought into L2.
 // `at` receives the fence the search stopped at.
 __device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 off, u64 len, u64 key, bool upper,
                                          u32& probes, bool interp = false, const u64* from = nullptr,
-                                         u64* at = nullptr) {
+                                         u64* at = nullptr, TopFences tf = TopFences{nullptr, 0u, 1ull}) {
   const u64 end = off + len;
   u64 lo = off, hi = end;
   const u64 g0 = (off + 63) / 64, g1 = len ? (end - 1) / 64 + 1 : g0;
@@ -1179,6 +1252,26 @@ __device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 
         }
         a = next + 1;
         step <<= 1;
+      }
+    } else if (tf.top) {
+      // first staged fence past the key: the answer lies in the gs fences up to it
+      u32 t = 0, tm = tf.ntop;
+      while (tm > 0) {
+        const u32 h = tm >> 1;
+        const u64 f = tf.top[t + h];
+        if (!(upper ? f > key : f >= key)) {
+          t += h + 1;
+          tm -= h + 1;
+        } else {
+          tm = h;
+        }
+      }
+      if (t == 0) {
+        m = 0;  // the run's first fence is already past the key
+      } else {
+        a = g0 + (u64)(t - 1) * tf.gs + 1;
+        const u64 b = g0 + (u64)t * tf.gs;
+        m = (b < g1 ? b : g1) - a;
       }
     } else if (interp) {
       if (upper && key == ~0ull) {
@@ -1225,20 +1318,62 @@ __device__ __forceinline__ u64 run_bound(const Tuple* xr, const u64* fence, u64 
 // fence search for the start and a gallop over the fences to the end (or the
 // paper's interpolation search over the fences), or with the learned R-side
 // model its predicted position times the run length followed by an exact
-// exponential + binary search
-__global__ void k_seg_search(const Seg* segs, const u32* nseg_ptr, u32 cap, const Job* jobs, const Run* runs,
-                             const Tuple* xr, const u64* fence, u32* swin, u32 maxT, LearnCtx lc) {
+// exponential + binary search.  Block (x, j) takes run j of every segment
+// x, x + gridDim.x, ... (in blockDim-sized groups); for the fence search it stages
+// run j's top-level fences (of the job its first segment belongs to) in shared
+// memory, and a segment of another job searches the fences alone.
+constexpr u32 NT_SEARCH = 256;
+
+__global__ void __launch_bounds__(NT_SEARCH, 6) k_seg_search(const Seg* segs, const u32* nseg_ptr, u32 cap,
+                                                          const Job* jobs, const Run* runs, const Tuple* xr,
+                                                          const u64* fence, u32* swin, u32 maxT, LearnCtx lc) {
+  __shared__ u64 s_top[TOP_CAP];
+  __shared__ u32 s_run;
+  __shared__ u32 s_ntop;
+  __shared__ u64 s_gs;
   u32 nseg = *nseg_ptr;
   if (nseg > cap) nseg = cap;
-  const u64 total = (u64)nseg * maxT;
+  const u32 j = blockIdx.y;
+  const u32 tid = threadIdx.x;
   u32 probes = 0, nsearch = 0;
   u64 err_sum = 0;
-  for (u64 idx = (u64)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (u64)gridDim.x * blockDim.x) {
-    const u32 item = (u32)(idx / maxT), j = (u32)(idx - (u64)item * maxT);
+  const bool staged = !lc.models && !lc.interp;
+  if (staged) {
+    if (tid == 0) {
+      s_run = 0xFFFFFFFFu;
+      s_ntop = 0;
+      s_gs = 1;
+      const u32 first = blockIdx.x * NT_SEARCH;
+      if (first < nseg) {
+        const Job& J = jobs[segs[first].job];
+        if (j < J.runs) {
+          const Run r = runs[J.run_base + j];
+          const u64 g0 = (r.off + 63) / 64, g1 = r.len ? (r.off + r.len - 1) / 64 + 1 : g0;
+          const u64 nf = g1 - g0;
+          const u64 gs = nf > TOP_CAP ? (nf + TOP_CAP - 1) / TOP_CAP : 1ull;
+          s_run = J.run_base + j;
+          s_gs = gs;
+          s_ntop = (u32)((nf + gs - 1) / gs);
+        }
+      }
+    }
+    __syncthreads();
+    if (s_run != 0xFFFFFFFFu) {
+      const Run r = runs[s_run];
+      const u64 g0 = (r.off + 63) / 64;
+      for (u32 t = tid; t < s_ntop; t += NT_SEARCH) s_top[t] = fence[g0 + (u64)t * s_gs];
+    }
+    __syncthreads();
+  }
+  const TopFences none{nullptr, 0u, 1ull};
+  const TopFences tf = staged ? TopFences{s_top, s_ntop, s_gs} : none;
+  for (u64 item = (u64)blockIdx.x * NT_SEARCH + tid; item < nseg; item += (u64)gridDim.x * NT_SEARCH) {
     const Seg sg = segs[item];
     const Job& J = jobs[sg.job];
     if (j >= J.runs) continue;
-    const Run r = runs[J.run_base + j];
+    const u64 idx = item * maxT + j;
+    const u32 ri = J.run_base + j;
+    const Run r = runs[ri];
     if (lc.models) {
       const RmiModel* M = &lc.models[2 * sg.job + 1];
       const Tuple* a = xr + r.off;
@@ -1257,7 +1392,8 @@ __global__ void k_seg_search(const Seg* segs, const u32* nseg_ptr, u32 cap, cons
       swin[2 * idx + 1] = (u32)hi;
     } else {  // fences by bisection, or by interpolation search (Sec. 3.2.2)
       u64 a = 0;
-      swin[2 * idx] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmin, false, probes, lc.interp, nullptr, &a);
+      const TopFences t = (staged && ri == s_run) ? tf : none;
+      swin[2 * idx] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmin, false, probes, lc.interp, nullptr, &a, t);
       swin[2 * idx + 1] = (u32)run_bound(xr, fence, r.off, r.len, sg.kmax, true, probes, lc.interp, &a);
     }
     nsearch += 2;
@@ -1373,7 +1509,7 @@ void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, con
                  const LearnCtx& lc, cudaStream_t st, int nsm) {
   if (mode == MODE_RADIX) {
     const size_t sm = F_MAX * 20;
-    k_hist<MODE_RADIX, F_MAX><<<nsm * 4, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs, src_where,
+    k_hist<MODE_RADIX, F_MAX><<<nsm * 2, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs, src_where,
                                                              hist, bmin, bmax, btot, lc);
   } else if (mode == MODE_LEARN) {
     k_hist<MODE_LEARN, F_MAX><<<nsm * 2, NT_PASS, SMEM_HIST_LEARN, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
@@ -1453,7 +1589,10 @@ void launch_fences(const Tuple* xr, u64 n, u64* fence, cudaStream_t st, int nsm)
 
 void launch_seg_search(const Seg* segs, const u32* nseg, u32 cap, const Job* jobs, const Run* runs, const Tuple* xr,
                        const u64* fence, u32* swin, u32 maxT, const LearnCtx& lc, cudaStream_t st, int nsm) {
-  k_seg_search<<<nsm * 8, 256, 0, st>>>(segs, nseg, cap, jobs, runs, xr, fence, swin, maxT, lc);
+  if (!maxT) return;
+  // one wave of six blocks per SM over all runs (gridDim.y = maxT <= RUNS_MAX)
+  const u32 bx = std::max<u32>(1u, (u32)((nsm * 6 + maxT - 1) / maxT));
+  k_seg_search<<<dim3(bx, maxT), NT_SEARCH, 0, st>>>(segs, nseg, cap, jobs, runs, xr, fence, swin, maxT, lc);
 }
 
 void launch_narrow_bounds_test(Seg* segs, const u32* nseg, u32 cap, cudaStream_t st) {

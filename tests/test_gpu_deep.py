@@ -51,11 +51,14 @@ def test_sparse_deep_levels_runs_and_partitions():
         assert p.merge_join() == oracle.join(R, S) == oracle.closed_form(w)
 
 
-@pytest.mark.parametrize("w", [gen.sparse(1 << 20, 1 << 21, seed=72), gen.plain(1 << 20, 1 << 22, seed=73),
-                               gen.zipf(1 << 19, 1 << 21, 1.1, seed=74)])
-def test_fused_segment_windows_match_oracle(w):
+# runs of 32K tuples (the automatic count) put every fence of a run in the search's
+# shared-memory top level; runs of 512K and 350K tuples make it every 4th and 3rd one
+@pytest.mark.parametrize("w,runs", [(gen.sparse(1 << 20, 1 << 21, seed=72), 0), (gen.plain(1 << 20, 1 << 22, seed=73), 0),
+                                    (gen.zipf(1 << 19, 1 << 21, 1.1, seed=74), 0),
+                                    (gen.plain(1 << 20, 1 << 22, seed=76), 2), (gen.sparse(1 << 20, 1 << 21, seed=77), 3)])
+def test_fused_segment_windows_match_oracle(w, runs):
     R, S = w.r_host(), w.s_host()
-    with Plan(w.n_r, w.n_s) as p:
+    with Plan(w.n_r, w.n_s, runs_r=runs) as p:
         assert p.join(to_dev(R), to_dev(S)) == oracle.join(R, S)
         v = p.view()
         T = v.runs_r
