@@ -285,8 +285,11 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
     u32 probes = 0, keys = 0;
     u32 fit_n = 0;
     // learned partitions of a dense job (at most 64 key values per S tuple) take their
-    // boundaries as bounds: only the counts are needed here
+    // boundaries as bounds: only the counts are needed here.  Likewise the interior fine
+    // buckets of a dense job: a partition's bounds then come from its buckets' key ranges,
+    // and only the two edge buckets keep exact extremes
     const bool ldense = MODE == MODE_LEARN && (kmax - kmin) / 64u <= jobs[S.job].nS;
+    const bool fdense = MODE == MODE_FINE && (kmax - kmin) / 64u <= jobs[S.job].nS;
     if (MODE == MODE_LEARN) {
       const Job& J = jobs[S.job];
       for (u32 f = threadIdx.x; f < J.nfine; f += NT_PASS) scell[f] = lc.cell[J.fine_base + f];
@@ -324,6 +327,7 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
         }
         atomicAdd(&scnt[b], 1u);
         if (MODE == MODE_RADIX && L.nominal && b - 1u < F - 2u) continue;  // an interior bucket of a dense level
+        if (fdense && b - 1u < F - 2u) continue;                            // an interior fine bucket of a dense job
         if (ldense) continue;
         atomicMin(&smin[b], k[i]);
         atomicMax(&smax[b], k[i]);
@@ -343,8 +347,10 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
       const u32 cnt = scnt[b];
       hrow[b] = cnt;
       if (cnt && !ldense && !(MODE == MODE_RADIX && L.nominal && b - 1u < F - 2u)) {
-        atomicMin(&bmin[L.bucket_base + b], smin[b]);
-        atomicMax(&bmax[L.bucket_base + b], smax[b]);
+        if (!(fdense && b - 1u < F - 2u)) {
+          atomicMin(&bmin[L.bucket_base + b], smin[b]);
+          atomicMax(&bmax[L.bucket_base + b], smax[b]);
+        }
         if (btot) atomicAdd(&btot[L.bucket_base + b], (u64)cnt);
       }
     }
@@ -388,9 +394,16 @@ __global__ void __launch_bounds__(NT_PASS) k_scan(const Seg* segs, const u32* ns
       start[b] = run;
       if (MODE == MODE_SPLIT) {
         const u32 fa = part_fstart[J.part_base + b], fb = part_fstart[J.part_base + b + 1];
+        // a dense job's interior fine buckets contribute their key ranges (the fine
+        // histogram kept exact extremes only for the edge buckets, as k_hist says)
+        const bool dense = (J.kmax - J.kmin) / 64u <= J.nS;
         u64 mn = ~0ull, mx = 0;
         for (u32 f = fa; f < fb; ++f) {
-          const u64 a = bmin[J.fine_base + f], z = bmax[J.fine_base + f];
+          u64 a = bmin[J.fine_base + f], z = bmax[J.fine_base + f];
+          if (dense && f - 1u < J.nfine - 2u) {
+            a = J.kmin + ((u64)f << J.fine_shift);
+            z = J.kmin + ((u64)(f + 1u) << J.fine_shift) - 1ull;
+          }
           mn = a < mn ? a : mn;
           mx = z > mx ? z : mx;
         }
