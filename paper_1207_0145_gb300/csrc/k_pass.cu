@@ -86,11 +86,20 @@ __device__ __forceinline__ void emit(Seg* out, u32* cnt, u32 cap, const Seg& s, 
   if (i < cap) out[i] = s; else atomicOr(err, (u32)DERR_SEG_OVERFLOW);
 }
 
-__device__ __forceinline__ u32 find_seg(const LSeg* ls, u32 n, u64 c) {
-  u32 lo = 0, hi = n;  // last s with chunk_base <= c
-  while (hi - lo > 1) {
-    const u32 mid = (lo + hi) >> 1;
-    if (ls[mid].chunk_base <= c) lo = mid; else hi = mid;
+// last s in [0, n) with ls[s].chunk_base <= c (ls[0].chunk_base is 0): a 32-way search
+// by one whole warp, so a chunk's segment costs about log32(n) dependent loads
+__device__ __forceinline__ u32 find_seg_warp(const LSeg* ls, u32 n, u64 c) {
+  const u32 lane = lane_id();
+  u32 lo = 0, len = n;  // the answer lies in [lo, lo + len), and ls[lo].chunk_base <= c
+  while (len > 1) {
+    const u32 step = (len + 31u) / 32u;
+    const u32 idx = lo + lane * step;
+    const bool ok = lane * step < len && ls[idx].chunk_base <= c;
+    const u32 m = __ballot_sync(0xffffffffu, ok);  // lane 0 always holds
+    const u32 k = 31u - (u32)__clz(m);
+    const u32 end = lo + len;
+    lo += k * step;
+    len = end - lo < step ? end - lo : step;
   }
   return lo;
 }
@@ -261,7 +270,10 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
   const u64 nch = totals[0];
   const u32 nseg = *nseg_ptr;
   for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
-    if (threadIdx.x == 0) s_seg = find_seg(ls, nseg, c);
+    if (threadIdx.x < 32) {
+      const u32 sg = find_seg_warp(ls, nseg, c);
+      if (threadIdx.x == 0) s_seg = sg;
+    }
     __syncthreads();
     const LSeg L = ls[s_seg];
     const Seg S = segs[s_seg];
@@ -543,7 +555,10 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
   const u32 nseg = *nseg_ptr;
   Tuple* dbase = dst_where == W_XR ? bufs.xr : (dst_where == W_XS ? bufs.xs : bufs.y);
   for (u64 c = blockIdx.x; c < nch; c += gridDim.x) {
-    if (tid == 0) s_seg = find_seg(ls, nseg, c);
+    if (tid < 32) {
+      const u32 sg = find_seg_warp(ls, nseg, c);
+      if (tid == 0) s_seg = sg;
+    }
     __syncthreads();
     const LSeg L = ls[s_seg];
     const Seg S = segs[s_seg];
