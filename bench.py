@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--splitter", default="hist", choices=["hist", "learned", "equi-height"])
     ap.add_argument("--fine-bits", type=int, default=0, help="B, fine histogram bits of S (0 = 12)")
     ap.add_argument("--search", default="binary", choices=["binary", "learned", "interp"])
+    ap.add_argument("--run-buckets", default="radix", choices=["radix", "learned"],
+                    help="bucket function of the runs' first sort pass")
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
     ap.add_argument("--pairs", action="store_true", help="materialise the matching pairs (|S| x 16 B buffer)")
     ap.add_argument("--side", default="s", choices=["s", "r", "smaller"], help="input that is range-partitioned")
@@ -515,6 +517,7 @@ def run_ours(args):
     plan = Plan(w.n_r, w.n_s, stream=stream.cuda_stream, runs_r=args.runs, partitions_s=args.parts,
                 partition_side={"s": 0, "r": 1, "smaller": 2}[args.side],
                 splitter_mode=SPLITTER_MODES[args.splitter], search_mode=SEARCH_MODES[args.search],
+                run_buckets={"radix": 0, "learned": 1}[args.run_buckets],
                 fine_bits=args.fine_bits)
 
     # the run side and the partitioned side (swapped under role reversal)
@@ -654,7 +657,11 @@ def run_ours(args):
         arms = {
             "zipf": arm_modes("zipf0.9-200M-800M", [("hist", {"splitter_mode": 0}), ("learned", {"splitter_mode": 1})],
                               args.seed, dev, local),
-            "sparse": arm_modes("sparse-1600M-1600M", [("binary", {"search_mode": 0}), ("learned", {"search_mode": 1})],
+            # learned: the runs' first sort pass cut at the run side's sample quantiles; the
+            # learned merge-start search alone is timed too
+            "sparse": arm_modes("sparse-1600M-1600M", [("binary", {"search_mode": 0}),
+                                                       ("learned", {"search_mode": 0, "run_buckets": 1}),
+                                                       ("learned_search", {"search_mode": 1})],
                                 args.seed, dev, local),
         }
         b = batch_measure(args.seed, ARM_STEPS, ARM_WARMUP, True, dev, local)
@@ -686,7 +693,8 @@ def run_ours(args):
                                                                                   key=lambda kv: -kv[1][1])},
             "levels": [st["levels_r"], st["levels_s"]], "imbalance": st["imbalance"],
             "balance": balance,
-            "modes": {"splitter": args.splitter, "search": args.search, "pairs": bool(args.pairs),
+            "modes": {"splitter": args.splitter, "search": args.search, "run_buckets": args.run_buckets,
+                      "pairs": bool(args.pairs),
                       "partitioned": args.side},
             "learned": {k: st[k] for k in ("ms_learn", "loss_s0", "loss_s", "loss_r0", "loss_r", "part_probes",
                                            "search_probes", "search_err", "part_max")},

@@ -70,6 +70,13 @@ enum { MPSM_SEARCH_BINARY = 0, MPSM_SEARCH_LEARNED = 1, MPSM_SEARCH_INTERP = 2 }
  * range-partitioned; the other one is cut into sorted runs.  The result does not
  * depend on it (pairs keep their (r_payload, s_payload) order either way). */
 enum { MPSM_PART_S = 0, MPSM_PART_R = 1, MPSM_PART_SMALLER = 2 };
+/* Bucket function of the first sort pass over each run (Sec. 3.2.1 radix clustering):
+ * RADIX takes equal-width ranges of the run's key range; LEARNED takes the quantiles of an
+ * evenly spaced sample of the run-side input, sorted first (the empirical CDF the
+ * learned splitters use, Sec. 4.1-4.2), so skewed or clustered keys still fill every
+ * bucket evenly and the runs need fewer passes.  A key equal to several quantiles goes
+ * whole to the first bucket they bound.  The sorted runs are the same. */
+enum { MPSM_RUNS_RADIX = 0, MPSM_RUNS_LEARNED = 1 };
 enum {
   MPSM_FLAG_TIMING = 1u,          /* record per-phase CUDA events (read by mpsm_plan_stats)        */
   MPSM_FLAG_KERNEL_TIMING = 2u,   /* record CUDA events around every kernel launch (read by
@@ -101,7 +108,8 @@ typedef struct {
   uint32_t partition_side; /* MPSM_PART_*: mpsm_join / mpsm_join_host partition S (default), R,
                               or the smaller input; the plan is then sized for either role.
                               The phase entry points and mpsm_join_batch use the default      */
-  uint32_t reserved[3];    /* must be zero                                                   */
+  uint32_t run_buckets;    /* MPSM_RUNS_*: bucket function of the runs' first sort pass      */
+  uint32_t reserved[2];    /* must be zero                                                   */
 } mpsm_options_t;
 
 /* Fills *opt with the defaults (all automatic, histogram splitters, binary search). */

@@ -47,14 +47,16 @@ enum Kid {
   K_SAMPLE, K_PLAN, K_INIT, K_HIST_RADIX, K_SCAN_RADIX, K_SCATTER_RADIX, K_SEG_SORT, K_RUN_BOUNDS, K_HIST_FINE,
   K_RUN_CDF, K_SPLITTERS, K_FOLD, K_SCAN_SPLIT, K_SCATTER_SPLIT, K_TILES, K_SEARCH, K_JOIN, K_PAIR_OFFSETS, K_CHECK,
   K_SAMPLE_S, K_RMI_DATA, K_RMI_GRAD, K_RMI_ADAM, K_RMI_TAB, K_RMI_LEAF, K_LEARN_BOUNDS, K_HIST_LEARN, K_SCAN_LEARN,
-  K_SCATTER_LEARN, K_FENCES, K_SEG_SEARCH, K_SORT_JOIN, K_RMI_TRAIN, K_NUM
+  K_SCATTER_LEARN, K_FENCES, K_SEG_SEARCH, K_SORT_JOIN, K_RMI_TRAIN, K_SAMPLE_R, K_RLEARN_TAB, K_HIST_RLEARN,
+  K_SCATTER_RLEARN, K_NUM
 };
 const char* const KNAME[K_NUM] = {"sample_bounds", "level_plan", "init_buckets", "hist_radix", "scan_radix",
                                   "scatter_radix", "seg_sort", "run_bounds", "hist_fine", "run_cdf", "splitters",
                                   "fold", "scan_split", "scatter_split", "tiles", "search", "join", "pair_offsets",
                                   "check_empty", "sample_s", "rmi_data", "rmi_grad", "rmi_adam", "rmi_tabulate",
                                   "rmi_leaves", "learn_bounds", "hist_learn", "scan_learn", "scatter_learn",
-                                  "fences", "seg_search", "sort_join", "rmi_train"};
+                                  "fences", "seg_search", "sort_join", "rmi_train", "sample_r", "rlearn_tables",
+                                  "hist_rlearn", "scatter_rlearn"};
 // learned model: sample and training sizes
 constexpr u32 RMI_SAMPLE_MAX = 1u << 21;  // largest sample per model
 constexpr u32 RMI_STEPS = 200;            // full-batch Adam steps
@@ -161,6 +163,15 @@ struct mpsm_plan {
   u32* d_brank = nullptr;           // their sample ranks, 2 P_MAX per job
   u64* d_lstat = nullptr;           // learned-path counters (LearnCtx::stat)
   mpsm_plan* sub = nullptr;         // sorts the S samples (one run per job)
+  // learned run bucket function (MPSM_RUNS_LEARNED)
+  RunLearn* d_rl = nullptr;         // per job
+  u32* d_rcell = nullptr;           // cell tables, FINE_MAX per job
+  u64* d_rbnd = nullptr;            // boundaries, P_MAX per job
+  Tuple* d_rsamp = nullptr;         // unsorted run-side samples (the run sub-plan's R input)
+  u64 rsamp_cap = 0;
+  u64 *d_rsamp_off = nullptr, *h_rsamp_off = nullptr;
+  u32 *d_rsamp_n = nullptr, *h_rsamp_n = nullptr;
+  mpsm_plan* rsub = nullptr;        // sorts the run-side samples (one run per job)
 };
 
 namespace {
@@ -244,6 +255,7 @@ u32 runs_for(const mpsm_plan* p, u64 nR) {
 Bufs bufs(const mpsm_plan* p) { return Bufs{p->xr, p->xs, p->y}; }
 
 bool split_learned(const mpsm_plan* p) { return p->opt.splitter_mode == MPSM_SPLIT_LEARNED; }
+bool runs_learned(const mpsm_plan* p) { return p->opt.run_buckets == MPSM_RUNS_LEARNED; }
 bool search_learned(const mpsm_plan* p) { return p->opt.search_mode == MPSM_SEARCH_LEARNED; }
 
 LearnCtx lctx(const mpsm_plan* p, bool models) {
@@ -255,6 +267,9 @@ LearnCtx lctx(const mpsm_plan* p, bool models) {
   c.seed = p->opt.seed;
   c.stat = p->d_lstat;
   c.interp = p->opt.search_mode == MPSM_SEARCH_INTERP;
+  c.rl = p->d_rl;
+  c.rcell = p->d_rcell;
+  c.rbnd = p->d_rbnd;
   return c;
 }
 
@@ -342,6 +357,45 @@ int alloc_learn(mpsm_plan* p) {
   if (rc) return rc;
   p->sub = sub;
   return MPSM_OK;
+}
+
+// learned run bucket function: tables, the run-side samples and the plan that sorts them
+int alloc_rlearn(mpsm_plan* p) {
+  if (p->d_rl) return MPSM_OK;
+  p->rsamp_cap = p->max_nR / 64 + 1024ull * p->max_jobs + 16;
+  if (dalloc(&p->d_rl, p->max_jobs) || dalloc(&p->d_rcell, (u64)p->max_jobs * FINE_MAX) ||
+      dalloc(&p->d_rbnd, (u64)p->max_jobs * P_MAX) ||
+      dalloc(&p->d_rsamp, p->rsamp_cap) || dalloc(&p->d_rsamp_off, p->max_jobs) ||
+      halloc(&p->h_rsamp_off, p->max_jobs) || dalloc(&p->d_rsamp_n, p->max_jobs) || halloc(&p->h_rsamp_n, p->max_jobs))
+    return MPSM_ERR_OOM;
+  mpsm_options_t so;
+  mpsm_options_default(&so);
+  so.runs_r = 1;  // each job's sample is one run
+  mpsm_plan_t* rsub = nullptr;
+  const int rc = mpsm_plan_create(&rsub, p->rsamp_cap, 16, p->max_jobs, &so, p->st);
+  if (rc) return rc;
+  p->rsub = rsub;
+  return MPSM_OK;
+}
+
+// sample sizes and the sample sort's jobs of a call with learned run buckets
+int setup_rlearn(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
+  int rc = alloc_rlearn(p);
+  if (rc) return rc;
+  std::vector<Jobh> rj(njobs);
+  u64 so = 0;
+  for (u32 i = 0; i < njobs; ++i) {
+    const u32 m = rmi_sample_size(p->h_jobs[i].nR);
+    p->h_rsamp_off[i] = so;
+    p->h_rsamp_n[i] = m;
+    rj[i] = Jobh{p->d_rsamp + so, nullptr, m, 0};
+    so += m;
+  }
+  if (so > p->rsamp_cap) return MPSM_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(p->d_rsamp_off, p->h_rsamp_off, njobs * sizeof(u64), cudaMemcpyHostToDevice, p->st));
+  CK(cudaMemcpyAsync(p->d_rsamp_n, p->h_rsamp_n, njobs * sizeof(u32), cudaMemcpyHostToDevice, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  return setup_jobs(p->rsub, rj.data(), njobs);
 }
 
 // sample sizes, model tasks and the sample sort's jobs of a learned call
@@ -498,6 +552,10 @@ int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
   p->kt_n = 0;
   p->learn = split_learned(p) || search_learned(p);
   CK(cudaMemsetAsync(p->d_lstat, 0, 8 * sizeof(u64), p->st));
+  if (runs_learned(p)) {
+    const int rc = setup_rlearn(p, jobs, njobs);
+    if (rc) return rc;
+  }
   if (p->learn) return setup_learn(p, jobs, njobs);
   return MPSM_OK;
 }
@@ -505,10 +563,14 @@ int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
 // radix passes over the big-segment list until every segment is final
 // keep_const: constant-key children stay where they are (the fused join reads them
 // in place) and the buckets aim at the fused kernel's tile
-int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels, bool keep_const = false) {
+// learned_first: the first pass takes each job's learned run bucket function
+int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels, bool keep_const = false,
+               bool learned_first = false) {
   u32 cur = 0, src = first_src;
   u32 done = 0;
   for (u32 lvl = 0; lvl < MAX_LEVELS; ++lvl) {
+    const bool rl = learned_first && lvl == 0;
+    const u32 mode = rl ? (u32)MODE_RLEARN : (u32)MODE_RADIX;
     if (!p->graph_mode) {
       CK(cudaMemcpyAsync(&p->h_cnt[C_BIG0 + cur], &p->d_cnt[C_BIG0 + cur], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
       CK(cudaStreamSynchronize(p->st));
@@ -518,16 +580,16 @@ int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels, bool k
     CK(cudaMemsetAsync(&p->d_cnt[C_BIG0 + (cur ^ 1)], 0, sizeof(u32), p->st));
     u64* tot = p->d_tot + T_LEVEL;
     const u32 rb = p->opt.radix_bits ? p->opt.radix_bits : 11u;
-    LAUNCH(K_PLAN, launch_level_plan(p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->big_cap, p->d_ls, tot, MODE_RADIX, CH_RADIX, rb,
+    LAUNCH(K_PLAN, launch_level_plan(p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->big_cap, p->d_ls, tot, mode, CH_RADIX, rb,
                       p->d_jobs, p->hist_a_cap, p->bucket_cap, &p->d_cnt[C_ERR], p->st,
-                      keep_const ? FILL_FUSED : 0));
+                      keep_const ? FILL_FUSED : 0, p->d_rl));
     LAUNCH(K_INIT, launch_init_buckets(p->d_bmin, p->d_bmax, nullptr, tot, p->st, p->nsm));
-    LAUNCH(K_HIST_RADIX, launch_hist(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs, src,
+    LAUNCH(rl ? K_HIST_RLEARN : K_HIST_RADIX, launch_hist(mode, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs, src,
                 p->d_hist_a, p->d_bmin, p->d_bmax, nullptr, lctx(p, false), p->st, p->nsm));
     LAUNCH(K_SCAN_RADIX, launch_scan(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, p->d_hist_a, p->d_bmin, p->d_bmax,
                 nullptr, p->d_big[cur ^ 1], &p->d_cnt[C_BIG0 + (cur ^ 1)], p->big_cap, p->d_fin, &p->d_cnt[C_FIN],
                 p->fin_cap, dst, p->d_jobs, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm, keep_const));
-    LAUNCH(K_SCATTER_RADIX, launch_scatter(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs,
+    LAUNCH(rl ? K_SCATTER_RLEARN : K_SCATTER_RADIX, launch_scatter(mode, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs,
                    src, dst, p->d_hist_a, nullptr, &p->d_cnt[C_ERR], lctx(p, false), p->st, p->nsm, lvl == 0));
     CK(cudaGetLastError());
     src = dst;
@@ -561,8 +623,21 @@ int final_sort(mpsm_plan* p, u32 dst_where) {
 int phase_runs(mpsm_plan* p) {
   record(p, EV_START);
   CK(cudaMemsetAsync(&p->d_cnt[C_ERR], 0, sizeof(u32), p->st));
+  const bool rl = runs_learned(p) && p->rsub;
+  if (rl) {
+    // the learned run bucket function: a run-side sample, sorted by the sub-plan, cut
+    // into quantiles
+    LAUNCH(K_SAMPLE_R, launch_sample_r(p->d_jobs, p->njobs, p->d_rsamp_off, p->d_rsamp_n, p->d_rsamp, p->st, p->nsm));
+    p->rsub->graph_mode = p->graph_mode;
+    p->rsub->opt.flags = p->opt.flags & MPSM_FLAG_KERNEL_TIMING;
+    const int src = phase_runs(p->rsub);
+    p->launches += p->rsub->launches;
+    if (src) return src;
+    LAUNCH(K_RLEARN_TAB, launch_rlearn_tables(p->d_jobs, p->njobs, p->rsub->xr, p->d_rsamp_off, p->d_rsamp_n, p->d_rl,
+                                              p->d_rcell, p->d_rbnd, p->st));
+  }
   LAUNCH(K_SAMPLE, launch_sample_bounds(p->d_big[0], &p->d_cnt[C_BIG0], p->h_cnt[C_BIG0] ? p->big_cap : 0, bufs(p), p->d_jobs, p->st));
-  int rc = run_levels(p, W_RIN, W_XR, &p->levels_r);
+  int rc = run_levels(p, W_RIN, W_XR, &p->levels_r, false, rl);
   if (rc) return rc;
   rc = final_sort(p, W_XR);
   if (rc) return rc;
@@ -603,11 +678,16 @@ int phase_learn(mpsm_plan* p) {
   LAUNCH(K_RMI_DATA, launch_rmi_setup(p->d_models, p->d_tasks, nm, p->d_jobs, true, p->st));
   LAUNCH(K_RMI_DATA, launch_fit_data(p->d_models, p->d_tasks, nm, p->d_jobs, p->d_runs, p->xr,
                                      p->sub ? p->sub->xr : nullptr, p->d_fitk, p->d_fity, p->st, p->nsm));
-  LAUNCH(K_RMI_DATA, launch_train_data(p->d_models, nm, p->d_fitk, p->d_fity, p->d_tx, p->d_ty, p->st));
-  const u32 steps = p->opt.learn_steps ? p->opt.learn_steps : RMI_STEPS;
-  if (int rc = train_models(p, nm, steps, RMI_LR, nullptr)) return rc;
-  LAUNCH(K_RMI_TAB, launch_rmi_tabulate(p->d_models, nm, p->st));
-  LAUNCH(K_RMI_LEAF, launch_leaf_fit(p->d_models, nm, p->d_leafacc, p->d_fitk, p->d_fity, p->st, p->nsm));
+  // The learned splitters take the sorted sample's quantiles (k_learn_bounds) and its
+  // cell table, not the network's predictions; only the learned search predicts with the
+  // trained models, so only it trains them.
+  if (search_learned(p)) {
+    LAUNCH(K_RMI_DATA, launch_train_data(p->d_models, nm, p->d_fitk, p->d_fity, p->d_tx, p->d_ty, p->st));
+    const u32 steps = p->opt.learn_steps ? p->opt.learn_steps : RMI_STEPS;
+    if (int rc = train_models(p, nm, steps, RMI_LR, nullptr)) return rc;
+    LAUNCH(K_RMI_TAB, launch_rmi_tabulate(p->d_models, nm, p->st));
+    LAUNCH(K_RMI_LEAF, launch_leaf_fit(p->d_models, nm, p->d_leafacc, p->d_fitk, p->d_fity, p->st, p->nsm));
+  }
   CK(cudaGetLastError());
   record(p, EV_LEARN);
   return MPSM_OK;
@@ -752,10 +832,13 @@ int phase_search(mpsm_plan* p) {
 int read_err(mpsm_plan* p) {
   CK(cudaMemcpyAsync(&p->h_cnt[C_ERR], &p->d_cnt[C_ERR], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
   const bool sub = p->learn && split_learned(p) && p->sub;
+  const bool rsub = runs_learned(p) && p->rsub;
   if (sub)
     CK(cudaMemcpyAsync(&p->sub->h_cnt[C_ERR], &p->sub->d_cnt[C_ERR], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
+  if (rsub)
+    CK(cudaMemcpyAsync(&p->rsub->h_cnt[C_ERR], &p->rsub->d_cnt[C_ERR], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
   CK(cudaStreamSynchronize(p->st));
-  p->device_errors = p->h_cnt[C_ERR] | (sub ? p->sub->h_cnt[C_ERR] : 0u);
+  p->device_errors = p->h_cnt[C_ERR] | (sub ? p->sub->h_cnt[C_ERR] : 0u) | (rsub ? p->rsub->h_cnt[C_ERR] : 0u);
   return p->device_errors ? MPSM_ERR_DEVICE : MPSM_OK;
 }
 
@@ -872,6 +955,15 @@ MPSM_API void mpsm_plan_destroy(mpsm_plan_t* p) {
   dfree(p->d_bnd);
   dfree(p->d_brank);
   if (p->sub) mpsm_plan_destroy(p->sub);
+  dfree(p->d_rl);
+  dfree(p->d_rcell);
+  dfree(p->d_rbnd);
+  dfree(p->d_rsamp);
+  dfree(p->d_rsamp_off);
+  hfree(p->h_rsamp_off);
+  dfree(p->d_rsamp_n);
+  hfree(p->h_rsamp_n);
+  if (p->rsub) mpsm_plan_destroy(p->rsub);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
@@ -900,9 +992,10 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   mpsm_options_t o;
   if (opt) {
     o = *opt;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
       if (o.reserved[i]) return MPSM_ERR_INVALID_ARG;
     if (o.partition_side > MPSM_PART_SMALLER) return MPSM_ERR_INVALID_ARG;
+    if (o.run_buckets > MPSM_RUNS_LEARNED) return MPSM_ERR_INVALID_ARG;
   } else {
     mpsm_options_default(&o);
   }
@@ -995,6 +1088,7 @@ MPSM_API int mpsm_plan_create(mpsm_plan_t** out, uint64_t max_nR, uint64_t max_n
   TRY(dalloc(&p->d_lstat, 8));
   TRY(dalloc(&p->d_fence, max_nR / 64 + 2));
   if (o.splitter_mode == MPSM_SPLIT_LEARNED || o.search_mode == MPSM_SEARCH_LEARNED) TRY(alloc_learn(p));
+  if (o.run_buckets == MPSM_RUNS_LEARNED) TRY(alloc_rlearn(p));
   {
     const u32 fl = o.flags;
     p->opt.flags = 0;
@@ -1382,6 +1476,10 @@ MPSM_API int mpsm_plan_set_flags(mpsm_plan_t* p, uint32_t flags) {
     const int rc = mpsm_plan_set_flags(p->sub, flags & MPSM_FLAG_KERNEL_TIMING);
     if (rc) return rc;
   }
+  if (p->rsub) {
+    const int rc = mpsm_plan_set_flags(p->rsub, flags & MPSM_FLAG_KERNEL_TIMING);
+    if (rc) return rc;
+  }
   return MPSM_OK;
 }
 
@@ -1403,6 +1501,7 @@ MPSM_API int mpsm_plan_kernel_times(mpsm_plan_t* p, mpsm_kernel_time_t* out, uin
   };
   add(p);
   if (p->learn && split_learned(p) && p->sub && p->sub->kt_ev) add(p->sub);  // the sample sort
+  if (runs_learned(p) && p->rsub && p->rsub->kt_ev) add(p->rsub);              // the run-side sample sort
   u32 k = 0;
   for (u32 id = 0; id < K_NUM; ++id) {
     if (!cnt[id]) continue;

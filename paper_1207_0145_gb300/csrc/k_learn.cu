@@ -617,6 +617,61 @@ __global__ void k_sample_s(const Job* jobs, const u64* samp_off, const u32* samp
   }
 }
 
+// Evenly spaced rows of each job's run-side input R, gathered for the sample sort
+// that the learned run bucket function is cut from (payload 0).
+__global__ void k_sample_r(const Job* jobs, const u64* samp_off, const u32* samp_n, Tuple* samp) {
+  const Job& J = jobs[blockIdx.y];
+  const u64 m = samp_n[blockIdx.y];
+  Tuple* out = samp + samp_off[blockIdx.y];
+  for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (u64)gridDim.x * blockDim.x) {
+    const u64 row = ((2 * t + 1) * J.nR) / (2 * m);
+    Tuple v;
+    v.key = J.R[row].key;
+    v.pay = 0;
+    out[t] = v;
+  }
+}
+
+// One block per job: the learned run bucket function (RunLearn) from the job's sorted
+// sample of m run-side keys (sorted[samp_off[j] ...]).  F buckets aim at N_LEAF tuples of
+// one run each (the runs of a job have equal lengths), at most P_MAX and at most one per 8
+// sample keys; boundary q is the sample key of rank (q + 1) m / F, and the cell table
+// marks where boundaries fall, as for the learned partitions (k_learn_cells).
+__global__ void k_rlearn_tables(const Job* jobs, const Tuple* sorted, const u64* samp_off, const u32* samp_n,
+                                RunLearn* rl, u32* rcell, u64* rbnd) {
+  const u32 j = blockIdx.x;
+  const Job& J = jobs[j];
+  const u64 m = samp_n[j];
+  const Tuple* sk = sorted + samp_off[j];
+  const u64 run_len = J.runs ? (J.nR + J.runs - 1) / J.runs : 0;
+  u64 F = (run_len + N_LEAF - 1) / N_LEAF;
+  F = F > P_MAX ? P_MAX : F;
+  F = F > m / 8 ? m / 8 : F;
+  F = F < 1 ? 1 : F;
+  const u32 nb = (u32)F - 1u;
+  u64* b = rbnd + (u64)j * P_MAX;
+  for (u32 q = threadIdx.x; q < nb; q += blockDim.x) b[q] = sk[((u64)(q + 1) * m) / F].key;
+  const u64 lo = m ? sk[0].key : 0ull, hi = m ? sk[m - 1].key : 0ull;
+  const u32 bits = bitlen64(hi - lo);
+  const u32 shift = bits > 12u ? bits - 12u : 0u;  // at most 4096 = FINE_MAX cells
+  const u32 ncell = (u32)((hi - lo) >> shift) + 1u;
+  if (threadIdx.x == 0) rl[j] = RunLearn{lo, shift, ncell, (u32)F, (u32)m};
+  __syncthreads();  // the boundaries, before the cells search them
+  auto at = [&](u64 i) { return b[i]; };
+  const u64 w = (1ull << shift) - 1ull;
+  for (u32 f = threadIdx.x; f < ncell; f += blockDim.x) {
+    const u64 clo = lo + ((u64)f << shift);
+    const u64 chi = (hi - clo < w) ? hi : clo + w;
+    // the last cell also takes every key above hi, the first every key below lo: no
+    // boundary lies there, so the entries below still give their buckets
+    const u64 top = f + 1u == ncell ? ~0ull : chi;
+    const u32 plo = (u32)lower_bound_at(at, nb, clo);                                 // #bnd < clo
+    const u32 phi = top == ~0ull ? nb : (u32)lower_bound_at(at, nb, top + 1ull);      // #bnd <= top
+    const u32 hot = (plo < phi && b[plo] == b[phi - 1]) ? LCELL_HOT : 0u;
+    rcell[(u64)j * FINE_MAX + f] = plo == phi ? plo : (plo | (phi << 16) | LCELL_SPLIT | hot);
+  }
+}
+
 __global__ void k_rmi_predict(const RmiModel* M, const u64* keys, u64 n, float* yhat, u32* leaf) {
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
     const u64 k = keys[i];
@@ -630,6 +685,16 @@ __global__ void k_rmi_predict(const RmiModel* M, const u64* keys, u64 n, float* 
 void launch_sample_s(const Job* jobs, u32 njobs, const u64* samp_off, const u32* samp_n, Tuple* samp,
                      cudaStream_t st, int nsm) {
   k_sample_s<<<dim3(nsm, njobs), 256, 0, st>>>(jobs, samp_off, samp_n, samp);
+}
+
+void launch_sample_r(const Job* jobs, u32 njobs, const u64* samp_off, const u32* samp_n, Tuple* samp,
+                     cudaStream_t st, int nsm) {
+  k_sample_r<<<dim3(nsm, njobs), 256, 0, st>>>(jobs, samp_off, samp_n, samp);
+}
+
+void launch_rlearn_tables(const Job* jobs, u32 njobs, const Tuple* sorted, const u64* samp_off, const u32* samp_n,
+                          RunLearn* rl, u32* rcell, u64* rbnd, cudaStream_t st) {
+  k_rlearn_tables<<<njobs, 1024, 0, st>>>(jobs, sorted, samp_off, samp_n, rl, rcell, rbnd);
 }
 
 void launch_learn_cells(const Job* jobs, u32 njobs, const u64* bnd, u32* cell, cudaStream_t st) {

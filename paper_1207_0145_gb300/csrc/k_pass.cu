@@ -142,7 +142,8 @@ __global__ void k_sample_bounds(Seg* segs, const u32* nseg_ptr, Bufs bufs, const
 // ---------------------------------------------------------------- level plan
 __global__ void __launch_bounds__(1024) k_level_plan(const Seg* segs, u32* nseg_ptr, u32 seg_cap, LSeg* ls,
                                                      u64* totals, u32 mode, u64 chunk, u32 radix_bits, u64 fill,
-                                                     const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err) {
+                                                     const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err,
+                                                     const RunLearn* rl) {
   __shared__ u64 s_warp[33];
   __shared__ u64 carry[3];
   u32 n = *nseg_ptr;
@@ -194,6 +195,12 @@ __global__ void __launch_bounds__(1024) k_level_plan(const Seg* segs, u32* nseg_
           F = (u32)range + 1u;
         }
         lo = s.kmin;
+      } else if (mode == MODE_RLEARN) {
+        // the job's learned bucket function: lo and shift give the cell of a key
+        const RunLearn& RL = rl[s.job];
+        lo = RL.lo;
+        shift = RL.shift;
+        F = RL.F;
       } else {
         const Job& J = jobs[s.job];
         lo = J.kmin;
@@ -296,6 +303,7 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
     const u64 row0 = S.off - jobs[S.job].s_base;  // MODE_LEARN: row of the tuple in the job's S
     u32 probes = 0, keys = 0;
     u32 fit_n = 0;
+    RunLearn RL{};
     // learned partitions of a dense job (at most 64 key values per S tuple) take their
     // boundaries as bounds: only the counts are needed here.  Likewise the interior fine
     // buckets of a dense job: a partition's bounds then come from its buckets' key ranges,
@@ -311,6 +319,12 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
         srank[2 * q + 1] = lc.brank[(u64)S.job * 2 * P_MAX + 2 * q + 1];
       }
       fit_n = lc.models[2 * S.job].fit_n;
+      __syncthreads();
+    }
+    if (MODE == MODE_RLEARN) {
+      RL = lc.rl[S.job];
+      for (u32 f = threadIdx.x; f < RL.ncell; f += NT_PASS) scell[f] = lc.rcell[(u64)S.job * FINE_MAX + f];
+      for (u32 q = threadIdx.x; q + 1u < F; q += NT_PASS) sbnd[q] = lc.rbnd[(u64)S.job * P_MAX + q];
       __syncthreads();
     }
     for (u64 t0 = a + threadIdx.x; t0 < e; t0 += NT_PASS * 4) {
@@ -333,6 +347,9 @@ __global__ void __launch_bounds__(NT_PASS) k_hist(const Seg* segs, const u32* ns
           b = learned_cell_part(scell[(k[i] - kmin) >> L.shift], sbnd, srank, F, fit_n, k[i], row0 + t, lc.seed,
                                 probes);
           ++keys;
+        } else if (MODE == MODE_RLEARN) {
+          b = run_learn_bucket(scell[run_learn_cell(RL, k[i])], sbnd, k[i]);
+          b = b < F ? b : F - 1u;
         } else {
           if (k[i] < kmin || k[i] > kmax) continue;
           b = (u32)((k[i] - kmin) >> L.shift);
@@ -599,6 +616,12 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
       }
       fit_n = lc.models[2 * S.job].fit_n;
     }
+    RunLearn RL{};
+    if (MODE == MODE_RLEARN) {  // the job's learned run bucket function (k_hist reads the same tables)
+      RL = lc.rl[S.job];
+      for (u32 f = tid; f < RL.ncell; f += NT_SC) spl32[f] = lc.rcell[(u64)S.job * FINE_MAX + f];
+      for (u32 q = tid; q + 1u < F; q += NT_SC) sbnd[q] = lc.rbnd[(u64)S.job * P_MAX + q];
+    }
     const u64 row0 = S.off - jobs[S.job].s_base;  // MODE_LEARN: row of the segment's first tuple in the job's S
     u32 probes = 0;
     const u64 a = ci * chunk;
@@ -652,6 +675,9 @@ __global__ void __launch_bounds__(NT_SC, SC_MINB) k_scatter(const Seg* segs, con
             e = spl32[(key - kmin) >> L.shift];
           }
           b = learned_cell_part(e, sbnd, srank, F, fit_n, key, row0 + t0 + x, lc.seed, probes);
+        } else if (MODE == MODE_RLEARN) {
+          b = run_learn_bucket(spl32[run_learn_cell(RL, key)], sbnd, key);
+          b = b < F ? b : F - 1u;
         } else {
           if (key < kmin || key > kmax) continue;
           b = spl[(key - kmin) >> L.shift];
@@ -1497,6 +1523,8 @@ void init_attrs_pass() {
   set_smem(k_hist<MODE_RADIX, F_MAX>, F_MAX * 20);
   set_smem(k_hist<MODE_FINE, FINE_MAX>, FINE_MAX * 20);
   set_smem(k_hist<MODE_LEARN, F_MAX>, SMEM_HIST_LEARN);
+  set_smem(k_hist<MODE_RLEARN, F_MAX>, SMEM_HIST_LEARN);
+  set_smem(k_scatter<MODE_RLEARN, LN_TILE, LN_NT, 1, 2>, smem_scatter(LN_TILE, 2, true));
   set_smem(k_scan<MODE_LEARN>, SMEM_SCAN);
   set_smem(k_scatter<MODE_LEARN, LN_TILE, LN_NT, 1, 2>, smem_scatter(LN_TILE, 2, true));
   set_smem(k_scatter<MODE_LEARN, RX_TILE, RX_NT, RX_MINB, RX_STAGES, LN_SMALL>,
@@ -1523,9 +1551,9 @@ void launch_sample_bounds(Seg* segs, const u32* nseg, u32 max_segs, Bufs bufs, c
 
 void launch_level_plan(const Seg* segs, u32* nseg, u32 seg_cap, LSeg* ls, u64* totals, u32 mode, u64 chunk,
                        u32 radix_bits, const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err, cudaStream_t st,
-                       u64 fill) {
+                       u64 fill, const RunLearn* rl) {
   k_level_plan<<<1, 1024, 0, st>>>(segs, nseg, seg_cap, ls, totals, mode, chunk, radix_bits, fill, jobs, hist_cap,
-                                   bucket_cap, err);
+                                   bucket_cap, err, rl);
 }
 
 void launch_init_buckets(u64* bmin, u64* bmax, u64* btot, const u64* totals, cudaStream_t st, int nsm) {
@@ -1539,6 +1567,9 @@ void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, con
     const size_t sm = F_MAX * 20;
     k_hist<MODE_RADIX, F_MAX><<<nsm * 2, NT_PASS, sm, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs, src_where,
                                                              hist, bmin, bmax, btot, lc);
+  } else if (mode == MODE_RLEARN) {
+    k_hist<MODE_RLEARN, F_MAX><<<nsm * 2, NT_PASS, SMEM_HIST_LEARN, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
+                                                                        src_where, hist, bmin, bmax, btot, lc);
   } else if (mode == MODE_LEARN) {
     k_hist<MODE_LEARN, F_MAX><<<nsm * 2, NT_PASS, SMEM_HIST_LEARN, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
                                                                        src_where, hist, bmin, bmax, btot, lc);
@@ -1583,6 +1614,9 @@ void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, 
             segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   } else if (mode == MODE_LEARN) {
     k_scatter<MODE_LEARN, LN_TILE, LN_NT, 1, 2><<<nsm, LN_NT, smem_scatter(LN_TILE, 2, true), st>>>(
+        segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
+  } else if (mode == MODE_RLEARN) {  // the learned run bucket tables take the learned pass's layout
+    k_scatter<MODE_RLEARN, LN_TILE, LN_NT, 1, 2><<<nsm, LN_NT, smem_scatter(LN_TILE, 2, true), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
   } else if (big_tiles) {
     k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB, RX_STAGES><<<nsm * RX_MINB, RX_NT, smem_scatter(RX_TILE, RX_STAGES), st>>>(

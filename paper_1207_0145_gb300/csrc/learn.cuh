@@ -3,9 +3,11 @@
 //
 // The model predicts the CDF value y in [0, 1] of a key.  It plays the role of
 // the paper's equi-height CDF of the runs (Sec. 4.1-4.2, Fig. 8): y times a
-// run's length predicts where the key's merge starts in that run (Sec. 3.2.2),
-// and y times P predicts the key's partition (Sec. 4.3).  Every prediction is
-// followed by an exact search, so the model changes speed, never results.
+// run's length predicts where the key's merge starts in that run (Sec. 3.2.2).
+// Every prediction is followed by an exact search, so the model changes speed,
+// never results.  The learned partitions (Sec. 4.3) and the learned run buckets
+// take the sorted sample's own quantiles -- its empirical CDF -- tabulated per
+// key cell, below.
 //
 //   stage 1 (root):  x = (key - kmin) / (kmax - kmin)
 //                    h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), yhat = W3 . h2 + b3
@@ -151,26 +153,18 @@ __device__ __forceinline__ u32 learned_part_from(const u64* bnd, const u32* rank
   return q > ub ? ub : q;
 }
 
-// The same with the model's prediction floor(P * yhat) as the starting guess, or
-// `hint` (< P) when the caller knows a closer one.
-__device__ __forceinline__ u32 learned_part(const RmiModel* M, const u64* bnd, const u32* rank, u32 P, u64 key,
-                                             u64 row, u64 seed, u32& probes, u32 hint = 0xFFFFFFFFu) {
-  const u32 g = hint != 0xFFFFFFFFu ? hint : (u32)(rmi_predict(M, key) * (float)P);
-  return learned_part_from<true>(bnd, rank, P, M->fit_n, key, row, seed, probes, g);
-}
-
 // Fine-cell table of the learned partitions (one u32 per fine bucket of the job):
 // the partition of every key in the cell, or -- with LCELL_SPLIT set -- the
 // partitions plo (bits 0-13) to phi (bits 16-29) that the cell reaches when
 // boundaries fall inside it.  LCELL_HOT marks a cell whose boundaries all equal one
 // key (a hot key cut across partitions plo..phi): a key below it lies in plo, one
-// above it in phi, and the key itself takes the hash-drawn share of learned_part,
+// above it in phi, and the key itself takes the hash-drawn share of learned_part_from,
 // with no search.
 constexpr u32 LCELL_SPLIT = 0x80000000u;
 constexpr u32 LCELL_HOT = 0x40000000u;
 
 // The learned partition of `key` from its fine cell's entry e (the same result as
-// learned_part; bnd and rank in shared memory).
+// learned_part_from; bnd and rank in shared memory).
 __device__ __forceinline__ u32 learned_cell_part(u32 e, const u64* bnd, const u32* rank, u32 P, u32 m, u64 key,
                                                  u64 row, u64 seed, u32& probes) {
   if (!(e & LCELL_SPLIT)) return e;
@@ -187,6 +181,46 @@ __device__ __forceinline__ u32 learned_cell_part(u32 e, const u64* bnd, const u3
   return q > phi ? phi : q;
 }
 
+// The bucket function of a learned first sort pass over a job's runs: F buckets cut
+// at F - 1 quantiles of a sorted, evenly spaced sample of m run-side keys, found
+// through a table of ncell equal cells over the sample's key range: cell =
+// min((key - lo) >> shift, ncell - 1), a key below lo taking cell 0.  bucket(key) =
+// #(boundaries < key): bucket b holds the keys in (boundary b - 1, boundary b], so a
+// key equal to several boundaries goes whole to the first bucket it bounds (a constant
+// child when it is frequent, which the sort leaves in place).
+struct RunLearn {
+  u64 lo;
+  u32 shift, ncell;
+  u32 F, m;
+};
+
+// the cell of `key` in a learned run bucket function's table
+__device__ __forceinline__ u32 run_learn_cell(const RunLearn& RL, u64 key) {
+  const u64 c = (key > RL.lo ? key - RL.lo : 0ull) >> RL.shift;
+  return c < (u64)RL.ncell ? (u32)c : RL.ncell - 1u;
+}
+
+// #(boundaries < key) from the key's cell entry e (the cell table's encoding, LCELL_*):
+// the cell's partition when no boundary falls in it, else a bisection over the
+// boundaries plo..phi - 1 that do (bnd in shared memory)
+__device__ __forceinline__ u32 run_learn_bucket(u32 e, const u64* bnd, u64 key) {
+  if (!(e & LCELL_SPLIT)) return e;
+  u32 pos = e & 0x3FFFu;
+  const u32 phi = (e >> 16) & 0x3FFFu;
+  if (e & LCELL_HOT) return key <= bnd[pos] ? pos : phi;  // every boundary here is one key
+  u32 len = phi - pos;
+  while (len > 0) {
+    const u32 h = len >> 1;
+    if (bnd[pos + h] < key) {
+      pos += h + 1;
+      len -= h + 1;
+    } else {
+      len = h;
+    }
+  }
+  return pos;
+}
+
 struct LearnCtx {
   const RmiModel* models;   // 2 per job: [2 j] = S-side model, [2 j + 1] = R-side model
   const u64* bnd;           // per job P_MAX learned partition boundaries
@@ -196,6 +230,9 @@ struct LearnCtx {
   u64* stat;                // [0] partition probes, [1] keys partitioned, [2] search probes,
                             // [3] searches, [4] sum of |prediction - exact| start positions
   u32 interp;               // without models: merge starts by interpolation search, not binary
+  const RunLearn* rl;       // per job: the learned run bucket function (MODE_RLEARN) ...
+  const u32* rcell;         // ... its cell table (FINE_MAX per job)
+  const u64* rbnd;          // ... and boundaries (P_MAX per job)
 };
 
 }  // namespace mpsm

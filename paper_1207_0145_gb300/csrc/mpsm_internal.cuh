@@ -46,7 +46,9 @@ constexpr u32 SEG_EXACT = 8u;     // every key of the segment lies in [kmin, kma
                                   // key range of the bucket that made it)
 
 // bucket functions of a partitioning pass
-enum PassMode : u32 { MODE_RADIX = 0, MODE_FINE = 1, MODE_SPLIT = 2, MODE_LEARN = 3 };
+// MODE_RLEARN: a sort pass over the runs whose bucket function is the run side's
+// sample quantiles (RunLearn in learn.cuh) instead of equal-width key ranges
+enum PassMode : u32 { MODE_RADIX = 0, MODE_FINE = 1, MODE_SPLIT = 2, MODE_LEARN = 3, MODE_RLEARN = 4 };
 
 // device-side error flags (bit set)
 enum DevErr : u32 {

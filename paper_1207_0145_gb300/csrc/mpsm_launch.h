@@ -18,7 +18,8 @@ void init_attrs_learn();
 void launch_sample_bounds(Seg* segs, const u32* nseg, u32 max_segs, Bufs bufs, const Job* jobs, cudaStream_t st);
 void launch_level_plan(const Seg* segs, u32* nseg, u32 seg_cap, LSeg* ls, u64* totals, u32 mode, u64 chunk,
                        u32 radix_bits, const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err, cudaStream_t st,
-                       u64 fill = 0);  // MODE_RADIX: target tuples per bucket, 0 = power-of-two buckets
+                       u64 fill = 0,   // MODE_RADIX: target tuples per bucket, 0 = power-of-two buckets
+                       const RunLearn* rl = nullptr);  // MODE_RLEARN: the jobs' learned run bucket functions
 void launch_init_buckets(u64* bmin, u64* bmax, u64* btot, const u64* totals, cudaStream_t st, int nsm);
 void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                  Bufs bufs, const Job* jobs, u32 src_where, u32* hist, u64* bmin, u64* bmax, u64* btot,
@@ -102,6 +103,11 @@ void launch_learn_bounds(Job* jobs, u32 njobs, const RmiModel* models, const u64
 void launch_sample_s(const Job* jobs, u32 njobs, const u64* samp_off, const u32* samp_n, Tuple* samp,
                      cudaStream_t st, int nsm);
 void launch_learn_cells(const Job* jobs, u32 njobs, const u64* bnd, u32* cell, cudaStream_t st);
+// the learned run bucket function: run-side sample, then its tables from the sorted sample
+void launch_sample_r(const Job* jobs, u32 njobs, const u64* samp_off, const u32* samp_n, Tuple* samp,
+                     cudaStream_t st, int nsm);
+void launch_rlearn_tables(const Job* jobs, u32 njobs, const Tuple* sorted, const u64* samp_off, const u32* samp_n,
+                          RunLearn* rl, u32* rcell, u64* rbnd, cudaStream_t st);
 void launch_rmi_predict(const RmiModel* M, const u64* keys, u64 n, float* yhat, u32* leaf, cudaStream_t st, int nsm);
 
 enum JoinMode : u32 { JOIN_AGG = 0, JOIN_COUNT = 1, JOIN_WRITE = 2 };

@@ -22,6 +22,7 @@ DEVERR_HIST_OVERFLOW, DEVERR_LEARN, DEVERR_BOUNDS = 16, 32, 64
 SPLIT_HIST, SPLIT_LEARNED, SPLIT_EQUI_HEIGHT = 0, 1, 2
 SEARCH_BINARY, SEARCH_LEARNED, SEARCH_INTERP = 0, 1, 2
 PART_S, PART_R, PART_SMALLER = 0, 1, 2
+RUNS_RADIX, RUNS_LEARNED = 0, 1
 FLAG_TIMING = 1
 FLAG_KERNEL_TIMING = 2
 FLAG_UNFUSED = 4
@@ -37,7 +38,7 @@ class Options(ctypes.Structure):
     _fields_ = [("runs_r", _u32), ("partitions_s", _u32), ("fine_bits", _u32), ("radix_bits", _u32),
                 ("join_tile", _u32), ("splitter_mode", _i32), ("search_mode", _i32), ("flags", _u32),
                 ("seed", _u64), ("learn_steps", _u32), ("run_len", _u32), ("partition_side", _u32),
-                ("reserved", _u32 * 3)]
+                ("run_buckets", _u32), ("reserved", _u32 * 2)]
 
 
 class Tuning(ctypes.Structure):
@@ -159,7 +160,7 @@ def _tuples(t) -> Tuple[int, int]:
 
 def make_options(runs_r=0, partitions_s=0, fine_bits=0, radix_bits=0, join_tile=0, splitter_mode=SPLIT_HIST,
                  search_mode=SEARCH_BINARY, timing=False, kernel_timing=False, flags=0,
-                 seed=20120145, learn_steps=0, run_len=0, partition_side=0) -> Options:
+                 seed=20120145, learn_steps=0, run_len=0, partition_side=0, run_buckets=0) -> Options:
     o = Options()
     lib().mpsm_options_default(ctypes.byref(o))
     o.runs_r, o.partitions_s, o.fine_bits, o.radix_bits, o.join_tile = runs_r, partitions_s, fine_bits, radix_bits, join_tile
@@ -169,6 +170,7 @@ def make_options(runs_r=0, partitions_s=0, fine_bits=0, radix_bits=0, join_tile=
     o.learn_steps = learn_steps
     o.run_len = run_len
     o.partition_side = partition_side
+    o.run_buckets = run_buckets
     return o
 
 

@@ -54,7 +54,8 @@ int main(void) {
   printf("mpsm_job_t %zu\n", sizeof(mpsm_job_t));
   printf("mpsm_pairs_t %zu\n", sizeof(mpsm_pairs_t));
   F(mpsm_options_t, seed); F(mpsm_options_t, flags); F(mpsm_options_t, learn_steps);
-  F(mpsm_options_t, run_len); F(mpsm_options_t, partition_side); F(mpsm_options_t, reserved);
+  F(mpsm_options_t, run_len); F(mpsm_options_t, partition_side); F(mpsm_options_t, run_buckets);
+  F(mpsm_options_t, reserved);
   printf("mpsm_rmi_info_t %zu\n", sizeof(mpsm_rmi_info_t));
   F(mpsm_stats_t, loss_s0); F(mpsm_stats_t, part_probes); F(mpsm_stats_t, search_err);
   F(mpsm_stats_t, s_kept); F(mpsm_stats_t, imbalance); F(mpsm_stats_t, tiles); F(mpsm_stats_t, segments_s);
