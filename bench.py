@@ -613,6 +613,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         plan.join_host(Rh, Sh)
         torch.cuda.synchronize()
+        h2d_before = measure_h2d(Sh, dev, stream)
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -627,12 +628,13 @@ def run_ours(args):
         h2d = measure_h2d(Sh, dev, stream)
         e2e = {"value": evalue, "unit": UNIT, "h2d_bytes_per_step": units * 16,
                "d2h_bytes_per_step": 16, "ms_per_step": ems,
-               "h2d_gbs_measured": round(h2d, 1),
+               "h2d_gbs_measured": round(h2d, 1), "h2d_gbs_before": round(h2d_before, 1),
                "copy_bound_ms": round(units * 16 / (h2d * 1e9) * 1e3, 2),
                "over_copy_bound": round(ems / (units * 16 / (h2d * 1e9) * 1e3), 3),
                "host_numa_pinned": host_numa_of(Sh.data_ptr()), "gpu_host_numa": gpu_host_numa(local),
                "what": "mpsm_join_host: R and S copied from pinned host memory every step, then joined; "
-                       "copy_bound_ms = the step's input bytes at the measured host-to-device rate"}
+                       "copy_bound_ms = the step's input bytes at the host-to-device rate measured right after the "
+                       "timed steps (h2d_gbs_before: the same copy right before them)"}
         del Rh, Sh
 
     balance = partition_balance(plan, st) if args.splitter != "learned" else None
