@@ -659,10 +659,11 @@ def run_ours(args):
         arms = {
             "zipf": arm_modes("zipf0.9-200M-800M", [("hist", {"splitter_mode": 0}), ("learned", {"splitter_mode": 1})],
                               args.seed, dev, local),
-            # learned: the runs' first sort pass cut at the run side's sample quantiles; the
-            # learned merge-start search alone is timed too
+            # learned: the runs' first sort pass and the partitions cut at the sample quantiles of
+            # each side; the learned merge-start search alone is timed too
             "sparse": arm_modes("sparse-1600M-1600M", [("binary", {"search_mode": 0}),
-                                                       ("learned", {"search_mode": 0, "run_buckets": 1}),
+                                                       ("learned", {"search_mode": 0, "run_buckets": 1,
+                                                                    "splitter_mode": 1}),
                                                        ("learned_search", {"search_mode": 1})],
                                 args.seed, dev, local),
         }

@@ -132,44 +132,58 @@ __device__ __forceinline__ u64 mix64(u64 z) {
 // sample's CDF, [rank_lt, rank_le) / m, is cut across the partitions it spans, and
 // each tuple takes the partition of a point drawn from that share by a hash of its
 // row -- a hot key fills its partitions to the mean instead of making one huge.
-// The exact search starts at the guess g.  bnd and rank may live in shared memory
-// (GLOBAL false) or in global memory (read through the read-only cache).
-template <bool GLOBAL>
-__device__ __forceinline__ u32 learned_part_from(const u64* bnd, const u32* rank, u32 P, u32 m, u64 key, u64 row,
-                                                 u64 seed, u32& probes, u32 g) {
-  const u32 nb = P - 1u;
-  if (nb == 0) return 0u;
-  if (g > nb) g = nb;
-  auto at = [&](u64 i) { return GLOBAL ? __ldg(&bnd[i]) : bnd[i]; };
-  auto rk = [&](u32 i) { return GLOBAL ? __ldg(&rank[i]) : rank[i]; };
-  const u32 lb = (u32)gallop_from(at, nb, g, key, probes);
-  if (lb >= nb || at(lb) != key) return lb;
-  const u32 ub = key == ~0ull ? nb : (u32)gallop_from(at, nb, lb, key + 1ull, probes);  // #(bnd <= key)
-  const float lo = (float)rk(2 * lb), hi = (float)rk(2 * lb + 1);
-  const float u = (float)(mix64(row ^ seed) >> 40) * (1.0f / 16777216.0f);  // [0, 1)
-  const float c = fmaf(u, hi - lo, lo) * ((float)P / (float)m);
-  u32 q = c > 0.0f ? (u32)c : 0u;
-  q = q < lb ? lb : q;
-  return q > ub ? ub : q;
-}
+// The function is computed from the key's fine cell (learned_cell_part).
 
 // Fine-cell table of the learned partitions (one u32 per fine bucket of the job):
 // the partition of every key in the cell, or -- with LCELL_SPLIT set -- the
 // partitions plo (bits 0-13) to phi (bits 16-29) that the cell reaches when
 // boundaries fall inside it.  LCELL_HOT marks a cell whose boundaries all equal one
 // key (a hot key cut across partitions plo..phi): a key below it lies in plo, one
-// above it in phi, and the key itself takes the hash-drawn share of learned_part_from,
-// with no search.
+// above it in phi, and the key itself takes its hash-drawn share, with no search.
 constexpr u32 LCELL_SPLIT = 0x80000000u;
 constexpr u32 LCELL_HOT = 0x40000000u;
 
-// The learned partition of `key` from its fine cell's entry e (the same result as
-// learned_part_from; bnd and rank in shared memory).
+// The learned partition of `key` (above) from its fine cell's entry e; bnd and rank
+// in shared memory.
 __device__ __forceinline__ u32 learned_cell_part(u32 e, const u64* bnd, const u32* rank, u32 P, u32 m, u64 key,
                                                  u64 row, u64 seed, u32& probes) {
   if (!(e & LCELL_SPLIT)) return e;
   const u32 plo = e & 0x3FFFu, phi = (e >> 16) & 0x3FFFu;
-  if (!(e & LCELL_HOT)) return learned_part_from<false>(bnd, rank, P, m, key, row, seed, probes, plo);
+  if (!(e & LCELL_HOT)) {
+    // the boundaries that cut the cell are bnd[plo, phi), every other one lies outside
+    // it: #(bnd < key) and, for a key equal to boundaries, #(bnd <= key) by bisection
+    // among them
+    u32 lb = plo, len = phi - plo;
+    while (len > 0) {
+      const u32 h = len >> 1;
+      ++probes;
+      if (bnd[lb + h] < key) {
+        lb += h + 1;
+        len -= h + 1;
+      } else {
+        len = h;
+      }
+    }
+    if (lb >= phi || bnd[lb] != key) return lb;
+    u32 ub = lb;
+    len = phi - lb;
+    while (len > 0) {
+      const u32 h = len >> 1;
+      ++probes;
+      if (bnd[ub + h] <= key) {
+        ub += h + 1;
+        len -= h + 1;
+      } else {
+        len = h;
+      }
+    }
+    const float lo = (float)rank[2 * lb], hi = (float)rank[2 * lb + 1];
+    const float u = (float)(mix64(row ^ seed) >> 40) * (1.0f / 16777216.0f);  // [0, 1)
+    const float c = fmaf(u, hi - lo, lo) * ((float)P / (float)m);
+    u32 q = c > 0.0f ? (u32)c : 0u;
+    q = q < lb ? lb : q;
+    return q > ub ? ub : q;
+  }
   ++probes;
   const u64 hot = bnd[plo];
   if (key != hot) return key < hot ? plo : phi;
