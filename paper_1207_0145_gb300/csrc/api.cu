@@ -563,14 +563,15 @@ int setup_jobs(mpsm_plan* p, const Jobh* jobs, u32 njobs) {
 // radix passes over the big-segment list until every segment is final
 // keep_const: constant-key children stay where they are (the fused join reads them
 // in place) and the buckets aim at the fused kernel's tile
-// learned_first: the first pass takes each job's learned run bucket function
+// first_mode: the bucket function of the first pass -- MODE_RADIX or MODE_RLEARN (each
+// job's learned run buckets); later passes are MODE_RADIX
 int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels, bool keep_const = false,
-               bool learned_first = false) {
+               u32 first_mode = MODE_RADIX) {
   u32 cur = 0, src = first_src;
   u32 done = 0;
   for (u32 lvl = 0; lvl < MAX_LEVELS; ++lvl) {
-    const bool rl = learned_first && lvl == 0;
-    const u32 mode = rl ? (u32)MODE_RLEARN : (u32)MODE_RADIX;
+    const u32 mode = lvl == 0 ? first_mode : (u32)MODE_RADIX;
+    const LearnCtx lcm = lctx(p, false);
     if (!p->graph_mode) {
       CK(cudaMemcpyAsync(&p->h_cnt[C_BIG0 + cur], &p->d_cnt[C_BIG0 + cur], sizeof(u32), cudaMemcpyDeviceToHost, p->st));
       CK(cudaStreamSynchronize(p->st));
@@ -582,15 +583,17 @@ int run_levels(mpsm_plan* p, u32 first_src, u32 final_where, u32* levels, bool k
     const u32 rb = p->opt.radix_bits ? p->opt.radix_bits : 11u;
     LAUNCH(K_PLAN, launch_level_plan(p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->big_cap, p->d_ls, tot, mode, CH_RADIX, rb,
                       p->d_jobs, p->hist_a_cap, p->bucket_cap, &p->d_cnt[C_ERR], p->st,
-                      keep_const ? FILL_FUSED : 0, p->d_rl));
+                      keep_const ? FILL_FUSED : 0, &lcm));
     LAUNCH(K_INIT, launch_init_buckets(p->d_bmin, p->d_bmax, nullptr, tot, p->st, p->nsm));
-    LAUNCH(rl ? K_HIST_RLEARN : K_HIST_RADIX, launch_hist(mode, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs, src,
-                p->d_hist_a, p->d_bmin, p->d_bmax, nullptr, lctx(p, false), p->st, p->nsm));
+    const Kid kh = mode == MODE_RLEARN ? K_HIST_RLEARN : K_HIST_RADIX;
+    const Kid ks = mode == MODE_RLEARN ? K_SCATTER_RLEARN : K_SCATTER_RADIX;
+    LAUNCH(kh, launch_hist(mode, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs, src,
+                p->d_hist_a, p->d_bmin, p->d_bmax, nullptr, lcm, p->st, p->nsm));
     LAUNCH(K_SCAN_RADIX, launch_scan(MODE_RADIX, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, p->d_hist_a, p->d_bmin, p->d_bmax,
                 nullptr, p->d_big[cur ^ 1], &p->d_cnt[C_BIG0 + (cur ^ 1)], p->big_cap, p->d_fin, &p->d_cnt[C_FIN],
                 p->fin_cap, dst, p->d_jobs, nullptr, &p->d_cnt[C_ERR], p->st, p->nsm, keep_const));
-    LAUNCH(rl ? K_SCATTER_RLEARN : K_SCATTER_RADIX, launch_scatter(mode, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs,
-                   src, dst, p->d_hist_a, nullptr, &p->d_cnt[C_ERR], lctx(p, false), p->st, p->nsm, lvl == 0));
+    LAUNCH(ks, launch_scatter(mode, p->d_big[cur], &p->d_cnt[C_BIG0 + cur], p->d_ls, tot, CH_RADIX, bufs(p), p->d_jobs,
+                   src, dst, p->d_hist_a, nullptr, &p->d_cnt[C_ERR], lcm, p->st, p->nsm, lvl == 0));
     CK(cudaGetLastError());
     src = dst;
     cur ^= 1;
@@ -637,7 +640,7 @@ int phase_runs(mpsm_plan* p) {
                                               p->d_rcell, p->d_rbnd, p->st));
   }
   LAUNCH(K_SAMPLE, launch_sample_bounds(p->d_big[0], &p->d_cnt[C_BIG0], p->h_cnt[C_BIG0] ? p->big_cap : 0, bufs(p), p->d_jobs, p->st));
-  int rc = run_levels(p, W_RIN, W_XR, &p->levels_r, false, rl);
+  int rc = run_levels(p, W_RIN, W_XR, &p->levels_r, false, rl ? (u32)MODE_RLEARN : (u32)MODE_RADIX);
   if (rc) return rc;
   rc = final_sort(p, W_XR);
   if (rc) return rc;

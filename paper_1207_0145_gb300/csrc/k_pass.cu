@@ -143,7 +143,7 @@ __global__ void k_sample_bounds(Seg* segs, const u32* nseg_ptr, Bufs bufs, const
 __global__ void __launch_bounds__(1024) k_level_plan(const Seg* segs, u32* nseg_ptr, u32 seg_cap, LSeg* ls,
                                                      u64* totals, u32 mode, u64 chunk, u32 radix_bits, u64 fill,
                                                      const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err,
-                                                     const RunLearn* rl) {
+                                                     LearnCtx lc) {
   __shared__ u64 s_warp[33];
   __shared__ u64 carry[3];
   u32 n = *nseg_ptr;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(1024) k_level_plan(const Seg* segs, u32* nseg_
         lo = s.kmin;
       } else if (mode == MODE_RLEARN) {
         // the job's learned bucket function: lo and shift give the cell of a key
-        const RunLearn& RL = rl[s.job];
+        const RunLearn& RL = lc.rl[s.job];
         lo = RL.lo;
         shift = RL.shift;
         F = RL.F;
@@ -1551,9 +1551,9 @@ void launch_sample_bounds(Seg* segs, const u32* nseg, u32 max_segs, Bufs bufs, c
 
 void launch_level_plan(const Seg* segs, u32* nseg, u32 seg_cap, LSeg* ls, u64* totals, u32 mode, u64 chunk,
                        u32 radix_bits, const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err, cudaStream_t st,
-                       u64 fill, const RunLearn* rl) {
+                       u64 fill, const LearnCtx* lc) {
   k_level_plan<<<1, 1024, 0, st>>>(segs, nseg, seg_cap, ls, totals, mode, chunk, radix_bits, fill, jobs, hist_cap,
-                                   bucket_cap, err, rl);
+                                   bucket_cap, err, lc ? *lc : LearnCtx{});
 }
 
 void launch_init_buckets(u64* bmin, u64* bmax, u64* btot, const u64* totals, cudaStream_t st, int nsm) {
@@ -1570,6 +1570,7 @@ void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, con
   } else if (mode == MODE_RLEARN) {
     k_hist<MODE_RLEARN, F_MAX><<<nsm * 2, NT_PASS, SMEM_HIST_LEARN, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
                                                                         src_where, hist, bmin, bmax, btot, lc);
+
   } else if (mode == MODE_LEARN) {
     k_hist<MODE_LEARN, F_MAX><<<nsm * 2, NT_PASS, SMEM_HIST_LEARN, st>>>(segs, nseg, ls, totals, chunk, bufs, jobs,
                                                                        src_where, hist, bmin, bmax, btot, lc);
@@ -1618,6 +1619,7 @@ void launch_scatter(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, 
   } else if (mode == MODE_RLEARN) {  // the learned run bucket tables take the learned pass's layout
     k_scatter<MODE_RLEARN, LN_TILE, LN_NT, 1, 2><<<nsm, LN_NT, smem_scatter(LN_TILE, 2, true), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);
+
   } else if (big_tiles) {
     k_scatter<MODE_RADIX, RX_TILE, RX_NT, RX_MINB, RX_STAGES><<<nsm * RX_MINB, RX_NT, smem_scatter(RX_TILE, RX_STAGES), st>>>(
         segs, nseg, ls, totals, chunk, bufs, jobs, src_where, dst_where, hist, sp, err, lc);

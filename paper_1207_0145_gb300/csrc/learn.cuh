@@ -198,10 +198,8 @@ __device__ __forceinline__ u32 learned_cell_part(u32 e, const u64* bnd, const u3
 // The bucket function of a learned first sort pass over a job's runs: F buckets cut
 // at F - 1 quantiles of a sorted, evenly spaced sample of m run-side keys, found
 // through a table of ncell equal cells over the sample's key range: cell =
-// min((key - lo) >> shift, ncell - 1), a key below lo taking cell 0.  bucket(key) =
-// #(boundaries < key): bucket b holds the keys in (boundary b - 1, boundary b], so a
-// key equal to several boundaries goes whole to the first bucket it bounds (a constant
-// child when it is frequent, which the sort leaves in place).
+// min((key - lo) >> shift, ncell - 1), a key below lo taking cell 0.  The bucket of a
+// key is run_learn_bucket's.
 struct RunLearn {
   u64 lo;
   u32 shift, ncell;
@@ -214,14 +212,21 @@ __device__ __forceinline__ u32 run_learn_cell(const RunLearn& RL, u64 key) {
   return c < (u64)RL.ncell ? (u32)c : RL.ncell - 1u;
 }
 
-// #(boundaries < key) from the key's cell entry e (the cell table's encoding, LCELL_*):
-// the cell's partition when no boundary falls in it, else a bisection over the
-// boundaries plo..phi - 1 that do (bnd in shared memory)
+// The learned bucket of `key` for sorted boundaries bnd: #(bnd < key), plus one when the
+// key equals a boundary.  Bucket b then holds the keys strictly between two boundary
+// values or one boundary value alone, so a key equal to two or more boundaries (a hot
+// key) fills a bucket of its own, a constant child; the function stays monotone.  From
+// the key's cell entry e (the cell table's encoding, LCELL_*): the cell's bucket when no
+// boundary falls in it, else a bisection over the boundaries plo..phi - 1 that do
+// (bnd in shared memory).
 __device__ __forceinline__ u32 run_learn_bucket(u32 e, const u64* bnd, u64 key) {
   if (!(e & LCELL_SPLIT)) return e;
   u32 pos = e & 0x3FFFu;
   const u32 phi = (e >> 16) & 0x3FFFu;
-  if (e & LCELL_HOT) return key <= bnd[pos] ? pos : phi;  // every boundary here is one key
+  if (e & LCELL_HOT) {  // every boundary here is one key
+    const u64 hot = bnd[pos];
+    return key < hot ? pos : (key == hot ? pos + 1u : phi);
+  }
   u32 len = phi - pos;
   while (len > 0) {
     const u32 h = len >> 1;
@@ -232,7 +237,7 @@ __device__ __forceinline__ u32 run_learn_bucket(u32 e, const u64* bnd, u64 key) 
       len = h;
     }
   }
-  return pos;
+  return (pos < phi && bnd[pos] == key) ? pos + 1u : pos;
 }
 
 struct LearnCtx {

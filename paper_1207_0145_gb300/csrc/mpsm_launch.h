@@ -19,7 +19,7 @@ void launch_sample_bounds(Seg* segs, const u32* nseg, u32 max_segs, Bufs bufs, c
 void launch_level_plan(const Seg* segs, u32* nseg, u32 seg_cap, LSeg* ls, u64* totals, u32 mode, u64 chunk,
                        u32 radix_bits, const Job* jobs, u64 hist_cap, u64 bucket_cap, u32* err, cudaStream_t st,
                        u64 fill = 0,   // MODE_RADIX: target tuples per bucket, 0 = power-of-two buckets
-                       const RunLearn* rl = nullptr);  // MODE_RLEARN: the jobs' learned run bucket functions
+                       const LearnCtx* lc = nullptr);  // MODE_RLEARN: the learned run bucket tables
 void launch_init_buckets(u64* bmin, u64* bmax, u64* btot, const u64* totals, cudaStream_t st, int nsm);
 void launch_hist(u32 mode, const Seg* segs, const u32* nseg, const LSeg* ls, const u64* totals, u64 chunk,
                  Bufs bufs, const Job* jobs, u32 src_where, u32* hist, u64* bmin, u64* bmax, u64* btot,
