@@ -119,3 +119,22 @@ def test_batch_jobs_each_take_their_own_bucket_function():
     with Plan(nR, nS, max_jobs=len(jobs), runs_r=3, run_buckets=M.RUNS_LEARNED) as p:
         counts, sums = p.join_batch([(to_dev(r), to_dev(s)) for r, s in hosts])
     assert list(zip(counts, sums)) == [oracle.join(r, s) for r, s in hosts]
+
+
+@pytest.mark.parametrize("w", [gen.plain(1 << 18, 1 << 21, seed=94), gen.zipf(1 << 18, 1 << 21, 1.1, seed=95)])
+def test_reversed_roles_sort_the_foreign_keys_into_runs(w):
+    # with R partitioned, S is cut into runs: its foreign keys repeat (hot keys under
+    # Zipf), so the learned run buckets meet keys equal to many boundaries
+    R, S = w.r_host(), w.s_host()
+    with Plan(w.n_r, w.n_s, partition_side=M.PART_R, runs_r=3, run_buckets=M.RUNS_LEARNED) as p:
+        assert p.join(to_dev(R), to_dev(S)) == oracle.join(R, S)
+        assert p.device_errors() == 0
+
+
+def test_short_runs_take_no_sort_pass():
+    # runs of at most 8192 tuples are sorted in shared memory directly; the option is inert
+    w = gen.plain(200_000, 800_000, seed=96)
+    R, S = w.r_host(), w.s_host()
+    with Plan(w.n_r, w.n_s, runs_r=64, run_buckets=M.RUNS_LEARNED) as p:
+        assert p.join(to_dev(R), to_dev(S)) == oracle.join(R, S)
+        assert p.stats()["levels_r"] == 0
