@@ -763,10 +763,16 @@ __device__ __forceinline__ u64 block_sum_u64(u64 v, u64* s_red) {
 // Join of a segment or piece whose keys all equal `key` (n tuples at s, global or
 // shared): every R tuple of its windows with that key matches every S tuple.
 // Each matching R tuple r adds n pairs and n r.pay + (sum of the S payloads) to
-// the calling thread's running count and checksum.
+// the calling thread's running count and checksum.  The windows of up to RCH runs at a
+// time are staged in rtab (free shared memory) with their prefix sums, so the block's
+// threads share every window position: a hot key's long window in one run is read by
+// all of them, not walked by one thread.
+constexpr u32 RCH = 128;
+
 template <u32 NT>
 __device__ __forceinline__ void seg_join_const(const Tuple* s, u32 n, u64 key, const Seg& sg, u32 item,
-                                               const FuseCtx& fc, u64* s_red, u64& acc_cnt, u64& acc_chk) {
+                                               const FuseCtx& fc, u64* s_red, u32* rtab, u64& acc_cnt,
+                                               u64& acc_chk) {
   const u32 tid = threadIdx.x;
   const Job& J = fc.jobs[sg.job];
   u64 ssum = 0;
@@ -775,12 +781,55 @@ __device__ __forceinline__ void seg_join_const(const Tuple* s, u32 n, u64 key, c
   if (tid == 0) s_red[0] = ssum;
   __syncthreads();
   ssum = s_red[0];
-  __syncthreads();
-  for (u32 j = tid; j < J.runs; j += NT) {
-    const u32* w = fc.swin + 2ull * ((u64)item * fc.maxT + j);
-    const Tuple* r = fc.xr + fc.runs[J.run_base + j].off;
-    for (u32 q = w[0]; q < w[1]; ++q) {  // the windows cover the segment's bounds, which may exceed `key`
-      const Tuple t = r[q];
+  u32* wl = rtab;                                            // RCH window starts
+  u32* wpre = rtab + RCH;                                    // RCH + 1 window prefix
+  u64* roff = reinterpret_cast<u64*>(rtab + 2 * RCH + 8);    // RCH run offsets
+  const u32 T = J.runs;
+  for (u32 j0 = 0; j0 < T; j0 += RCH) {
+    const u32 nr = T - j0 < RCH ? T - j0 : RCH;
+    __syncthreads();  // ssum read; the previous chunk's readers are done
+    if (tid < nr) {
+      const u32* w = fc.swin + 2ull * ((u64)item * fc.maxT + j0 + tid);
+      wl[tid] = w[0];
+      wpre[tid] = w[1] > w[0] ? w[1] - w[0] : 0u;
+      roff[tid] = fc.runs[J.run_base + j0 + tid].off;
+    }
+    __syncthreads();
+    if (tid < 32) {  // exclusive scan of the window lengths, 4 per lane
+      u32 v[4], sum = 0;
+#pragma unroll
+      for (u32 k = 0; k < 4; ++k) {
+        const u32 idx = tid * 4 + k;
+        v[k] = idx < nr ? wpre[idx] : 0u;
+        sum += v[k];
+      }
+      u32 inc = sum;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const u32 y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (tid >= (u32)d) inc += y;
+      }
+      u32 run = inc - sum;
+#pragma unroll
+      for (u32 k = 0; k < 4; ++k) {
+        const u32 idx = tid * 4 + k;
+        if (idx < nr) wpre[idx] = run;
+        run += v[k];
+      }
+      const u32 tot = __shfl_sync(0xffffffffu, inc, 31);
+      if (tid == 0) wpre[nr] = tot;
+    }
+    __syncthreads();
+    const u32 W = wpre[nr];
+    for (u32 q = tid; q < W; q += NT) {
+      u32 lo = 0, hi = nr;  // run: last with wpre[lo] <= q
+      while (hi - lo > 1) {
+        const u32 mid = (lo + hi) >> 1;
+        if (wpre[mid] <= q) lo = mid;
+        else hi = mid;
+      }
+      // the windows cover the segment's bounds, which may exceed `key`
+      const Tuple t = ld_stream(fc.xr + roff[lo] + wl[lo] + (q - wpre[lo]));
       if (t.key == key) {
         acc_cnt += n;
         acc_chk += ssum + (u64)n * t.pay;
@@ -808,7 +857,6 @@ __device__ __forceinline__ void flush_job_result(u64& acc_cnt, u64& acc_chk, u32
 // order-preserving directory of at most CAP/2 key buckets, unless cdir gives the
 // exact per-key starts; rtab (free shared memory) stages up to RCH runs' windows
 // and their prefix sums at a time, so every thread takes any window position.
-constexpr u32 RCH = 128;
 
 // The window of run tid (< RCH) of the block's segment, read by thread tid when the
 // segment starts, so that its latency hides behind the sort; the first RCH runs'
@@ -1033,7 +1081,7 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     if (constant) {
       publish_next();
       if (FUSE) {
-        seg_join_const<NT>(src, n, sg.kmin, sg, item, fc, s_red, acc_cnt, acc_chk);
+        seg_join_const<NT>(src, n, sg.kmin, sg, item, fc, s_red, reinterpret_cast<u32*>(ib), acc_cnt, acc_chk);
       } else if (!inplace) {
         for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, src[i]);
       }
@@ -1109,7 +1157,7 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
     const u32 bits = bitlen64(mx - mn);
     if (bits == 0) {
       if (FUSE) {
-        seg_join_const<NT>(tup, n, mn, sg, item, fc, s_red, acc_cnt, acc_chk);
+        seg_join_const<NT>(tup, n, mn, sg, item, fc, s_red, reinterpret_cast<u32*>(ib), acc_cnt, acc_chk);
       } else if (!inplace) {
         for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, tup[i]);
       }

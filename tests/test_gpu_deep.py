@@ -14,7 +14,7 @@ import pytest
 
 import gen
 import oracle
-from tests.helpers import from_dev_ptr, same_multiset, to_dev
+from tests.helpers import from_dev_ptr, random_tuples, same_multiset, to_dev
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -97,3 +97,18 @@ def test_pairs_at_ten_million_match_the_per_row_closed_form():
     with Plan(w.n_r, w.n_s) as p:
         assert p.join(to_dev(R), to_dev(S), pairs=out) == oracle.closed_form(w)
     assert same_multiset(out.cpu().numpy().view(np.uint64), want)
+
+
+def test_hot_key_in_both_inputs_on_the_fused_path():
+    # half of R is one key and 20000 S tuples carry it: the S key's constant segments
+    # (in 8192-tuple pieces) meet a window of about 2^18 R tuples in each of the 4 runs,
+    # which every thread of the block shares
+    rng = np.random.default_rng(97)
+    R = random_tuples(rng, 1 << 21, 1 << 30)
+    S = random_tuples(rng, 1 << 21, 1 << 30)
+    R[: 1 << 20, 0] = np.uint64(7)
+    S[:20000, 0] = np.uint64(7)
+    R = R[rng.permutation(len(R))]
+    with Plan(len(R), len(S), runs_r=4) as p:
+        assert p.join(to_dev(R), to_dev(S)) == oracle.join(R, S)
+        assert p.device_errors() == 0
