@@ -236,6 +236,8 @@ __global__ void k_run_cdf(const Job* jobs, u32 njobs, const Run* runs, const Tup
   }
 }
 
+constexpr u32 KCAND = 2048;  // candidate costs the splitter solve sorts in shared memory (a power of two)
+
 __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s, const u64* rc, u64* fine_r, u32* sp,
                                                     u32* part_fstart, u32* err, bool height) {
   constexpr u32 NT = 1024;
@@ -332,12 +334,29 @@ __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s
     Ahi[a] = (u16)nb;
   }
   __syncthreads();
-  // bisection on the largest admissible cost C
+  // Bisection on the largest admissible cost C.  Feasibility changes only at costs
+  // cost(a, b) of some bucket range, so the optimum is lo itself or the cost of a range
+  // b in (Alo[a], Ahi[a]] for some a (the jumps at a cost below lo and at hi).  Once there
+  // are fewer than KCAND such ranges, the optimum is the smallest feasible value among
+  // lo and their costs: they are sorted and the bisection continues over their indices
+  // (candidate mode), with the same feasibility test.
+  u64* cand = reinterpret_cast<u64*>(jarr + 5 * AW);  // KCAND
+  bool cmode = false;
+  u32 ci_lo = 0, ci_hi = 0;
   for (;;) {
-    const u64 lo = s_lo;
-    const u64 hi = s_hi;
-    const bool last = !(lo < hi);
-    const u64 C = last ? lo : lo + (hi - lo) / 2;
+    bool last;
+    u64 C;
+    u32 cmid = 0;
+    if (!cmode) {
+      const u64 lo = s_lo;
+      const u64 hi = s_hi;
+      last = !(lo < hi);
+      C = last ? lo : lo + (hi - lo) / 2;
+    } else {
+      last = !(ci_lo < ci_hi);
+      cmid = last ? ci_lo : ci_lo + (ci_hi - ci_lo) / 2;
+      C = cand[cmid];
+    }
     for (u32 a = tid; a < nb; a += NT) {
       u32 l = Alo[a], h = Ahi[a];  // cost(a, l) <= C, and A_C[a] <= h
       const u64 ha = PH[a], ga = PG[a];
@@ -366,8 +385,14 @@ __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s
     }
     __syncthreads();
     const bool feasible = pos == nb;
-    if (tid == 0) {
-      if (feasible) s_hi = C; else s_lo = C + 1;
+    if (!cmode) {
+      if (tid == 0) {
+        if (feasible) s_hi = C; else s_lo = C + 1;
+      }
+    } else if (feasible) {
+      ci_hi = cmid;  // every thread keeps the same indices
+    } else {
+      ci_lo = cmid + 1;
     }
     u16* t = Acur;
     if (feasible) {
@@ -378,6 +403,69 @@ __global__ void __launch_bounds__(1024) k_splitters(Job* jobs, const u64* fine_s
       Alo = t;
     }
     __syncthreads();
+    if (!cmode) {
+      // the ranges whose cost lies in the bracket (block-uniform count)
+      u64 k = 0;
+      for (u32 a = tid; a < nb; a += NT) k += (u64)(Ahi[a] - Alo[a]);
+      k = warp_sum(k);
+      if (lane_id() == 0) s_red[warp_id()] = k;
+      __syncthreads();
+      u64 K = 0;
+      for (u32 w = 0; w < NT / 32; ++w) K += s_red[w];
+      __syncthreads();
+      if (K + 1 <= KCAND) {
+        if (tid == 0) {
+          s_parts = 1;
+          cand[0] = s_lo;
+        }
+        __syncthreads();
+        for (u32 a = tid; a < nb; a += NT) {
+          const u64 ha = PH[a], ga = PG[a];
+          for (u32 b = Alo[a] + 1u; b <= Ahi[a]; ++b) {
+            const u32 at = atomicAdd(&s_parts, 1u);
+            cand[at] = split_cost(PH[b] - ha, PG[b] - ga, T, height, bad);
+          }
+        }
+        const u32 KC = (u32)K + 1u;
+        u32 KP = 1;
+        while (KP < KC) KP <<= 1;
+        for (u32 i = KC + tid; i < KP; i += NT) cand[i] = ~0ull;
+        __syncthreads();
+        // bitonic sort of the KP <= KCAND candidates
+        for (u32 sz = 2; sz <= KP; sz <<= 1) {
+          for (u32 st = sz >> 1; st > 0; st >>= 1) {
+            for (u32 i = tid; i < KP; i += NT) {
+              const u32 j = i ^ st;
+              if (j > i) {
+                const bool up = (i & sz) == 0;
+                const u64 x = cand[i], y = cand[j];
+                if ((x > y) == up) {
+                  cand[i] = y;
+                  cand[j] = x;
+                }
+              }
+            }
+            __syncthreads();
+          }
+        }
+        cmode = true;
+        // costs below lo (ranges the first jumps admit without a test) cannot be the
+        // optimum; starting at lo keeps every tested cost inside the jumps' bracket
+        const u64 lo = s_lo;
+        ci_lo = 0;
+        u32 m = KC;
+        while (m > 0) {
+          const u32 h = m >> 1;
+          if (cand[ci_lo + h] < lo) {
+            ci_lo += h + 1;
+            m -= h + 1;
+          } else {
+            m = h;
+          }
+        }
+        ci_hi = KC - 1u;  // the largest candidate is at least the optimum, so feasible
+      }
+    }
   }
   if (bad) atomicOr(&s_bad, 1u);
   // leftmost greedy grouping at the optimum
@@ -445,7 +533,8 @@ __global__ void k_fold(const Seg* segs, const u32* nseg_ptr, const LSeg* ls_fine
   }
 }
 
-constexpr size_t SMEM_SPLITTERS = 2 * (FINE_MAX + 1) * sizeof(u64) + 5 * (FINE_MAX + 8) * sizeof(u16);
+constexpr size_t SMEM_SPLITTERS = 2 * (FINE_MAX + 1) * sizeof(u64) + 5 * (FINE_MAX + 8) * sizeof(u16) +
+                                  KCAND * sizeof(u64);
 
 }  // namespace
 
