@@ -152,8 +152,10 @@ def phase2_oracle(R, S, v, T):
     return Rs, run_off, kmin, kmax
 
 
+# (8, 200) and (12, 2000): few buckets per partition, so the splitter solve reaches its
+# candidate bisection early; (12, 512): the headline's partition count
 @pytest.mark.parametrize("fine_bits,parts,kind", [(12, 0, 0), (6, 9, 0), (2, 2, 0), (10, 0, 1), (12, 0, 1),
-                                                  (10, 0, 0)])
+                                                  (10, 0, 0), (8, 200, 0), (12, 2000, 0), (12, 512, 0)])
 def test_phase2_histograms_splitters_prefix_sums(fine_bits, parts, kind):
     # kind 1: equi-height splitters (Sec. 5.6) on the negatively correlated workload
     w = gen.zipf(60_000, 500_000, 0.9, seed=13) if (kind == 0 and fine_bits != 10) else gen.negcorr(60_000, 240_000, seed=17)
