@@ -276,17 +276,27 @@ def traffic_per_tuple(config: str):
         return None
 
 
-def host_numa_of(ptr: int):
-    """NUMA node(s) holding the pages of the host mapping that contains ptr (Linux numa_maps)."""
+def host_numa_of(ptr: int, nbytes: int = 1):
+    """Pages per NUMA node of the host mappings that overlap [ptr, ptr + nbytes), summed
+    (Linux maps and numa_maps), as "N0=pages N1=pages"."""
     try:
-        best = None
+        starts = set()
+        with open("/proc/self/maps") as f:
+            for line in f:
+                lo, hi = (int(x, 16) for x in line.split()[0].split("-"))
+                if lo < ptr + nbytes and hi > ptr:
+                    starts.add(lo)
+        nodes = {}
         with open("/proc/self/numa_maps") as f:
             for line in f:
                 parts = line.split()
-                a = int(parts[0], 16)
-                if a <= ptr and (best is None or a > best[0]):
-                    best = (a, [p for p in parts[1:] if p[:1] == "N" and "=" in p])
-        return " ".join(best[1]) if best else None
+                if int(parts[0], 16) not in starts:
+                    continue
+                for q in parts[1:]:
+                    if q[:1] == "N" and "=" in q:
+                        k, v = q.split("=")
+                        nodes[k] = nodes.get(k, 0) + int(v)
+        return " ".join(f"{k}={v}" for k, v in sorted(nodes.items())) or None
     except (OSError, ValueError):
         return None
 
@@ -325,6 +335,31 @@ def measure_h2d(host, dev, stream, nbytes: int = 4 << 30, reps: int = 3):
         best = max(best, n / (e0.elapsed_time(e1) / 1e3) / 1e9)
     del dst
     return best
+
+
+def measure_h2d_whole(bufs, dev, stream, chunk: int = 4 << 30):
+    """Milliseconds to copy every byte of the pinned buffers `bufs` to the device, in chunks
+    of `chunk` bytes into one device buffer (the link over the whole of each buffer, not a
+    prefix), and the slowest chunk's GB/s."""
+    import torch
+
+    dst = torch.empty(chunk, dtype=torch.uint8, device=dev)
+    evs = []
+    with torch.cuda.stream(stream):
+        for h in bufs:
+            src = h.view(torch.uint8).reshape(-1)
+            for a in range(0, src.numel(), chunk):
+                n = min(chunk, src.numel() - a)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                dst[:n].copy_(src[a:a + n], non_blocking=True)
+                e1.record(stream)
+                evs.append((n, e0, e1))
+    evs[-1][2].synchronize()
+    total = sum(e0.elapsed_time(e1) for _, e0, e1 in evs)
+    slowest = min(n / (e0.elapsed_time(e1) / 1e3) / 1e9 for n, e0, e1 in evs)
+    del dst
+    return total, slowest
 
 
 def cpu_baseline(w, div: int):
@@ -615,26 +650,32 @@ def run_ours(args):
         torch.cuda.synchronize()
         h2d_before = measure_h2d(Sh, dev, stream)
         barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(args.steps):
+        fe = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        fe[0].record(stream)
+        for i in range(args.steps):
             plan.join_host(Rh, Sh)
-        f1.record(stream)
-        f1.synchronize()
+            fe[i + 1].record(stream)
+        fe[-1].synchronize()
         barrier()
-        ems, evalue = aggregate_replicas(f0.elapsed_time(f1) / args.steps, units, dist, dev)
+        ems, evalue = aggregate_replicas(fe[0].elapsed_time(fe[-1]) / args.steps, units, dist, dev)
+        each = [round(fe[i].elapsed_time(fe[i + 1]), 1) for i in range(args.steps)]
         # the host link as this run saw it, right after the timed steps: plain copies from the
-        # same pinned buffer, and where that buffer's pages and the GPU sit
+        # same pinned buffers, and where their pages and the GPU sit
         h2d = measure_h2d(Sh, dev, stream)
+        whole_ms, whole_min_gbs = measure_h2d_whole((Rh, Sh), dev, stream)
         e2e = {"value": evalue, "unit": UNIT, "h2d_bytes_per_step": units * 16,
                "d2h_bytes_per_step": 16, "ms_per_step": ems,
                "h2d_gbs_measured": round(h2d, 1), "h2d_gbs_before": round(h2d_before, 1),
                "copy_bound_ms": round(units * 16 / (h2d * 1e9) * 1e3, 2),
                "over_copy_bound": round(ems / (units * 16 / (h2d * 1e9) * 1e3), 3),
-               "host_numa_pinned": host_numa_of(Sh.data_ptr()), "gpu_host_numa": gpu_host_numa(local),
+               "ms_each_step": each, "copy_whole_ms": round(whole_ms, 2),
+               "copy_whole_slowest_chunk_gbs": round(whole_min_gbs, 1),
+               "host_numa_pinned": host_numa_of(Sh.data_ptr(), Sh.numel() * Sh.element_size()),
+               "gpu_host_numa": gpu_host_numa(local),
                "what": "mpsm_join_host: R and S copied from pinned host memory every step, then joined; "
                        "copy_bound_ms = the step's input bytes at the host-to-device rate measured right after the "
-                       "timed steps (h2d_gbs_before: the same copy right before them)"}
+                       "timed steps (h2d_gbs_before: the same copy right before them); copy_whole_ms = plain copies of all "
+                       "of R and S in 4 GiB chunks, right after"}
         del Rh, Sh
 
     balance = partition_balance(plan, st) if args.splitter != "learned" else None
