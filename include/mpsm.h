@@ -139,9 +139,9 @@ int mpsm_join(mpsm_plan_t* plan, const mpsm_tuple_t* R, uint64_t nR, const mpsm_
  * and joins them there.  The run side is copied first and sorted while the
  * partitioned side is still on the host link.  When the partitioned side holds at
  * least 2^28 tuples (and no learned mode or MPSM_FLAG_UNFUSED is set), it is copied
- * in pieces of 2^27 tuples (more once 64 pieces would not cover it), and each piece
- * is range-partitioned, sorted and joined against the sorted runs while the next
- * one is in flight; the result is the same, since the join sums over the pairs of
+ * in equal pieces of about a quarter of the run side, between 2^26 and 2^27 tuples
+ * (larger once 64 pieces would not cover it), and each piece is range-partitioned,
+ * sorted and joined against the sorted runs while the next one is in flight; the result is the same, since the join sums over the pairs of
  * each piece.  mpsm_plan_stats then describes the last piece's partitioning.
  * Synchronises the plan's stream. */
 int mpsm_join_host(mpsm_plan_t* plan, const mpsm_tuple_t* R_host, uint64_t nR,

@@ -768,6 +768,9 @@ __device__ __forceinline__ u64 block_sum_u64(u64 v, u64* s_red) {
 // threads share every window position: a hot key's long window in one run is read by
 // all of them, not walked by one thread.
 constexpr u32 RCH = 128;
+// shared memory the fused kernel adds after the counting array, so that the u16
+// directory of a segment covers 2^14 keys (two blocks per SM still fit)
+constexpr u32 DIR_EXT_BYTES = 16384;
 
 template <u32 NT>
 __device__ __forceinline__ void seg_join_const(const Tuple* s, u32 n, u64 key, const Seg& sg, u32 item,
@@ -853,10 +856,11 @@ __device__ __forceinline__ void flush_job_result(u64& acc_cnt, u64& acc_chk, u32
 
 // Join of a sorted segment (tup in the order ia, n tuples, keys in [mn, mx])
 // against its R windows, added to the calling thread's running count and
-// checksum.  dir (the free ping-pong index array, CAP entries) becomes an
-// order-preserving directory of at most CAP/2 key buckets, unless cdir gives the
-// exact per-key starts; rtab (free shared memory) stages up to RCH runs' windows
-// and their prefix sums at a time, so every thread takes any window position.
+// checksum.  dir (free shared memory, 2^DIRB u16 entries) becomes an
+// order-preserving directory of at most 2^DIRB - 1 key buckets -- one key per
+// bucket when the segment's key range allows -- unless cdir gives the exact per-key
+// starts; rtab (free shared memory) stages up to RCH runs' windows and their prefix
+// sums at a time, so every thread takes any window position.
 
 // The window of run tid (< RCH) of the block's segment, read by thread tid when the
 // segment starts, so that its latency hides behind the sort; the first RCH runs'
@@ -866,17 +870,18 @@ struct WinReg {
   u64 off;     // the run's first position in xr
 };
 
-template <u32 CAP, u32 NT>
+template <u32 CAP, u32 NT, u32 DIRB>
 __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* dir, u32* rtab, const u32* cdir, u32 n,
                                          u64 mn, u64 mx, const Seg& sg, u32 item, const FuseCtx& fc, const WinReg& wr,
                                          u64& cnt, u64& chk) {
-  constexpr u32 DB = (CAP >= 8192u) ? 12u : 11u;  // 2^DB = CAP / 2 buckets
-  const u32 tid = threadIdx.x;
+  const u32 tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
   const Job& J = fc.jobs[sg.job];
   const u32 T = J.runs, run_base = J.run_base;
-  const u32 rbits = bitlen64(mx - mn);
-  const u32 dsh = rbits > DB ? rbits - DB : 0u;
-  const u32 nbk = (u32)((mx - mn) >> dsh) + 1u;
+  const u64 range = mx - mn;
+  const u32 rbits = bitlen64(range);
+  u32 dsh = rbits > DIRB ? rbits - DIRB : 0u;
+  if ((range >> dsh) + 2u > (u64)(1u << DIRB)) ++dsh;  // nbk + 1 entries fit
+  const u32 nbk = (u32)(range >> dsh) + 1u;
   if (!cdir) {
     // the caller checked every key against [mn, mx]; the clamp keeps the writes inside
     // the nbk + 1 directory entries regardless
@@ -892,9 +897,10 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
         for (u32 x = b + 1u; x <= nbk; ++x) dir[x] = (u16)n;
     }
   }
-  u32* wl = rtab;                                            // RCH window starts
-  u32* wpre = rtab + RCH;                                    // RCH + 1 window prefix
-  u64* roff = reinterpret_cast<u64*>(rtab + 2 * RCH + 8);    // RCH run offsets
+  // wpre: RCH + 1 window prefix sums; rbase: per run, the xr index of window position
+  // q is rbase + q (the window's first tuple minus its prefix, modulo 2^64)
+  u32* wpre = rtab;
+  u64* rbase = reinterpret_cast<u64*>(rtab + RCH + 8);
   for (u32 j0 = 0; j0 < T; j0 += RCH) {
     const u32 nr = T - j0 < RCH ? T - j0 : RCH;
     // directory built; the previous chunk's readers are done (with cdir, the caller's
@@ -913,9 +919,8 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
         hi = w[1];
         off = fc.runs[run_base + j0 + tid].off;
       }
-      wl[tid] = lo;
       wpre[tid] = hi > lo ? hi - lo : 0u;  // empty unless the run was sorted (a failed check)
-      roff[tid] = off;
+      rbase[tid] = off + lo;
     }
     __syncthreads();
     if (tid < 32) {  // exclusive scan of the window lengths, 4 per lane
@@ -936,7 +941,10 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
 #pragma unroll
       for (u32 k = 0; k < 4; ++k) {
         const u32 idx = tid * 4 + k;
-        if (idx < nr) wpre[idx] = run;
+        if (idx < nr) {
+          wpre[idx] = run;
+          rbase[idx] -= run;
+        }
         run += v[k];
       }
       const u32 tot = __shfl_sync(0xffffffffu, inc, 31);
@@ -944,28 +952,34 @@ __device__ __forceinline__ void seg_join(const Tuple* tup, const u16* ia, u16* d
     }
     __syncthreads();
     const u32 W = wpre[nr];
-    constexpr u32 U = 4;  // R loads in flight per thread
-    for (u32 q0 = 0; q0 < W; q0 += NT * U) {
+    constexpr u32 U = 4;  // most R loads in flight per thread
+    // each warp takes 32 Ub consecutive window positions per step, Ub loads of 32
+    // consecutive positions, so a warp's positions span few runs: one search finds the
+    // run of its first position, and each lane walks on from there.  Ub grows with the
+    // windows (1 to U), so that short windows still spread over every warp.
+    const u32 Ub = W >= NT * U ? U : (W + NT - 1u) / NT;
+    for (u32 q0 = wid * (32u * Ub); q0 < W; q0 += NT * Ub) {
+      u32 j = 0, hi = nr;  // the last run whose prefix is <= q0
+      while (hi - j > 1) {
+        const u32 mid = (j + hi) >> 1;
+        if (wpre[mid] <= q0) j = mid;
+        else hi = mid;
+      }
       Tuple r[U];
 #pragma unroll
       for (u32 u = 0; u < U; ++u) {
-        const u32 q = q0 + u * NT + tid;
+        const u32 q = q0 + u * 32u + lane;
         r[u].key = 0;
         r[u].pay = 0;
-        if (q < W) {
-          u32 lo = 0, hi = nr;  // run: last with wpre[lo] <= q
-          while (hi - lo > 1) {
-            const u32 mid = (lo + hi) >> 1;
-            if (wpre[mid] <= q) lo = mid;
-            else hi = mid;
-          }
-          r[u] = ld_stream(fc.xr + roff[lo] + wl[lo] + (q - wpre[lo]));
+        if (u < Ub && q < W) {
+          while (wpre[j + 1] <= q) ++j;  // wpre[nr] = W > q ends the walk
+          r[u] = ld_stream(fc.xr + (rbase[j] + q));
         }
       }
 #pragma unroll
       for (u32 u = 0; u < U; ++u) {
-        const u32 q = q0 + u * NT + tid;
-        if (q >= W) continue;
+        const u32 q = q0 + u * 32u + lane;
+        if (u >= Ub || q >= W) continue;
         const u64 key = r[u].key;
         if (key < mn || key > mx) continue;
         u32 lb, ub;
@@ -1015,7 +1029,7 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
   Tuple* tup = reinterpret_cast<Tuple*>(sm_raw);        // CAP
   u16* ia = reinterpret_cast<u16*>(tup + CAP);          // CAP
   u16* ib = ia + CAP;                                   // CAP
-  u32* cnt = reinterpret_cast<u32*>(ib + CAP);          // NW * 256 (>= 2048)
+  u32* cnt = reinterpret_cast<u32*>(ib + CAP);          // NW * 256 (>= 2048); fused: DIR_EXT_BYTES after it
   __shared__ __align__(8) u64 mbar;
   __shared__ u32 s_item[2];
   __shared__ u32 s_warp[NT / 32 + 1];
@@ -1272,11 +1286,18 @@ __global__ void __launch_bounds__(NT, MINB) k_seg_sort(const Seg* segs, const u3
       sh += w;
     }
     if (FUSE) {
-      if (bits <= 11u)  // one counting pass: its digit starts are an exact per-key directory
-        seg_join<CAP, NT>(tup, ia, nullptr, reinterpret_cast<u32*>(ib), cnt, n, mn, mx, sg, item, fc, wr, acc_cnt,
-                          acc_chk);
+      // the free index array stages the windows; the counting pass's digit starts are an
+      // exact per-key directory after one pass, else the counters and the extension
+      // after them hold a u16 directory
+      constexpr u32 DIRB = 14;
+      static_assert((1u << DIRB) * sizeof(u16) <= NW * 256u * sizeof(u32) + DIR_EXT_BYTES,
+                    "the u16 directory fits the counting array and its extension");
+      if (bits <= 11u)
+        seg_join<CAP, NT, DIRB>(tup, ia, nullptr, reinterpret_cast<u32*>(ib), cnt, n, mn, mx, sg, item, fc, wr,
+                                acc_cnt, acc_chk);
       else
-        seg_join<CAP, NT>(tup, ia, ib, cnt, nullptr, n, mn, mx, sg, item, fc, wr, acc_cnt, acc_chk);
+        seg_join<CAP, NT, DIRB>(tup, ia, reinterpret_cast<u16*>(cnt), reinterpret_cast<u32*>(ib), nullptr, n, mn, mx,
+                                sg, item, fc, wr, acc_cnt, acc_chk);
     } else {
       for (u32 i = tid; i < n; i += NT) st_tuple(dst + i, tup[ia[i]]);
     }
@@ -1553,6 +1574,8 @@ constexpr u32 LN_SMALL = 512;
 constexpr u32 LN_TILE = 4096, LN_NT = 1024;
 constexpr size_t SMEM_HIST_LEARN = F_MAX * 20 + FINE_MAX * 4 + P_MAX * (sizeof(u64) + 2 * sizeof(u32));
 constexpr size_t smem_sort(u32 cap, u32 nt) { return cap * sizeof(Tuple) + 2 * cap * sizeof(u16) + (nt / 32) * 256 * sizeof(u32); }
+// the fused kernel's shared memory: the sort's, then the directory's extension
+constexpr size_t smem_sort_join(u32 cap, u32 nt) { return smem_sort(cap, nt) + DIR_EXT_BYTES; }
 constexpr u32 NT_BIG = 512;  // threads of the 8192-tuple class (one block per SM; 1024 measured slower)
 constexpr size_t SMEM_SCAN = (3 * F_MAX + 1) * sizeof(u64);
 
@@ -1584,7 +1607,7 @@ void init_attrs_pass() {
   set_smem(k_scatter<MODE_SPLIT, RX_TILE, RX_NT, RX_MINB, RX_STAGES>, smem_scatter(RX_TILE, RX_STAGES));
   set_smem(k_seg_sort<NMAX / 2, 2, false, NT_SORT>, smem_sort(NMAX / 2, NT_SORT));
   set_smem(k_seg_sort<NMAX, 1, false, NT_BIG>, smem_sort(NMAX, NT_BIG));
-  set_smem(k_seg_sort<NMAX / 2, 2, true, NT_SORT>, smem_sort(NMAX / 2, NT_SORT));
+  set_smem(k_seg_sort<NMAX / 2, 2, true, NT_SORT>, smem_sort_join(NMAX / 2, NT_SORT));
 }
 
 namespace {
@@ -1691,7 +1714,7 @@ void launch_seg_sort(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs 
 void launch_seg_sort_join(const Seg* segs, const u32* nseg, u32 cap, u32* work, Bufs bufs, const Job* jobs, u32* err,
                           const FuseCtx& fc, cudaStream_t st, int nsm) {
   // one size class: segments above 4096 tuples are sorted and joined in pieces
-  k_seg_sort<NMAX / 2, 2, true, NT_SORT><<<nsm * 2, NT_SORT, smem_sort(NMAX / 2, NT_SORT), st>>>(
+  k_seg_sort<NMAX / 2, 2, true, NT_SORT><<<nsm * 2, NT_SORT, smem_sort_join(NMAX / 2, NT_SORT), st>>>(
       segs, nseg, cap, work, bufs, jobs, W_XS, err, fc);
 }
 

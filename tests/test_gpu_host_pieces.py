@@ -1,11 +1,12 @@
 """mpsm_join_host with the partitioned side copied and joined in pieces.
 
 Above 2^28 partitioned-side tuples the host-buffer join copies that side in
-pieces of 2^27 and joins each piece against the sorted runs while the next one
-is in flight.  The join sums over pairs, so any split gives the same count and
-checksum; these cases check that against the generator's closed form, with a
-ragged last piece, a last piece of a few tuples, and skewed keys whose hot keys
-fall into every piece.
+equal pieces (a quarter of the run side, between 2^26 and 2^27 tuples) and joins
+each piece against the sorted runs while the next one is in flight.  The join
+sums over pairs, so any split gives the same count and checksum; these cases
+check that against the generator's closed form, with a split that leaves the
+last piece a few tuples short, and skewed keys whose hot keys fall into every
+piece.
 """
 import numpy as np
 import pytest

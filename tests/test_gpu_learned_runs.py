@@ -93,7 +93,7 @@ def test_joins_with_learned_runs(w):
 
 
 def test_host_buffers_in_pieces_with_learned_runs():
-    # 2^28 partitioned tuples take the piecewise host join (pieces of 2^27)
+    # 2^28 partitioned tuples take the piecewise host join (four pieces of 2^26)
     w = gen.sparse(1 << 24, 1 << 28, seed=88)
     R = torch.empty((w.n_r, 2), dtype=torch.int64, device="cuda")
     S = torch.empty((w.n_s, 2), dtype=torch.int64, device="cuda")
