@@ -141,12 +141,31 @@ int mpsm_join(mpsm_plan_t* plan, const mpsm_tuple_t* R, uint64_t nR, const mpsm_
  * least 2^28 tuples (and no learned mode or MPSM_FLAG_UNFUSED is set), it is copied
  * in equal pieces of about a quarter of the run side, between 2^26 and 2^27 tuples
  * (larger once 64 pieces would not cover it), and each piece is range-partitioned,
- * sorted and joined against the sorted runs while the next one is in flight; the result is the same, since the join sums over the pairs of
- * each piece.  mpsm_plan_stats then describes the last piece's partitioning.
+ * sorted and joined against the sorted runs while the next one is in flight; the
+ * result is the same, since the join sums over the pairs of each piece.
+ * mpsm_plan_stats then describes the last piece's partitioning.
  * Synchronises the plan's stream. */
 int mpsm_join_host(mpsm_plan_t* plan, const mpsm_tuple_t* R_host, uint64_t nR,
                    const mpsm_tuple_t* S_host, uint64_t nS, uint64_t* out_count,
                    uint64_t* out_checksum);
+
+/* Host memory for mpsm_join_host's inputs (the paper has no counterpart: its inputs
+ * start in memory).  Puts `bytes` (> 0) of zeroed, page-locked host memory in *out,
+ * owned by the caller until mpsm_host_free.  It is an anonymous mapping advised for
+ * transparent huge pages (Linux madvise MADV_HUGEPAGE, then MADV_POPULATE_WRITE and
+ * MADV_COLLAPSE where the kernel has them) and registered with the CUDA driver
+ * (cudaHostRegister).  A plain page-locked allocation made once host memory is
+ * fragmented can hold regions that the host-to-device link reads at a tenth of its
+ * rate; huge pages keep the whole buffer at the link's rate.  Where huge pages are
+ * unavailable the memory is still page-locked, on base pages.  Errors:
+ * MPSM_ERR_INVALID_ARG (null out, bytes == 0), MPSM_ERR_OOM (the mapping failed),
+ * MPSM_ERR_CUDA (the registration failed; nothing stays allocated). */
+int mpsm_host_alloc(uint64_t bytes, void** out);
+
+/* Releases memory from mpsm_host_alloc (p and the same bytes); p == NULL is a no-op.
+ * No copy from it may still be in flight.  MPSM_ERR_CUDA if the unregistration fails
+ * (the mapping is released anyway). */
+int mpsm_host_free(void* p, uint64_t bytes);
 
 /* ---- phase entry points: mpsm_join == these five in order ---------------- */
 /* They run the plain modes; on a plan created with a learned mode,

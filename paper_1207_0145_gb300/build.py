@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmpsm.so")
-SOURCES = ["api.cu", "k_pass.cu", "k_split.cu", "k_join.cu", "k_learn.cu"]
+SOURCES = ["api.cu", "k_pass.cu", "k_split.cu", "k_join.cu", "k_learn.cu", "host_mem.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

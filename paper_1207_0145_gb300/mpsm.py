@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from dataclasses import dataclass
 from typing import Optional, Sequence, Tuple
 
@@ -106,6 +107,8 @@ def lib():
             "mpsm_plan_destroy": ([_p], None),
             "mpsm_join": ([_p, _p, _u64, _p, _u64, P(_u64), P(_u64), P(Pairs)], ctypes.c_int),
             "mpsm_join_host": ([_p, _p, _u64, _p, _u64, P(_u64), P(_u64)], ctypes.c_int),
+            "mpsm_host_alloc": ([_u64, P(_p)], ctypes.c_int),
+            "mpsm_host_free": ([_p, _u64], ctypes.c_int),
             "mpsm_sort_runs": ([_p, _p, _u64], ctypes.c_int),
             "mpsm_splitters": ([_p, _p, _u64], ctypes.c_int),
             "mpsm_scatter": ([_p], ctypes.c_int),
@@ -136,6 +139,21 @@ def lib():
             fn.restype = res
         _lib = L
     return _lib
+
+
+def host_tuples(n: int):
+    """An [n, 2] uint64 numpy array in mpsm_host_alloc memory (zeroed, page-locked, on
+    huge pages where the host allows) for mpsm_join_host's inputs; the memory is released
+    with the last view of it."""
+    import numpy as np
+
+    rows = max(1, int(n))
+    nbytes = rows * 16
+    p = _p()
+    _check(lib().mpsm_host_alloc(nbytes, ctypes.byref(p)), "mpsm_host_alloc")
+    buf = (ctypes.c_uint64 * (2 * rows)).from_address(p.value)
+    weakref.finalize(buf, lib().mpsm_host_free, p.value, nbytes)
+    return np.ctypeslib.as_array(buf).reshape(rows, 2)[: int(n)]
 
 
 class MPSMError(RuntimeError):

@@ -48,3 +48,11 @@ def test_host_numa_of_reads_numa_maps():
     a = np.ones(1 << 20, dtype=np.uint8)
     got = bench.host_numa_of(a.ctypes.data)
     assert got is None or all(p.startswith("N") for p in got.split())
+
+
+def test_host_huge_bytes_of_reads_smaps():
+    import numpy as np
+
+    a = np.ones(1 << 20, dtype=np.uint8)
+    v = bench.host_huge_bytes_of(a.ctypes.data, a.nbytes)
+    assert v is None or (isinstance(v, int) and 0 <= v <= (4 << 30))

@@ -78,3 +78,28 @@ def test_fused_piece_of_equal_keys_inside_a_mixed_segment():
     want = oracle.join(R, S)
     with Plan(16, 8192, partitions_s=1, runs_r=1) as p:
         assert p.join(to_dev(R), to_dev(S)) == want
+
+
+@pytest.mark.parametrize("n_s", [8 << 20, 1 << 20, 500_000, 128_000, 8_000])
+def test_fused_directory_widths(n_s):
+    # R holds 2M dense unique keys, so a segment of about 3840 S tuples spans about
+    # 3840 * 2M / |S| key values: 1K (the counting pass's exact directory), 8K and 15K
+    # (one u16 directory entry per key), 60K and beyond (several keys per entry, a
+    # bisection inside the entry)
+    w = gen.plain(2 << 20, n_s, seed=97)
+    R, S = w.r_host(), w.s_host()
+    want = oracle.join(R, S)
+    with Plan(w.n_r, w.n_s) as p:
+        assert p.join(to_dev(R), to_dev(S)) == want
+        assert p.device_errors() == 0
+
+
+@pytest.mark.parametrize("theta", [0.8, 1.3])
+def test_fused_wide_segments_with_hot_keys(theta):
+    # few S tuples against many R keys and Zipf duplicates: wide directory entries hold
+    # runs of equal keys
+    w = gen.zipf(2 << 20, 300_000, theta, seed=98)
+    R, S = w.r_host(), w.s_host()
+    with Plan(w.n_r, w.n_s) as p:
+        assert p.join(to_dev(R), to_dev(S)) == oracle.join(R, S)
+        assert p.device_errors() == 0

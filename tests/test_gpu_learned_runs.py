@@ -100,8 +100,8 @@ def test_host_buffers_in_pieces_with_learned_runs():
     w.fill_r_device(R.data_ptr(), torch.cuda.current_stream().cuda_stream)
     w.fill_s_device(S.data_ptr(), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
-    Rh = torch.empty(R.shape, dtype=torch.int64, pin_memory=True)
-    Sh = torch.empty(S.shape, dtype=torch.int64, pin_memory=True)
+    Rh = torch.from_numpy(M.host_tuples(w.n_r).view(np.int64))
+    Sh = torch.from_numpy(M.host_tuples(w.n_s).view(np.int64))
     Rh.copy_(R)
     Sh.copy_(S)
     del R, S
