@@ -156,8 +156,13 @@ int mpsm_join_host(mpsm_plan_t* plan, const mpsm_tuple_t* R_host, uint64_t nR,
  * MADV_COLLAPSE where the kernel has them) and registered with the CUDA driver
  * (cudaHostRegister).  A plain page-locked allocation made once host memory is
  * fragmented can hold regions that the host-to-device link reads at a tenth of its
- * rate; huge pages keep the whole buffer at the link's rate.  Where huge pages are
- * unavailable the memory is still page-locked, on base pages.  Errors:
+ * rate; huge pages keep the whole buffer at the link's rate.  From one huge page up
+ * (2 MiB under 4 KiB base pages, 512 MiB under 64 KiB ones) the mapping starts on a
+ * huge-page boundary and spans whole huge pages, so up to one huge page more than
+ * `bytes` is held.  Huge pages are advice: where host memory has just been fragmented
+ * by other processes, part of the buffer can stay on base pages (a buffer made seconds
+ * later usually gets huge pages throughout).  Where huge pages are unavailable the
+ * memory is still page-locked, on base pages.  Errors:
  * MPSM_ERR_INVALID_ARG (null out, bytes == 0), MPSM_ERR_OOM (the mapping failed),
  * MPSM_ERR_CUDA (the registration failed; nothing stays allocated). */
 int mpsm_host_alloc(uint64_t bytes, void** out);
