@@ -678,11 +678,13 @@ def run_ours(args):
                 held.append(t)
                 time.sleep(2.0)
 
+        # each buffer filled before the next one is made: the host splits huge pages that
+        # hold only zeros when memory runs short, as it does while the next buffer is made
         Rh = huge_host(w.n_r, "R")
-        Sh = huge_host(w.n_s, "S")
-        held.clear()
         Rh.copy_(R)
+        Sh = huge_host(w.n_s, "S")
         Sh.copy_(S)
+        held.clear()
         del R, S
         torch.cuda.empty_cache()
         plan.join_host(Rh, Sh)

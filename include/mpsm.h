@@ -161,7 +161,9 @@ int mpsm_join_host(mpsm_plan_t* plan, const mpsm_tuple_t* R_host, uint64_t nR,
  * huge-page boundary and spans whole huge pages, so up to one huge page more than
  * `bytes` is held.  Huge pages are advice: where host memory has just been fragmented
  * by other processes, part of the buffer can stay on base pages (a buffer made seconds
- * later usually gets huge pages throughout).  Where huge pages are unavailable the
+ * later usually gets huge pages throughout), and a kernel that splits underused huge
+ * pages (Linux 6.12 and later) can split those of a buffer still all zeros when memory
+ * runs short, so fill a buffer before making the next large one.  Where huge pages are unavailable the
  * memory is still page-locked, on base pages.  Errors:
  * MPSM_ERR_INVALID_ARG (null out, bytes == 0), MPSM_ERR_OOM (the mapping failed),
  * MPSM_ERR_CUDA (the registration failed; nothing stays allocated). */

@@ -33,10 +33,10 @@ def pinned_inputs(w):
     # the library's page-locked huge-page buffers: released when the test drops them,
     # not kept by the process's pinned-memory pool
     Rh = torch.from_numpy(M.host_tuples(w.n_r).view(np.int64))
-    Sh = torch.from_numpy(M.host_tuples(w.n_s).view(np.int64))
-    assert Rh.is_pinned() and Sh.is_pinned()
     Rh.copy_(R)
+    Sh = torch.from_numpy(M.host_tuples(w.n_s).view(np.int64))
     Sh.copy_(S)
+    assert Rh.is_pinned() and Sh.is_pinned()
     return R, S, Rh, Sh
 
 
