@@ -333,6 +333,7 @@ CONFIGS = {
     # multiplicities 1 and 16 beside the headline's 4 (role reversal, Sec. 5.4)
     "plain-800M-800M": lambda seed=DEFAULT_SEED: plain(800 * M, 800 * M, seed),
     "plain-200M-3200M": lambda seed=DEFAULT_SEED: plain(200 * M, 3200 * M, seed),
+    "plain-283M-2263M": lambda seed=DEFAULT_SEED: plain(283 * M, 2263 * M, seed),  # multiplicity 8
     "zipf0.9-200M-800M": lambda seed=DEFAULT_SEED: zipf(200 * M, 800 * M, 0.9, seed),
     "sparse-1600M-1600M": lambda seed=DEFAULT_SEED: sparse(1600 * M, 1600 * M, 0.7, seed),
     # Sec. 5.6 (multiplicity 4, at a quarter of the paper's 1600M x 6400M)
